@@ -1,0 +1,55 @@
+"""Write the oracle's expected values for the named workloads.
+
+Calls only the CPU oracle (``oracle``) and the shared input generators
+(``graphgen``).  Each output file records, per workload: vertex and edge
+counts, the SHA-256 of the int32 core-number array (little endian), the
+maximum core number, the maximum clique size omega with one witness, and
+the oracle's run statistics.  Usage:
+
+    python tests/golden/make_golden.py chung-lu-20k rmat-s22 ...
+"""
+import hashlib
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import numpy as np  # noqa: E402
+
+import oracle  # noqa: E402
+from graphgen import workloads as W  # noqa: E402
+
+SLUGS = {
+    "chung-lu-20k": (W.CHUNG_LU_20K, W.chung_lu_20k),
+    "rmat-s22": (W.RMAT_S22, W.rmat_s22),
+    "rmat-s24": (W.RMAT_S24, W.rmat_s24),
+}
+
+
+def core_hash(core: np.ndarray) -> str:
+    return hashlib.sha256(np.ascontiguousarray(core, dtype="<i4").tobytes()).hexdigest()
+
+
+def main(slugs):
+    for slug in slugs:
+        name, fn = SLUGS[slug]
+        g = fn()
+        t0 = time.time()
+        core = oracle.core_numbers(g)
+        t1 = time.time()
+        om, wit, st = oracle.max_clique(g)
+        t2 = time.time()
+        assert oracle.is_clique(g, wit) and len(wit) == om
+        out = {"workload": name, "n": g.n, "m": g.m, "core_sha256": core_hash(core),
+               "max_core": int(core.max()), "omega": int(om), "witness": [int(x) for x in wit],
+               "oracle_stats": st, "oracle_core_s": round(t1 - t0, 3), "oracle_max_clique_s": round(t2 - t1, 3)}
+        with open(os.path.join(HERE, slug + ".json"), "w") as f:
+            json.dump(out, f, indent=1)
+        print(slug, om, st, round(t2 - t1, 1), flush=True)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:] or ["chung-lu-20k"])

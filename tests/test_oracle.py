@@ -1,0 +1,241 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Core numbers (Section 3): brute-force k-core definition, closed forms,
+networkx's independent routine, and the peeling certificate.
+omega (Section 1 definition; Algorithm 2): brute-force subset enumeration on
+n <= 18, closed forms, networkx's independent exact routine, planted cliques in
+sparse graphs, Fact 1's bound chain, relabelling invariance.
+Algorithm 1: returns a clique no larger than omega and no larger than K+1,
+exact on disjoint unions of cliques.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+
+def adj_sets(g):
+    return [set(g.col_idx[g.row_ptr[v]:g.row_ptr[v + 1]].tolist()) for v in range(g.n)]
+
+
+def brute_cores(g):
+    """K(v) = largest k such that v survives in the k-core, where the k-core is
+    what remains after repeatedly deleting vertices of degree < k."""
+    adj = adj_sets(g)
+    core = [0] * g.n
+    k = 0
+    while True:
+        alive = set(range(g.n))
+        changed = True
+        while changed:
+            changed = False
+            for v in list(alive):
+                if len(adj[v] & alive) < k:
+                    alive.discard(v)
+                    changed = True
+        if not alive:
+            break
+        for v in alive:
+            core[v] = k
+        k += 1
+    return np.array(core, np.int32)
+
+
+def brute_omega(g):
+    """Largest subset S with every pair adjacent, by enumerating all 2^n subsets."""
+    n = g.n
+    if n == 0:
+        return 0
+    assert n <= 18
+    masks = np.zeros(n, np.int64)
+    for v, nb in enumerate(adj_sets(g)):
+        for u in nb:
+            masks[v] |= 1 << u
+    S = np.arange(1 << n, dtype=np.int64)
+    ok = np.ones(S.shape, bool)
+    for v in range(n):
+        inS = (S >> v) & 1 == 1
+        allowed = masks[v] | (1 << v)
+        ok &= ~inS | ((S & ~allowed) == 0)
+    pop = np.zeros(S.shape, np.int64)
+    for v in range(n):
+        pop += (S >> v) & 1
+    return int(pop[ok].max())
+
+
+def small_random_graphs():
+    out = []
+    for seed in range(40):
+        n = 3 + seed % 16
+        p = [0.1, 0.3, 0.5, 0.7, 0.9][seed % 5]
+        out.append(gg.random_small(n, p, seed + 100))
+    return out
+
+
+# ------------------------------------------------------------ core numbers --
+
+@pytest.mark.parametrize("g", small_random_graphs(), ids=lambda g: g.name)
+def test_cores_match_bruteforce_definition(g):
+    assert np.array_equal(oracle.core_numbers(g), brute_cores(g))
+
+
+def test_cores_closed_forms():
+    assert np.all(oracle.core_numbers(gg.complete(9)) == 8)
+    assert np.all(oracle.core_numbers(gg.cycle(11)) == 2)
+    assert np.all(oracle.core_numbers(gg.path(7)) == 1)
+    assert np.all(oracle.core_numbers(gg.star(12)) == 1)
+    assert np.all(oracle.core_numbers(gg.empty(5)) == 0)
+    assert np.all(oracle.core_numbers(gg.petersen()) == 3)  # 3-regular, connected
+    assert np.all(oracle.core_numbers(gg.complete_bipartite(4, 7)) == 4)
+    c = oracle.core_numbers(gg.disjoint_cliques([3, 5, 2]))
+    assert c.tolist() == [2] * 3 + [4] * 5 + [1] * 2
+
+
+def test_cores_match_networkx_on_generated_graphs():
+    nx = pytest.importorskip("networkx")
+    for g in [gg.chung_lu(3000, 2.5, 8.0, 300.0, planted=9, seed=7),
+              gg.rmat(11, 8, planted=12, seed=3),
+              gg.erdos_renyi(500, 0.05, planted=10, seed=5)]:
+        G = nx.Graph()
+        G.add_nodes_from(range(g.n))
+        src = np.repeat(np.arange(g.n), g.degrees())
+        G.add_edges_from(zip(src.tolist(), g.col_idx.tolist()))
+        ref = nx.core_number(G)
+        assert np.array_equal(oracle.core_numbers(g), np.array([ref[v] for v in range(g.n)]))
+
+
+def test_core_peeling_certificate():
+    """K(v) = k iff v has >= k neighbours of core >= k and fewer than k+1
+    neighbours of core >= k+1 (both follow from the k-core definition)."""
+    g = gg.rmat(12, 16, planted=20, seed=9)
+    K = oracle.core_numbers(g)
+    src = np.repeat(np.arange(g.n), g.degrees())
+    kn = K[g.col_idx]
+    ge = np.bincount(src[kn >= K[src]], minlength=g.n)
+    gt = np.bincount(src[kn >= K[src] + 1], minlength=g.n)
+    assert np.all(ge >= K)
+    assert np.all(gt < K + 1)
+
+
+def test_core_order_is_degeneracy_order():
+    """In the returned visiting order every vertex has at most K(v) later neighbours."""
+    g = gg.chung_lu(4000, 2.2, 10.0, 500.0, planted=12, seed=4)
+    K, order = oracle.core_numbers(g, with_order=True)
+    pos = np.empty(g.n, np.int64)
+    pos[order] = np.arange(g.n)
+    src = np.repeat(np.arange(g.n), g.degrees())
+    later = np.bincount(src[pos[g.col_idx] > pos[src]], minlength=g.n)
+    assert np.all(later <= K)
+    assert np.all(np.diff(K[order]) >= 0)
+
+
+# ------------------------------------------------------------------ omega --
+
+@pytest.mark.parametrize("g", small_random_graphs(), ids=lambda g: g.name)
+def test_omega_matches_bruteforce(g):
+    om, wit, _ = oracle.max_clique(g)
+    assert om == brute_omega(g)
+    assert len(wit) == om and oracle.is_clique(g, wit)
+
+
+def test_omega_closed_forms():
+    cases = [
+        (gg.empty(0), 0), (gg.empty(1), 1), (gg.empty(6), 1),
+        (gg.complete(2), 2), (gg.complete(17), 17),
+        (gg.cycle(3), 3), (gg.cycle(4), 2), (gg.cycle(9), 2),
+        (gg.path(10), 2), (gg.star(20), 2), (gg.petersen(), 2),
+        (gg.complete_bipartite(6, 9), 2),
+        (gg.turan(20, 4), 4), (gg.turan(31, 7), 7),
+        (gg.disjoint_cliques([4, 9, 3, 9, 2]), 9),
+        (gg.mycielski(4), 2), (gg.mycielski(6), 2),
+    ]
+    for g, want in cases:
+        om, wit, _ = oracle.max_clique(g)
+        assert om == want, g.name
+        assert len(wit) == om and oracle.is_clique(g, wit)
+    om, wit, _ = oracle.max_clique(gg.empty(6))
+    assert wit.tolist() == [0] or len(wit) == 1
+
+
+def test_omega_matches_networkx_exact():
+    nx = pytest.importorskip("networkx")
+    for seed in range(6):
+        g = gg.erdos_renyi(60 + 10 * seed, [0.3, 0.5, 0.7][seed % 3], planted=0, seed=200 + seed)
+        G = nx.Graph()
+        G.add_nodes_from(range(g.n))
+        src = np.repeat(np.arange(g.n), g.degrees())
+        G.add_edges_from(zip(src.tolist(), g.col_idx.tolist()))
+        _, w = nx.max_weight_clique(G, weight=None)
+        om, wit, _ = oracle.max_clique(g)
+        assert om == w
+        assert oracle.is_clique(g, wit)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_planted_clique_in_sparse_graph(seed):
+    """Sparse G(n, p) with p*n << n has natural omega <= 4 w.h.p.; a planted
+    k >= 8 clique is then exactly omega and the planted set is the witness."""
+    k = 8 + 3 * seed
+    g = gg.erdos_renyi(2000, 4.0 / 1999, planted=k, seed=300 + seed)
+    om, wit, _ = oracle.max_clique(g)
+    assert om == k
+    assert np.array_equal(np.sort(wit), np.sort(g.planted))
+
+
+def test_fact1_bound_chain_and_witness():
+    """omega <= L(G) <= K(G)+1 <= Delta(G)+1 with L the greedy colouring in
+    degeneracy order (decreasing core number)."""
+    for g in [gg.chung_lu(5000, 2.5, 8.0, 400.0, planted=11, seed=1),
+              gg.rmat(12, 16, planted=14, seed=2), gg.turan(40, 6), gg.mycielski(5)]:
+        K, order = oracle.core_numbers(g, with_order=True)
+        L = oracle.greedy_colors(g, order[::-1].copy())
+        om, wit, st = oracle.max_clique(g)
+        H = oracle.heuristic_clique(g, K)
+        assert len(H) <= om <= L <= K.max() + 1 <= g.degrees().max() + 1
+        assert oracle.is_clique(g, wit) and oracle.is_clique(g, H)
+        assert st["max_core"] == K.max() and st["heuristic"] == len(H)
+
+
+def test_relabel_invariance():
+    g = gg.chung_lu(3000, 2.3, 12.0, 300.0, planted=10, seed=11)
+    h = gg.relabel(g, 5)
+    assert oracle.max_clique(g)[0] == oracle.max_clique(h)[0]
+    assert np.array_equal(np.sort(oracle.core_numbers(g)), np.sort(oracle.core_numbers(h)))
+
+
+# -------------------------------------------------------------- heuristic --
+
+def test_heuristic_disjoint_cliques_exact():
+    g = gg.disjoint_cliques([5, 12, 7, 12, 3])
+    for mode in (0, 1):
+        H = oracle.heuristic_clique(g, mode=mode)
+        assert len(H) == 12 and oracle.is_clique(g, H)
+    # mode 1 breaks ties by the smallest start vertex: the first 12-clique
+    assert oracle.heuristic_clique(g, mode=1).tolist() == list(range(5, 17))
+
+
+@pytest.mark.parametrize("g", small_random_graphs()[::3], ids=lambda g: g.name)
+def test_heuristic_valid_and_bounded(g):
+    K = oracle.core_numbers(g)
+    om = brute_omega(g)
+    for mode in (0, 1):
+        H = oracle.heuristic_clique(g, K, mode)
+        assert oracle.is_clique(g, H)
+        assert len(H) <= om
+        assert len(H) <= (K.max() + 1 if g.n else 0)
+        if g.n:
+            assert len(H) >= 1
+
+
+def test_heuristic_mode1_is_max_over_start_vertices():
+    """Mode 1 is the largest greedy clique over all start vertices: it is at
+    least the greedy clique grown from any single vertex, here checked through
+    the planted clique (every planted vertex's greedy run stays inside it when
+    the planted vertices dominate the core order)."""
+    g = gg.erdos_renyi(400, 0.02, planted=15, seed=42)
+    H = oracle.heuristic_clique(g, mode=1)
+    assert len(H) == 15
+    assert np.array_equal(H, np.sort(g.planted))
