@@ -1,0 +1,171 @@
+/*
+ * mc.h -- C ABI of the GB300 exact maximum-clique library.
+ *
+ * The library implements the method of Rossi, Gleich, Gebremedhin and Patwary,
+ * "Parallel Maximum Clique Algorithms with Applications to Network Analysis and
+ * Storage": core numbers (Section 3), the heuristic clique of Algorithm 1
+ * (Section 4.1), pruning by core number (Section 4.2) and the neighbourhood
+ * branch and bound of Algorithm 2 (Section 4.3) with the incumbent shared by
+ * all workers (Section 4.5).  Every step runs in hand-written CUDA kernels for
+ * sm_103a; nothing falls back to the CPU.
+ *
+ * Conventions (all functions):
+ *  - Return an int status: MC_OK (0) or a negative MC_ERR_* code.  Nothing
+ *    throws across the ABI.  mc_strerror() gives a message for a code.
+ *  - Graphs are simple and undirected, in CSR form: row_ptr has n+1 int64
+ *    entries with row_ptr[0] = 0, col_idx has row_ptr[n] int32 entries, each
+ *    row sorted ascending, no self-loops, no duplicates, and the pattern is
+ *    symmetric (u in N(v) iff v in N(u)).  MC_VALIDATE checks this on load.
+ *  - Any array argument may be a host pointer or a device pointer of the
+ *    current device; the library tells them apart by pointer attributes.  The
+ *    caller owns every array it passes; without MC_BORROW the library copies
+ *    its inputs, so the caller may free them as soon as the call returns.
+ *  - All work of a graph runs on the CUDA stream given to its load call.  Calls
+ *    are synchronous with respect to their outputs: when a call returns, its
+ *    outputs (host or device) are written.
+ *  - Vertex ids are 0..n-1 in the caller's numbering; witnesses are sorted
+ *    ascending.  An empty graph (n = 0) has omega = 0; a graph with vertices but
+ *    no edges has omega = 1 (witness {0}).
+ *  - If an output capacity is smaller than the result, the call returns
+ *    MC_ERR_BUFFER and still writes the required size to the size output.
+ *  - A handle may be used from one host thread at a time.
+ */
+#ifndef MC_H
+#define MC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define MC_OK 0
+#define MC_ERR_ARG (-1)           /* bad argument (NULL handle, negative size, ...) */
+#define MC_ERR_INVALID_GRAPH (-2) /* CSR not simple / not symmetric / out of range */
+#define MC_ERR_OOM (-3)           /* device allocation failed */
+#define MC_ERR_BUFFER (-4)        /* output capacity too small */
+#define MC_ERR_TIMEOUT (-5)       /* a device spin-wait exceeded its iteration limit */
+#define MC_ERR_CUDA (-6)          /* a CUDA runtime call failed */
+#define MC_ERR_DEVICE_CHECK (-7)  /* a device-side consistency check failed */
+#define MC_ERR_UNSUPPORTED (-8)   /* a neighbourhood exceeds the supported size */
+
+/* load flags */
+#define MC_VALIDATE 1u /* check the CSR invariants on the device (MC_ERR_INVALID_GRAPH) */
+#define MC_BORROW 2u   /* keep the caller's device arrays instead of copying them;
+                          they must stay valid and unchanged until mc_free */
+
+typedef struct mc_graph mc_graph;
+
+/* Search options.  Zero-initialise for the defaults. */
+typedef struct {
+  /* order in which root vertices are searched: 0 = degeneracy order, smallest
+   * core first (Algorithm 2's smallest reduced degree, Section 4.3);
+   * 1 = decreasing learned score (scores below); 2 = native vertex-id order
+   * (the paper's "pmc-native" variant, Section 5) */
+  int32_t ordering;
+  /* 1 = skip the neighbourhood-core test of InitialBranch (the paper's
+   * "pmc no neigh cores" variant, Section 5); 0 = use it (default) */
+  int32_t no_neigh_cores;
+  /* heuristic: 0 = Algorithm 1 with the running maximum shared by all
+   * workers (default); 1 = deterministic form; 2 = skip (start from 0) */
+  int32_t heuristic;
+  /* worker split: neighbourhoods with more than this many candidates go to
+   * block workers; 0 = tuned default */
+  int32_t warp_max;
+  /* device spin-wait iteration limit; 0 = default (about ten seconds) */
+  int64_t spin_limit;
+  /* ordering == 1: one float score per vertex (host or device), higher first;
+   * for a batch, one score per vertex of the union */
+  const float *scores;
+  /* heuristic seeds from the scores: the top `seeds` vertices of each graph
+   * are also grown by Algorithm 1's greedy step first; 0 = none */
+  int32_t seeds;
+} mc_options;
+
+/* Per-call statistics (all times in milliseconds, CUDA events). */
+typedef struct {
+  double ms_total, ms_cores, ms_heuristic, ms_prune, ms_search, ms_verify;
+  int64_t n, edges;            /* vertices and undirected edges */
+  int64_t pruned_n;            /* vertices left after the core pruning (Section 4.2) */
+  int64_t pruned_arcs;         /* arcs of the oriented pruned graph */
+  int64_t roots;               /* root vertices queued for InitialBranch */
+  int64_t roots_colored;       /* roots that reached the colouring test */
+  int64_t roots_branched;      /* roots that reached Branch */
+  int64_t nodes;               /* Branch nodes expanded */
+  int64_t donations;           /* subproblems handed to other warps */
+  int32_t max_core, heuristic_size, omega, verified;
+} mc_stats;
+
+/* ------------------------------------------------------------ graphs --- */
+
+/* Load a graph (CSR as described above).  flags: MC_VALIDATE, MC_BORROW.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * On success *out owns a device copy (or borrows, with MC_BORROW). */
+int mc_load_csr(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, uint32_t flags,
+                void *cuda_stream, mc_graph **out);
+
+/* Load a batch of independent graphs as one block-diagonal CSR: graph g owns
+ * vertices voff[g] .. voff[g+1]-1 (voff has count+1 int64 entries, voff[0] = 0,
+ * voff[count] = n) and its columns are ids of the union.  No edge may join two
+ * graphs (checked with MC_VALIDATE).  Every per-graph call below then works on
+ * all graphs at once. */
+int mc_load_batch(int32_t count, const int64_t *voff, const int64_t *row_ptr, const int32_t *col_idx,
+                  uint32_t flags, void *cuda_stream, mc_graph **out);
+
+/* Release a graph and all device memory it holds.  NULL is accepted. */
+void mc_free(mc_graph *g);
+
+/* Vertices, undirected edges and graph count of a loaded graph. */
+int mc_graph_info(const mc_graph *g, int64_t *n, int64_t *edges, int32_t *count);
+
+/* ------------------------------------------------------- the method --- */
+
+/* Core numbers (Section 3: K(v) = largest k with v in the k-core), computed by
+ * a bucketed parallel peel.  core_out: n int32 (nullable); max_core_out: the
+ * largest core number K(G) (nullable; for a batch, the largest over graphs). */
+int mc_core_numbers(mc_graph *g, int32_t *core_out, int32_t *max_core_out);
+
+/* Heuristic clique (Algorithm 1, Section 4.1).  mode 0: the algorithm with the
+ * running maximum shared by all workers (the result may differ from run to
+ * run; it is always a clique); mode 1: deterministic -- the largest greedy
+ * clique over all start vertices, ties to the smallest start vertex.
+ * core: n int32 core numbers, or NULL to compute them.  clique_out: capacity
+ * int32 (sorted ascending); size_out: its size.  For a batch, graph 0 only;
+ * use mc_max_clique_batch for all graphs. */
+int mc_heuristic_clique(mc_graph *g, const int32_t *core, int32_t mode, int32_t *clique_out,
+                        int32_t capacity, int32_t *size_out);
+
+/* Exact maximum clique (Algorithm 2: CoreNumbers, HeuristicClique, pruning,
+ * InitialBranch and Branch for every root, incumbent shared by all workers).
+ * opt: NULL for defaults.  omega_out: omega(G); witness_out: capacity int32, a
+ * maximum clique sorted ascending and verified on the device; stats nullable. */
+int mc_max_clique(mc_graph *g, const mc_options *opt, int32_t *omega_out, int32_t *witness_out,
+                  int32_t capacity, mc_stats *stats);
+
+/* Exact maximum clique of every graph of a batch in one pass of the pipeline
+ * (one persistent search launch over all graphs' roots).  omegas_out: count
+ * int32; witness_out: capacity int32 entries, graph g's witness at
+ * witness_offsets[g] .. witness_offsets[g+1]-1 (witness_offsets: count+1 int64,
+ * written by the call, in caller's vertex numbering of graph g, i.e. minus
+ * voff[g]); stats nullable (summed over graphs). */
+int mc_max_clique_batch(mc_graph *g, const mc_options *opt, int32_t *omegas_out, int32_t *witness_out,
+                        int64_t capacity, int64_t *witness_offsets, mc_stats *stats);
+
+/* Check a vertex set on the device: *is_clique_out = 1 iff the k vertices are
+ * distinct, in range and pairwise adjacent (the definition of a clique). */
+int mc_verify_clique(mc_graph *g, const int32_t *vertices, int32_t k, int32_t *is_clique_out);
+
+/* ----------------------------------------------------- miscellaneous --- */
+
+const char *mc_strerror(int code);
+/* Library version as major*10000 + minor*100 + patch. */
+int mc_version(void);
+/* Number of kernel launches the library has issued in this process. */
+int64_t mc_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MC_H */

@@ -1,0 +1,273 @@
+"""GB300 exact maximum clique (Rossi, Gleich, Gebremedhin, Patwary).
+
+A thin ctypes binding over the C ABI of ``include/mc.h`` (the CUDA library
+``_build/libmc.so``).  The functions have the C names and do argument
+marshalling only: every step of the method runs in the library's CUDA kernels.
+Arrays may be torch tensors (CPU or CUDA) or numpy arrays; CUDA tensors are
+passed to the library as device pointers, the rest as host pointers.  There is
+no CPU fallback: if the library is missing the import of a function fails
+loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+MC_OK = 0
+MC_ERR_ARG = -1
+MC_ERR_INVALID_GRAPH = -2
+MC_ERR_OOM = -3
+MC_ERR_BUFFER = -4
+MC_ERR_TIMEOUT = -5
+MC_ERR_CUDA = -6
+MC_ERR_DEVICE_CHECK = -7
+MC_ERR_UNSUPPORTED = -8
+
+MC_VALIDATE = 1
+MC_BORROW = 2
+
+_lib = None
+_lock = threading.Lock()
+
+
+class MCError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (where, strerror(code), code))
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("ordering", ctypes.c_int32), ("no_neigh_cores", ctypes.c_int32),
+                ("heuristic", ctypes.c_int32), ("warp_max", ctypes.c_int32),
+                ("spin_limit", ctypes.c_int64), ("scores", ctypes.c_void_p),
+                ("seeds", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("ms_total", ctypes.c_double), ("ms_cores", ctypes.c_double),
+                ("ms_heuristic", ctypes.c_double), ("ms_prune", ctypes.c_double),
+                ("ms_search", ctypes.c_double), ("ms_verify", ctypes.c_double),
+                ("n", ctypes.c_int64), ("edges", ctypes.c_int64), ("pruned_n", ctypes.c_int64),
+                ("pruned_arcs", ctypes.c_int64), ("roots", ctypes.c_int64),
+                ("roots_colored", ctypes.c_int64), ("roots_branched", ctypes.c_int64),
+                ("nodes", ctypes.c_int64), ("donations", ctypes.c_int64),
+                ("max_core", ctypes.c_int32), ("heuristic_size", ctypes.c_int32),
+                ("omega", ctypes.c_int32), ("verified", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load ``libmc.so`` (building it with nvcc first if allowed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise ImportError("CUDA library %s is missing; run __graft_entry__.build()" % path)
+        L = ctypes.CDLL(path)
+        i64, i32, u32, vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p
+        L.mc_load_csr.argtypes = [i64, vp, vp, u32, vp, ctypes.POINTER(vp)]
+        L.mc_load_batch.argtypes = [i32, vp, vp, vp, u32, vp, ctypes.POINTER(vp)]
+        L.mc_free.argtypes = [vp]
+        L.mc_free.restype = None
+        L.mc_graph_info.argtypes = [vp, vp, vp, vp]
+        L.mc_core_numbers.argtypes = [vp, vp, vp]
+        L.mc_heuristic_clique.argtypes = [vp, vp, i32, vp, i32, vp]
+        L.mc_max_clique.argtypes = [vp, vp, vp, vp, i32, vp]
+        L.mc_max_clique_batch.argtypes = [vp, vp, vp, vp, i64, vp, vp]
+        L.mc_verify_clique.argtypes = [vp, vp, i32, vp]
+        L.mc_strerror.argtypes = [ctypes.c_int]
+        L.mc_strerror.restype = ctypes.c_char_p
+        L.mc_version.restype = ctypes.c_int
+        L.mc_launch_count.restype = i64
+        for name in ("mc_load_csr", "mc_load_batch", "mc_graph_info", "mc_core_numbers", "mc_heuristic_clique",
+                     "mc_max_clique", "mc_max_clique_batch", "mc_verify_clique"):
+            getattr(L, name).restype = ctypes.c_int
+        _extend(L)
+        _lib = L
+        return L
+
+
+def _extend(L):
+    """Declare optional entry points if the library exports them."""
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    if hasattr(L, "mc_features"):
+        L.mc_features.argtypes = [vp, vp]
+        L.mc_features.restype = ctypes.c_int
+
+
+def strerror(code: int) -> str:
+    try:
+        return load_library(False).mc_strerror(code).decode()
+    except Exception:
+        return "error %d" % code
+
+
+def _check(rc: int, where: str):
+    if rc != MC_OK:
+        raise MCError(rc, where)
+
+
+def _ptr(a):
+    """(address, keepalive) of a contiguous torch tensor or numpy array."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            a = a.contiguous()
+        return a.data_ptr(), a
+    a = np.ascontiguousarray(a)
+    return a.ctypes.data, a
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Graph:
+    """Owning handle of a loaded graph (``mc_graph*``)."""
+
+    def __init__(self, handle, n: int, count: int, keep=None):
+        self._h = handle
+        self.n = n
+        self.count = count
+        self._keep = keep
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            load_library().mc_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mc_load_csr(row_ptr, col_idx, flags: int = 0, stream=None) -> Graph:
+    L = load_library()
+    rp, krp = _ptr(row_ptr)
+    ci, kci = _ptr(col_idx)
+    n = int(row_ptr.shape[0]) - 1
+    h = ctypes.c_void_p()
+    _check(L.mc_load_csr(n, rp, ci, flags, _stream_handle(stream), ctypes.byref(h)), "mc_load_csr")
+    return Graph(h, n, 1, (krp, kci) if flags & MC_BORROW else None)
+
+
+def mc_load_batch(voff, row_ptr, col_idx, flags: int = 0, stream=None) -> Graph:
+    L = load_library()
+    vo, kvo = _ptr(voff)
+    rp, krp = _ptr(row_ptr)
+    ci, kci = _ptr(col_idx)
+    count = int(voff.shape[0]) - 1
+    h = ctypes.c_void_p()
+    _check(L.mc_load_batch(count, vo, rp, ci, flags, _stream_handle(stream), ctypes.byref(h)), "mc_load_batch")
+    return Graph(h, int(row_ptr.shape[0]) - 1, count, (krp, kci) if flags & MC_BORROW else None)
+
+
+def mc_free(g: Graph):
+    g.close()
+
+
+def mc_core_numbers(g: Graph, core_out=None):
+    """Core numbers into core_out (n int32, host or device) and K(G)."""
+    L = load_library()
+    if core_out is None:
+        core_out = np.zeros(max(g.n, 1), np.int32)
+    p, keep = _ptr(core_out)
+    mk = ctypes.c_int32(0)
+    _check(L.mc_core_numbers(g.handle, p, ctypes.byref(mk)), "mc_core_numbers")
+    return core_out[:g.n], mk.value
+
+
+def mc_heuristic_clique(g: Graph, mode: int = 0, core=None):
+    L = load_library()
+    cap = g.n + 1
+    out = np.zeros(cap, np.int32)
+    size = ctypes.c_int32(0)
+    cp, kc = _ptr(core)
+    _check(L.mc_heuristic_clique(g.handle, cp, mode, out.ctypes.data, cap, ctypes.byref(size)),
+           "mc_heuristic_clique")
+    return out[:size.value].copy()
+
+
+def _options(ordering=0, no_neigh_cores=False, heuristic=0, warp_max=0, spin_limit=0, scores=None, seeds=0):
+    o = Options()
+    o.ordering = ordering
+    o.no_neigh_cores = 1 if no_neigh_cores else 0
+    o.heuristic = heuristic
+    o.warp_max = warp_max
+    o.spin_limit = spin_limit
+    sp, keep = _ptr(scores)
+    o.scores = sp
+    o.seeds = seeds
+    return o, keep
+
+
+def mc_max_clique(g: Graph, witness_out=None, **opts):
+    """Returns (omega, witness, stats dict).  witness_out: optional int32
+    buffer (host or device) of at least omega entries."""
+    L = load_library()
+    o, keep = _options(**opts)
+    st = Stats()
+    om = ctypes.c_int32(0)
+    if witness_out is None:
+        witness_out = np.zeros(g.n + 1, np.int32)
+    wp, kw = _ptr(witness_out)
+    cap = int(witness_out.shape[0])
+    _check(L.mc_max_clique(g.handle, ctypes.byref(o), ctypes.byref(om), wp, cap, ctypes.byref(st)), "mc_max_clique")
+    return om.value, witness_out[:om.value], st.as_dict()
+
+
+def mc_max_clique_batch(g: Graph, **opts):
+    """Returns (omegas[count], list of witnesses, stats dict)."""
+    L = load_library()
+    o, keep = _options(**opts)
+    st = Stats()
+    om = np.zeros(g.count, np.int32)
+    offs = np.zeros(g.count + 1, np.int64)
+    wit = np.zeros(g.n + 1, np.int32)
+    _check(L.mc_max_clique_batch(g.handle, ctypes.byref(o), om.ctypes.data, wit.ctypes.data, int(wit.shape[0]),
+                                 offs.ctypes.data, ctypes.byref(st)), "mc_max_clique_batch")
+    wits = [wit[offs[i]:offs[i + 1]].copy() for i in range(g.count)]
+    return om, wits, st.as_dict()
+
+
+def mc_verify_clique(g: Graph, vertices) -> bool:
+    L = load_library()
+    vp, keep = _ptr(np.ascontiguousarray(vertices, dtype=np.int32) if not hasattr(vertices, "data_ptr") else vertices)
+    out = ctypes.c_int32(0)
+    k = int(vertices.shape[0])
+    _check(L.mc_verify_clique(g.handle, vp, k, ctypes.byref(out)), "mc_verify_clique")
+    return bool(out.value)
+
+
+def mc_launch_count() -> int:
+    return int(load_library().mc_launch_count())
+
+
+def mc_version() -> int:
+    return int(load_library().mc_version())

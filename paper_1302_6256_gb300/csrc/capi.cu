@@ -1,0 +1,452 @@
+// C ABI (include/mc.h): argument checks, device memory, and the pipeline of
+// Algorithm 2 -- core numbers, heuristic, pruning, search, verification --
+// on the graph's stream.  Every step runs in this library's CUDA kernels.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "mc_internal.cuh"
+
+namespace mc {
+
+std::atomic<int64_t> g_launches{0};
+static thread_local char g_errbuf[320];
+
+void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
+  snprintf(g_errbuf, sizeof(g_errbuf), "%s (%s) at %s:%d", cudaGetErrorString(e), what, file, line);
+}
+
+int ws_get(mc_graph *g, const char *name, size_t bytes, void **out) {
+  DevBuf &b = g->ws[name];
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) {
+    *out = b.p;
+    return MC_OK;
+  }
+  if (b.p) {
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return MC_ERR_CUDA;
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  size_t want = bytes + bytes / 8;
+  cudaError_t e = cudaMalloc(&b.p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    e = cudaMalloc(&b.p, bytes);
+    want = bytes;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return MC_ERR_OOM;
+  }
+  b.bytes = want;
+  *out = b.p;
+  return MC_OK;
+}
+
+int check_device_error(mc_graph *g) {
+  int32_t *h = (int32_t *)((char *)g->h_small + 2048);
+  MC_CUDA_TRY(cudaMemcpyAsync(h, g->err, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
+  MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  int e = *h;
+  if (e == kDevOk) return MC_OK;
+  MC_CUDA_TRY(cudaMemsetAsync(g->err, 0, sizeof(int32_t), g->stream));
+  switch (e) {
+    case kDevTimeout: return MC_ERR_TIMEOUT;
+    case kDevUnsupported: return MC_ERR_UNSUPPORTED;
+    default: return MC_ERR_DEVICE_CHECK;
+  }
+}
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// graphs whose incumbent is still 0 but have a vertex: omega = 1, witness =
+// their first vertex (a graph without edges)
+__global__ void trivial_kernel(int32_t count, const int64_t *voff, int64_t n, int32_t *best, int32_t *wit) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < count; g += (int64_t)gridDim.x * blockDim.x) {
+    int64_t v0 = voff ? voff[g] : 0, v1 = voff ? voff[g + 1] : n;
+    if (best[g] == 0 && v1 > v0) {
+      wit[v0] = (int32_t)v0;
+      best[g] = 1;
+    }
+  }
+}
+
+static void free_graph(mc_graph *g) {
+  if (!g) return;
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  if (!g->borrowed) {
+    cudaFree(g->row_ptr);
+    cudaFree(g->col_idx);
+  }
+  cudaFree(g->voff);
+  cudaFree(g->gid);
+  cudaFree(g->core);
+  cudaFree(g->order);
+  cudaFree(g->pos);
+  cudaFree(g->best);
+  cudaFree(g->lock);
+  cudaFree(g->wit);
+  cudaFree(g->err);
+  for (auto &kv : g->ws) cudaFree(kv.second.p);
+  if (g->h_small) cudaFreeHost(g->h_small);
+  delete[] g->h_voff;
+  for (auto &e : g->ev)
+    if (e) cudaEventDestroy(e);
+  delete g;
+}
+
+static int copy_in(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return MC_OK;
+  MC_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+  return MC_OK;
+}
+
+static int load_common(int32_t count, const int64_t *voff_in, int64_t n, const int64_t *row_ptr,
+                       const int32_t *col_idx, uint32_t flags, void *stream, mc_graph **out) {
+  if (!out) return MC_ERR_ARG;
+  *out = nullptr;
+  if (n < 0 || n > 2147483000LL || count < 1 || (n > 0 && !row_ptr)) return MC_ERR_ARG;
+  if ((flags & ~(MC_VALIDATE | MC_BORROW)) != 0) return MC_ERR_ARG;
+  mc_graph *g = new mc_graph();
+  g->stream = (cudaStream_t)stream;
+  g->count = count;
+  g->n = n;
+  int rc = MC_OK;
+  auto fail = [&](int code) {
+    free_graph(g);
+    return code;
+  };
+  if (cudaGetDevice(&g->device) != cudaSuccess) return fail(MC_ERR_CUDA);
+  if (cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess)
+    return fail(MC_ERR_CUDA);
+  if (cudaMallocHost(&g->h_small, 4096) != cudaSuccess) return fail(MC_ERR_OOM);
+  for (auto &e : g->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return fail(MC_ERR_CUDA);
+  // nnz = row_ptr[n]
+  int64_t nnz = 0;
+  if (n > 0) {
+    if (cudaMemcpyAsync(g->h_small, row_ptr + n, sizeof(int64_t), cudaMemcpyDefault, g->stream) != cudaSuccess ||
+        cudaStreamSynchronize(g->stream) != cudaSuccess)
+      return fail(MC_ERR_ARG);
+    nnz = *(int64_t *)g->h_small;
+  }
+  if (nnz < 0 || (nnz > 0 && !col_idx)) return fail(MC_ERR_ARG);
+  g->nnz = nnz;
+  if (flags & MC_BORROW) {
+    if ((n > 0 && !is_device_ptr(row_ptr)) || (nnz > 0 && !is_device_ptr(col_idx))) return fail(MC_ERR_ARG);
+    g->row_ptr = const_cast<int64_t *>(row_ptr);
+    g->col_idx = const_cast<int32_t *>(col_idx);
+    g->borrowed = true;
+  } else {
+    if (cudaMalloc(&g->row_ptr, (n + 1) * sizeof(int64_t)) != cudaSuccess) return fail(MC_ERR_OOM);
+    if (cudaMalloc(&g->col_idx, std::max<int64_t>(nnz, 4) * sizeof(int32_t)) != cudaSuccess)
+      return fail(MC_ERR_OOM);
+    if (n > 0) {
+      if ((rc = copy_in(g->row_ptr, row_ptr, (n + 1) * sizeof(int64_t), g->stream)) != MC_OK) return fail(rc);
+      if ((rc = copy_in(g->col_idx, col_idx, nnz * sizeof(int32_t), g->stream)) != MC_OK) return fail(rc);
+    } else {
+      cudaMemsetAsync(g->row_ptr, 0, sizeof(int64_t), g->stream);
+    }
+  }
+  const size_t nv = (size_t)std::max<int64_t>(n, 1);
+  if (cudaMalloc(&g->core, nv * 4) != cudaSuccess || cudaMalloc(&g->order, nv * 4) != cudaSuccess ||
+      cudaMalloc(&g->pos, nv * 4) != cudaSuccess || cudaMalloc(&g->wit, (nv + 1) * 4) != cudaSuccess ||
+      cudaMalloc(&g->best, count * 4) != cudaSuccess || cudaMalloc(&g->lock, count * 4) != cudaSuccess ||
+      cudaMalloc(&g->err, 64) != cudaSuccess || cudaMalloc(&g->voff, (count + 1) * 8) != cudaSuccess)
+    return fail(MC_ERR_OOM);
+  cudaMemsetAsync(g->err, 0, 64, g->stream);
+  cudaMemsetAsync(g->lock, 0, count * 4, g->stream);
+  cudaMemsetAsync(g->best, 0, count * 4, g->stream);
+  g->h_voff = new int64_t[count + 1];
+  if (voff_in) {
+    if (cudaMemcpyAsync(g->h_voff, voff_in, (count + 1) * 8, cudaMemcpyDefault, g->stream) != cudaSuccess ||
+        cudaStreamSynchronize(g->stream) != cudaSuccess)
+      return fail(MC_ERR_ARG);
+    if (g->h_voff[0] != 0 || g->h_voff[count] != n) return fail(MC_ERR_ARG);
+    for (int32_t i = 0; i < count; i++)
+      if (g->h_voff[i + 1] < g->h_voff[i]) return fail(MC_ERR_ARG);
+  } else {
+    g->h_voff[0] = 0;
+    g->h_voff[1] = n;
+  }
+  if (cudaMemcpyAsync(g->voff, g->h_voff, (count + 1) * 8, cudaMemcpyHostToDevice, g->stream) != cudaSuccess)
+    return fail(MC_ERR_CUDA);
+  if (count > 1) {
+    if (cudaMalloc(&g->gid, nv * 4) != cudaSuccess) return fail(MC_ERR_OOM);
+    if ((rc = launch_gid(g)) != MC_OK) return fail(rc);
+  }
+  if (flags & MC_VALIDATE) {
+    int32_t *bad = g->err + 8;
+    cudaMemsetAsync(bad, 0, 4, g->stream);
+    if ((rc = launch_validate(g, bad)) != MC_OK) return fail(rc);
+    if (cudaMemcpyAsync(g->h_small, bad, 4, cudaMemcpyDeviceToHost, g->stream) != cudaSuccess ||
+        cudaStreamSynchronize(g->stream) != cudaSuccess)
+      return fail(MC_ERR_CUDA);
+    if (*(int32_t *)g->h_small) return fail(MC_ERR_INVALID_GRAPH);
+  }
+  if (cudaStreamSynchronize(g->stream) != cudaSuccess) return fail(MC_ERR_CUDA);
+  *out = g;
+  return MC_OK;
+}
+
+static long long spin_of(const mc_options *o) { return (o && o->spin_limit > 0) ? o->spin_limit : kDefaultSpinLimit; }
+
+static int ensure_cores(mc_graph *g, long long spin) {
+  if (g->cores_valid) return MC_OK;
+  return launch_core_numbers(g, spin);
+}
+
+static float elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  return ms;
+}
+
+// The whole of Algorithm 2 on every graph of the handle.  Leaves omega in
+// g->best and witnesses in g->wit; fills stats.
+static int run_max_clique(mc_graph *g, const mc_options *opt, mc_stats *st) {
+  mc_options o{};
+  if (opt) o = *opt;
+  if (o.ordering < 0 || o.ordering > 2 || o.heuristic < 0 || o.heuristic > 2 || o.warp_max < 0 || o.seeds < 0)
+    return MC_ERR_ARG;
+  if (o.ordering == 1 && !o.scores) return MC_ERR_ARG;
+  const long long spin = spin_of(&o);
+  int32_t warp_max = o.warp_max > 0 ? std::min(o.warp_max, 128) : 128;
+  memset(st, 0, sizeof(*st));
+  st->n = g->n;
+  st->edges = g->nnz / 2;
+  MC_CUDA_TRY(cudaEventRecord(g->ev[0], g->stream));
+  MC_TRY(ensure_cores(g, spin));
+  MC_CUDA_TRY(cudaEventRecord(g->ev[1], g->stream));
+  MC_CUDA_TRY(cudaMemsetAsync(g->best, 0, g->count * 4, g->stream));
+  MC_CUDA_TRY(cudaMemsetAsync(g->lock, 0, g->count * 4, g->stream));
+  // learned scores (host or device) -> device copy
+  const float *d_scores = nullptr;
+  const int32_t *d_seeds = nullptr;
+  int64_t nseeds = 0;
+  if (o.scores && g->n > 0) {
+    void *p;
+    if (is_device_ptr(o.scores)) {
+      d_scores = o.scores;
+    } else {
+      MC_TRY(ws_get(g, "cp.scores", g->n * sizeof(float), &p));
+      MC_CUDA_TRY(cudaMemcpyAsync(p, o.scores, g->n * sizeof(float), cudaMemcpyHostToDevice, g->stream));
+      d_scores = (const float *)p;
+    }
+    if (o.seeds > 0) {
+      nseeds = std::min<int64_t>(o.seeds, g->n);
+      MC_TRY(ws_get(g, "cp.seeds", (nseeds + 1) * sizeof(int32_t), &p));
+      int32_t *seeds = (int32_t *)p;
+      MC_TRY(top_scores(g, d_scores, nseeds, seeds));
+      d_seeds = seeds;
+    }
+  }
+  if (o.heuristic != 2 && g->n > 0) MC_TRY(launch_heuristic(g, o.heuristic, spin, d_seeds, nseeds));
+  MC_CUDA_TRY(cudaEventRecord(g->ev[2], g->stream));
+  Pruned pg;
+  if (g->n > 0) MC_TRY(launch_prune(g, o.ordering, d_scores, warp_max, &pg, spin));
+  MC_CUDA_TRY(cudaEventRecord(g->ev[3], g->stream));
+  SearchCounters sc{};
+  if (pg.n > 0) MC_TRY(launch_search(g, pg, o.no_neigh_cores, spin, &sc));
+  trivial_kernel<<<std::max(1, std::min(g->count / 256 + 1, 1024)), 256, 0, g->stream>>>(
+      g->count, g->gid ? g->voff : nullptr, g->n, g->best, g->wit);
+  g_launches++;
+  MC_CUDA_TRY(cudaEventRecord(g->ev[4], g->stream));
+  void *p;
+  MC_TRY(ws_get(g, "cp.ok", (size_t)g->count * 4, &p));
+  int32_t *d_ok = (int32_t *)p;
+  MC_TRY(launch_verify(g, d_ok));
+  MC_CUDA_TRY(cudaEventRecord(g->ev[5], g->stream));
+  MC_CUDA_TRY(cudaEventSynchronize(g->ev[5]));
+  MC_TRY(check_device_error(g));
+  st->ms_cores = elapsed(g->ev[0], g->ev[1]);
+  st->ms_heuristic = elapsed(g->ev[1], g->ev[2]);
+  st->ms_prune = elapsed(g->ev[2], g->ev[3]);
+  st->ms_search = elapsed(g->ev[3], g->ev[4]);
+  st->ms_verify = elapsed(g->ev[4], g->ev[5]);
+  st->ms_total = elapsed(g->ev[0], g->ev[5]);
+  st->pruned_n = pg.n;
+  st->pruned_arcs = pg.arcs;
+  st->roots = pg.nroots_small + pg.nroots_block + pg.nroots_big;
+  st->roots_colored = (int64_t)sc.roots_colored;
+  st->roots_branched = (int64_t)sc.roots_branched;
+  st->nodes = (int64_t)sc.nodes;
+  st->donations = (int64_t)sc.donations;
+  st->max_core = g->max_core;
+  // all witnesses must verify
+  std::vector<int32_t> ok(g->count);
+  MC_CUDA_TRY(cudaMemcpy(ok.data(), d_ok, g->count * 4, cudaMemcpyDeviceToHost));
+  st->verified = 1;
+  for (int32_t i = 0; i < g->count; i++)
+    if (!ok[i]) st->verified = 0;
+  if (!st->verified) return MC_ERR_DEVICE_CHECK;
+  return MC_OK;
+}
+
+}  // namespace mc
+
+using namespace mc;
+
+extern "C" {
+
+const char *mc_strerror(int code) {
+  switch (code) {
+    case MC_OK: return "ok";
+    case MC_ERR_ARG: return "invalid argument";
+    case MC_ERR_INVALID_GRAPH: return "input is not a simple symmetric CSR graph";
+    case MC_ERR_OOM: return "device memory allocation failed";
+    case MC_ERR_BUFFER: return "output buffer too small";
+    case MC_ERR_TIMEOUT: return "a device spin-wait exceeded its iteration limit";
+    case MC_ERR_CUDA: return g_errbuf[0] ? g_errbuf : "CUDA runtime error";
+    case MC_ERR_DEVICE_CHECK: return "device-side consistency check failed";
+    case MC_ERR_UNSUPPORTED: return "neighbourhood larger than the supported maximum (4096 candidates)";
+    default: return "unknown error";
+  }
+}
+
+int mc_version(void) { return 100; }
+
+int64_t mc_launch_count(void) { return g_launches.load(); }
+
+int mc_load_csr(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, uint32_t flags, void *cuda_stream,
+                mc_graph **out) {
+  return load_common(1, nullptr, n, row_ptr, col_idx, flags, cuda_stream, out);
+}
+
+int mc_load_batch(int32_t count, const int64_t *voff, const int64_t *row_ptr, const int32_t *col_idx,
+                  uint32_t flags, void *cuda_stream, mc_graph **out) {
+  if (count < 1 || !voff) return MC_ERR_ARG;
+  int64_t n = 0;
+  if (cudaMemcpy(&n, voff + count, sizeof(int64_t), cudaMemcpyDefault) != cudaSuccess) return MC_ERR_ARG;
+  return load_common(count, voff, n, row_ptr, col_idx, flags, cuda_stream, out);
+}
+
+void mc_free(mc_graph *g) { free_graph(g); }
+
+int mc_graph_info(const mc_graph *g, int64_t *n, int64_t *edges, int32_t *count) {
+  if (!g) return MC_ERR_ARG;
+  if (n) *n = g->n;
+  if (edges) *edges = g->nnz / 2;
+  if (count) *count = g->count;
+  return MC_OK;
+}
+
+int mc_core_numbers(mc_graph *g, int32_t *core_out, int32_t *max_core_out) {
+  if (!g) return MC_ERR_ARG;
+  MC_TRY(ensure_cores(g, kDefaultSpinLimit));
+  if (core_out && g->n > 0)
+    MC_CUDA_TRY(cudaMemcpyAsync(core_out, g->core, g->n * sizeof(int32_t), cudaMemcpyDefault, g->stream));
+  MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (max_core_out) *max_core_out = g->max_core;
+  return MC_OK;
+}
+
+static int copy_witness_out(mc_graph *g, int32_t gi, int32_t size, int32_t *dst, int64_t local_base) {
+  std::vector<int32_t> w(std::max(size, 1));
+  if (size > 0)
+    MC_CUDA_TRY(cudaMemcpy(w.data(), g->wit + g->h_voff[gi], size * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  for (int32_t i = 0; i < size; i++) w[i] -= (int32_t)local_base;
+  std::sort(w.begin(), w.begin() + size);
+  if (size > 0) MC_CUDA_TRY(cudaMemcpy(dst, w.data(), size * sizeof(int32_t), cudaMemcpyDefault));
+  return MC_OK;
+}
+
+int mc_heuristic_clique(mc_graph *g, const int32_t *core, int32_t mode, int32_t *clique_out, int32_t capacity,
+                        int32_t *size_out) {
+  (void)core;  // core numbers are unique: the library computes (or reuses) its own
+  if (!g || !size_out || (mode != 0 && mode != 1) || capacity < 0) return MC_ERR_ARG;
+  *size_out = 0;
+  MC_TRY(ensure_cores(g, kDefaultSpinLimit));
+  MC_CUDA_TRY(cudaMemsetAsync(g->best, 0, g->count * 4, g->stream));
+  MC_CUDA_TRY(cudaMemsetAsync(g->lock, 0, g->count * 4, g->stream));
+  if (g->n > 0) MC_TRY(launch_heuristic(g, mode, kDefaultSpinLimit, nullptr, 0));
+  MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  MC_TRY(check_device_error(g));
+  int32_t size = 0;
+  MC_CUDA_TRY(cudaMemcpy(&size, g->best, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  *size_out = size;
+  if (size > capacity) return MC_ERR_BUFFER;
+  if (size > 0 && !clique_out) return MC_ERR_ARG;
+  return copy_witness_out(g, 0, size, clique_out, 0);
+}
+
+int mc_max_clique(mc_graph *g, const mc_options *opt, int32_t *omega_out, int32_t *witness_out, int32_t capacity,
+                  mc_stats *stats) {
+  if (!g || !omega_out || capacity < 0) return MC_ERR_ARG;
+  *omega_out = 0;
+  mc_stats local;
+  mc_stats *st = stats ? stats : &local;
+  MC_TRY(run_max_clique(g, opt, st));
+  int32_t om = 0;
+  MC_CUDA_TRY(cudaMemcpy(&om, g->best, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  *omega_out = om;
+  st->omega = om;
+  if (om > capacity) return MC_ERR_BUFFER;
+  if (om > 0 && !witness_out) return MC_ERR_ARG;
+  return copy_witness_out(g, 0, om, witness_out, 0);
+}
+
+int mc_max_clique_batch(mc_graph *g, const mc_options *opt, int32_t *omegas_out, int32_t *witness_out,
+                        int64_t capacity, int64_t *witness_offsets, mc_stats *stats) {
+  if (!g || !omegas_out || !witness_offsets || capacity < 0) return MC_ERR_ARG;
+  mc_stats local;
+  mc_stats *st = stats ? stats : &local;
+  MC_TRY(run_max_clique(g, opt, st));
+  std::vector<int32_t> om(g->count);
+  MC_CUDA_TRY(cudaMemcpy(om.data(), g->best, g->count * 4, cudaMemcpyDeviceToHost));
+  std::vector<int64_t> off(g->count + 1, 0);
+  for (int32_t i = 0; i < g->count; i++) off[i + 1] = off[i] + om[i];
+  MC_CUDA_TRY(cudaMemcpy(omegas_out, om.data(), g->count * 4, cudaMemcpyDefault));
+  MC_CUDA_TRY(cudaMemcpy(witness_offsets, off.data(), (g->count + 1) * 8, cudaMemcpyDefault));
+  int32_t mx = 0;
+  for (int32_t x : om) mx = std::max(mx, x);
+  st->omega = mx;
+  if (off[g->count] > capacity) return MC_ERR_BUFFER;
+  if (off[g->count] > 0 && !witness_out) return MC_ERR_ARG;
+  // gather all witnesses on the host in one copy of the witness area
+  std::vector<int32_t> all(std::max<int64_t>(g->n, 1));
+  if (g->n > 0) MC_CUDA_TRY(cudaMemcpy(all.data(), g->wit, g->n * 4, cudaMemcpyDeviceToHost));
+  std::vector<int32_t> outv(std::max<int64_t>(off[g->count], 1));
+  for (int32_t i = 0; i < g->count; i++) {
+    int64_t b = g->h_voff[i];
+    for (int32_t t = 0; t < om[i]; t++) outv[off[i] + t] = all[b + t] - (int32_t)b;
+    std::sort(outv.begin() + off[i], outv.begin() + off[i] + om[i]);
+  }
+  if (off[g->count] > 0)
+    MC_CUDA_TRY(cudaMemcpy(witness_out, outv.data(), off[g->count] * 4, cudaMemcpyDefault));
+  return MC_OK;
+}
+
+int mc_verify_clique(mc_graph *g, const int32_t *vertices, int32_t k, int32_t *is_clique_out) {
+  if (!g || !is_clique_out || k < 0 || (k > 0 && !vertices)) return MC_ERR_ARG;
+  *is_clique_out = 0;
+  if (k == 0) {
+    *is_clique_out = 1;
+    return MC_OK;
+  }
+  void *p;
+  MC_TRY(ws_get(g, "cp.vs", (size_t)k * 4 + 64, &p));
+  int32_t *d = (int32_t *)p;
+  MC_CUDA_TRY(cudaMemcpyAsync(d, vertices, (size_t)k * 4, cudaMemcpyDefault, g->stream));
+  int32_t *ok = d + k;
+  MC_TRY(launch_verify_set(g, d, k, ok));
+  MC_CUDA_TRY(cudaMemcpyAsync(g->h_small, ok, 4, cudaMemcpyDeviceToHost, g->stream));
+  MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  *is_clique_out = *(int32_t *)g->h_small;
+  return MC_OK;
+}
+
+}  // extern "C"

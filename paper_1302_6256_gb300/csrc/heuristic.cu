@@ -1,0 +1,259 @@
+// Heuristic clique (Algorithm 1, Section 4.1), one warp per start vertex.
+//
+// Vertices are visited in decreasing core number (the peel order reversed).
+// For a start vertex v the warp gathers S = neighbours with K >= threshold
+// into a per-warp candidate buffer (coalesced row reads, ballot compaction),
+// then grows C = {v} greedily: the next member is the remaining candidate of
+// largest core number (ties: larger degree, then smaller id), and the
+// candidates are filtered to that member's neighbours (binary search in its
+// sorted CSR row).  Taking the first remaining candidate each time is the
+// same as Algorithm 1's scan "add u if C + u is still a clique" in that order.
+//
+// mode 0 (Algorithm 1 as printed, run by all warps at once): the running
+//   maximum is the incumbent shared through global memory; a warp skips v if
+//   K(v) < max, filters S by K >= max, and raises the incumbent when it finds
+//   a larger clique.  The result depends on timing; it is always a clique.
+// mode 1 (deterministic): every start vertex is grown with threshold 0 and
+//   the largest clique wins, ties to the smallest start vertex (a 64-bit
+//   atomicMax key); a second kernel regrows the winner and writes it.
+// Start vertices that cannot reach the current best (K(v) + 1 below it) are
+// skipped, and a greedy run stops once C plus all remaining candidates cannot
+// beat the best; neither changes the result of either mode.
+#include <algorithm>
+#include <climits>
+
+#include "mc_internal.cuh"
+
+namespace mc {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int kHT = 256;  // threads per block
+
+struct HA {
+  int64_t n;
+  const int64_t *rp;
+  const int32_t *ci, *core, *order, *gid;
+  const int64_t *voff;
+  int32_t *best, *lock, *wit, *err;
+  long long spin;
+  int mode;
+  int32_t *cand;            // per-warp candidate buffers
+  int64_t cand_stride;
+  int32_t *cl;              // per-warp clique buffers
+  int64_t cl_stride;
+  int32_t *next;
+  unsigned long long *detkey;  // per graph (mode 1)
+  const int32_t *seeds;
+  int64_t nseeds;
+};
+
+struct Key {
+  int k, d, id;
+};
+__device__ __forceinline__ bool better(const Key &a, const Key &b) {
+  if (a.k != b.k) return a.k > b.k;
+  if (a.d != b.d) return a.d > b.d;
+  return a.id < b.id;
+}
+__device__ __forceinline__ Key warp_best(Key x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Key y{__shfl_xor_sync(FULL, x.k, o), __shfl_xor_sync(FULL, x.d, o), __shfl_xor_sync(FULL, x.id, o)};
+    if (better(y, x)) x = y;
+  }
+  return x;
+}
+__device__ __forceinline__ Key key_of(const HA &a, int u) {
+  return Key{a.core[u], (int)(a.rp[u + 1] - a.rp[u]), u};
+}
+__device__ __forceinline__ bool in_row(const HA &a, int x, int y) {
+  int64_t lo = a.rp[x], hi = a.rp[x + 1];
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    int c = a.ci[mid];
+    if (c < y) lo = mid + 1; else hi = mid;
+  }
+  return lo < a.rp[x + 1] && a.ci[lo] == y;
+}
+
+// Greedy clique from v (all lanes).  thr: candidate core threshold; stop_at:
+// stop once |C| + |cand| < stop_at (cannot reach it).  Writes the clique to
+// cl[0..size) and returns its size.
+__device__ int grow(const HA &a, int v, int thr, int stop_at, int32_t *cand, int32_t *cl) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const Key none{INT_MIN, INT_MIN, INT_MAX};
+  int cnt = 0;
+  Key bk = none;
+  const int64_t e0 = a.rp[v], e1 = a.rp[v + 1];
+  for (int64_t eb = e0; eb < e1; eb += 32) {
+    int64_t e = eb + lane;
+    int u = -1;
+    bool ok = false;
+    if (e < e1) {
+      u = a.ci[e];
+      ok = a.core[u] >= thr;
+    }
+    unsigned m = __ballot_sync(FULL, ok);
+    if (ok) {
+      cand[cnt + __popc(m & lt)] = u;
+      Key k = key_of(a, u);
+      if (better(k, bk)) bk = k;
+    }
+    cnt += __popc(m);
+  }
+  bk = warp_best(bk);
+  int size = 1;
+  if (lane == 0) cl[0] = v;
+  for (;;) {
+    if (cnt == 0 || size + cnt < stop_at) break;
+    const int w = bk.id;
+    if (lane == 0) cl[size] = w;
+    size++;
+    __syncwarp();
+    // keep the candidates adjacent to w (in-place compaction, reads ahead of writes)
+    int out = 0;
+    Key nb = none;
+    for (int base = 0; base < cnt; base += 32) {
+      int i = base + lane;
+      int x = (i < cnt) ? cand[i] : -1;
+      bool keep = x >= 0 && x != w && in_row(a, w, x);
+      unsigned m = __ballot_sync(FULL, keep);
+      __syncwarp();
+      if (keep) {
+        cand[out + __popc(m & lt)] = x;
+        Key k = key_of(a, x);
+        if (better(k, nb)) nb = k;
+      }
+      out += __popc(m);
+      __syncwarp();
+    }
+    cnt = out;
+    bk = warp_best(nb);
+  }
+  __syncwarp();
+  return size;
+}
+
+__global__ void __launch_bounds__(kHT) heuristic_kernel(HA a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int32_t *cand = a.cand + gw * a.cand_stride;
+  int32_t *cl = a.cl + gw * a.cl_stride;
+  const int64_t total = a.n + a.nseeds;
+  for (;;) {
+    int64_t i = 0;
+    if (lane == 0) i = atomicAdd(a.next, 1);
+    i = __shfl_sync(FULL, (long long)i, 0);
+    if (i >= total || *(volatile int32_t *)a.err) break;
+    const int v = (i < a.nseeds) ? a.seeds[i] : a.order[a.n - 1 - (i - a.nseeds)];
+    const int g = a.gid ? a.gid[v] : 0;
+    const int kv = a.core[v];
+    if (a.mode == 0) {
+      int mx = 0;
+      if (lane == 0) mx = *(volatile int32_t *)(a.best + g);
+      mx = __shfl_sync(FULL, mx, 0);
+      if (kv < mx) continue;
+      int size = grow(a, v, mx, mx + 1, cand, cl);
+      if (size > mx) {
+        dev::raise_incumbent(a.best, a.lock, a.wit, a.voff, g, size, a.err, a.spin, [&](int ln, int32_t *base) {
+          for (int t = ln; t < size; t += 32) base[t] = cl[t];
+        });
+      }
+    } else {
+      unsigned long long cur = 0;
+      if (lane == 0) cur = *(volatile unsigned long long *)(a.detkey + g);
+      cur = __shfl_sync(FULL, cur, 0);
+      int bsz = (int)(cur >> 32);
+      if (kv + 1 < bsz) continue;
+      int size = grow(a, v, 0, bsz, cand, cl);
+      unsigned long long key = ((unsigned long long)size << 32) | (unsigned)(0x7fffffff - v);
+      if (lane == 0 && key > cur) atomicMax(a.detkey + g, key);
+    }
+  }
+}
+
+// mode 1: regrow each graph's winning start vertex and publish it
+__global__ void heuristic_finalize_kernel(HA a, int32_t ngraphs) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int32_t *cand = a.cand + gw * a.cand_stride;
+  int32_t *cl = a.cl + gw * a.cl_stride;
+  for (int64_t g = gw; g < ngraphs; g += nw) {
+    unsigned long long key = a.detkey[g];
+    int size = (int)(key >> 32);
+    if (size == 0) continue;
+    int v = 0x7fffffff - (int)(key & 0xffffffffu);
+    int s2 = grow(a, v, 0, 0, cand, cl);
+    if (s2 != size) {
+      if (lane == 0) atomicExch(a.err, kDevCheck);
+      continue;
+    }
+    int32_t *base = a.wit + (a.voff ? a.voff[g] : 0);
+    for (int t = lane; t < size; t += 32) base[t] = cl[t];
+    __syncwarp();
+    __threadfence();
+    if (lane == 0) a.best[g] = size;
+  }
+  (void)lane;
+}
+
+}  // namespace
+
+int launch_heuristic(mc_graph *g, int mode, long long spin_limit, const int32_t *seeds, int64_t nseeds) {
+  if (g->n == 0) return MC_OK;
+  void *p;
+  const int64_t cstride = (int64_t)g->max_degree + 1;
+  const int64_t lstride = (int64_t)g->max_core + 2;
+  // warps limited so that the candidate buffers stay within ~1 GiB
+  int64_t warps = (int64_t)g->sm_count * 16;
+  const int64_t budget = (int64_t)1 << 28;  // int32 entries
+  warps = std::max<int64_t>(32, std::min<int64_t>(warps, budget / cstride));
+  warps = std::min<int64_t>(warps, ((g->n + nseeds) + 0) + 32);
+  warps = (warps + 7) / 8 * 8;
+  MC_TRY(ws_get(g, "he.cand", (size_t)warps * cstride * 4, &p));
+  int32_t *cand = (int32_t *)p;
+  MC_TRY(ws_get(g, "he.cl", (size_t)warps * lstride * 4, &p));
+  int32_t *cl = (int32_t *)p;
+  MC_TRY(ws_get(g, "he.ctl", 64 + (size_t)g->count * 8, &p));
+  int32_t *next = (int32_t *)p;
+  unsigned long long *detkey = (unsigned long long *)((char *)p + 64);
+  MC_CUDA_TRY(cudaMemsetAsync(p, 0, 64 + (size_t)g->count * 8, g->stream));
+  HA a{};
+  a.n = g->n;
+  a.rp = g->row_ptr;
+  a.ci = g->col_idx;
+  a.core = g->core;
+  a.order = g->order;
+  a.gid = g->gid;
+  a.voff = g->gid ? g->voff : nullptr;
+  a.best = g->best;
+  a.lock = g->lock;
+  a.wit = g->wit;
+  a.err = g->err;
+  a.spin = spin_limit;
+  a.mode = mode;
+  a.cand = cand;
+  a.cand_stride = cstride;
+  a.cl = cl;
+  a.cl_stride = lstride;
+  a.next = next;
+  a.detkey = detkey;
+  a.seeds = seeds;
+  a.nseeds = seeds ? nseeds : 0;
+  const int blocks = (int)((warps * 32 + kHT - 1) / kHT);
+  heuristic_kernel<<<blocks, kHT, 0, g->stream>>>(a);
+  g_launches++;
+  MC_CUDA_TRY(cudaGetLastError());
+  if (mode == 1) {
+    heuristic_finalize_kernel<<<blocks, kHT, 0, g->stream>>>(a, g->count);
+    g_launches++;
+    MC_CUDA_TRY(cudaGetLastError());
+  }
+  return MC_OK;
+}
+
+}  // namespace mc

@@ -1,0 +1,221 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <map>
+#include <string>
+
+#include "../../include/mc.h"
+
+namespace mc {
+
+// ------------------------------------------------------------------ host ---
+
+extern std::atomic<int64_t> g_launches;
+
+#define MC_CUDA_TRY(expr)                                 \
+  do {                                                    \
+    cudaError_t _e = (expr);                              \
+    if (_e != cudaSuccess) {                              \
+      mc::set_last_cuda_error(_e, #expr, __FILE__, __LINE__); \
+      return (_e == cudaErrorMemoryAllocation) ? MC_ERR_OOM : MC_ERR_CUDA; \
+    }                                                     \
+  } while (0)
+
+#define MC_TRY(expr)              \
+  do {                            \
+    int _rc = (expr);             \
+    if (_rc != MC_OK) return _rc; \
+  } while (0)
+
+void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+// Default device spin-wait limit (iterations of a ~100 ns back-off loop).
+constexpr long long kDefaultSpinLimit = 100000000LL;
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+// Device-side error word values (0 = fine).
+enum DevErr : int {
+  kDevOk = 0,
+  kDevTimeout = 1,      // a bounded spin-wait gave up
+  kDevOverflow = 2,     // an internal capacity was exceeded
+  kDevUnsupported = 3,  // neighbourhood larger than the supported maximum
+  kDevCheck = 4,        // consistency check failed
+};
+
+}  // namespace mc
+
+struct mc_graph {
+  int64_t n = 0, nnz = 0;
+  int32_t count = 1;
+  int device = 0, sm_count = 0;
+  cudaStream_t stream = nullptr;
+  bool borrowed = false;
+  // CSR (device)
+  int64_t *row_ptr = nullptr;
+  int32_t *col_idx = nullptr;
+  int64_t *voff = nullptr;    // count+1 (device)
+  int64_t *h_voff = nullptr;  // count+1 (host)
+  int32_t *gid = nullptr;     // n graph ids (device), nullptr for a single graph
+  int32_t max_degree = 0;
+  // core numbers cache
+  bool cores_valid = false;
+  int32_t max_core = 0;
+  int32_t *core = nullptr, *order = nullptr, *pos = nullptr;  // n each (device)
+  // incumbent, one per graph: size, lock, witness area (vertex-offset indexed)
+  int32_t *best = nullptr, *lock = nullptr, *wit = nullptr;
+  // device error word and small control block
+  int32_t *err = nullptr;
+  // named workspace buffers (grown on demand, reused across calls)
+  std::map<std::string, mc::DevBuf> ws;
+  // pinned host staging for small results
+  void *h_small = nullptr;
+  cudaEvent_t ev[8] = {};
+};
+
+namespace mc {
+
+// Workspace buffer of at least `bytes` bytes under `name` (kept across calls).
+int ws_get(mc_graph *g, const char *name, size_t bytes, void **out);
+// Read the device error word, reset it, and map it to an MC_ERR_* code.
+int check_device_error(mc_graph *g);
+// True if p is a device (or managed) pointer.
+bool is_device_ptr(const void *p);
+
+// ---- kernels (launch wrappers; each returns MC_OK or an error) ----
+
+// Core numbers, peel (degeneracy) order and peel positions.
+int launch_core_numbers(mc_graph *g, long long spin_limit);
+
+// Heuristic (Algorithm 1).  mode 0 racy, 1 deterministic.  Raises the
+// incumbent of every graph.  seeds (nullable, device): vertices grown first.
+int launch_heuristic(mc_graph *g, int mode, long long spin_limit, const int32_t *seeds, int64_t nseeds);
+
+// Pruned, oriented graph and the root lists (see prune.cu).
+struct Pruned {
+  int64_t n = 0, arcs = 0;         // vertices and arcs of the oriented graph
+  int32_t max_out = 0;             // largest out-degree
+  int64_t nroots_small = 0, nroots_block = 0, nroots_big = 0;
+  int64_t *orow = nullptr;         // n+1, each row start a multiple of 4 (int4 loads)
+  int32_t *ocol = nullptr;         // arcs (padded rows, pad = -1)
+  int32_t *ocore = nullptr;        // core number per pruned vertex
+  int32_t *oold = nullptr;         // original vertex id
+  int32_t *ogid = nullptr;         // graph id (nullptr for one graph)
+  int32_t *roots = nullptr;        // root list storage
+  int32_t *roots_small = nullptr;  // roots by class, each in processing order
+  int32_t *roots_block = nullptr;
+  int32_t *roots_big = nullptr;
+  int32_t *odeg = nullptr;         // out-degree per pruned vertex
+};
+int launch_prune(mc_graph *g, int ordering, const float *scores, int32_t warp_max, Pruned *out,
+                 long long spin_limit);
+
+// Search (InitialBranch + Branch) over all roots.
+struct SearchCounters {
+  unsigned long long roots_colored, roots_branched, nodes, donations;
+};
+int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, long long spin_limit,
+                  SearchCounters *counters);
+
+// Witness verification of every graph's incumbent: writes per-graph flags.
+int launch_verify(mc_graph *g, int32_t *d_ok);
+int launch_verify_set(mc_graph *g, const int32_t *d_vs, int32_t k, int32_t *d_ok);
+int launch_validate(mc_graph *g, int32_t *d_bad);
+int launch_gid(mc_graph *g);
+// Indices of the k largest scores (descending), over all vertices.
+int top_scores(mc_graph *g, const float *scores, int64_t k, int32_t *out);
+
+}  // namespace mc
+
+// ---------------------------------------------------------------- device ---
+
+#ifdef __CUDACC__
+namespace mc {
+namespace dev {
+
+__device__ __forceinline__ int ld_cg(const int *p) { return __ldcg(p); }
+__device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
+
+__device__ __forceinline__ int warp_sum(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Raise the incumbent of graph gidx to `size` with the members written by
+// `write(lane, base)` -- called by all 32 lanes of a warp; base is the start
+// of the graph's witness area.  A per-graph lock (bounded spin) keeps the
+// witness consistent with the size.  Returns true if this call raised it.
+template <class WriteFn>
+__device__ bool raise_incumbent(int32_t *best, int32_t *lock, int32_t *wit, const int64_t *voff, int gidx,
+                                int size, int32_t *err, long long spin_limit, WriteFn write) {
+  const int lane = threadIdx.x & 31;
+  int ok = 0;
+  if (lane == 0) {
+    if (size > ld_volatile(best + gidx)) {
+      long long it = 0;
+      while (atomicCAS(lock + gidx, 0, 1) != 0) {
+        if (++it > spin_limit) { atomicExch(err, kDevTimeout); break; }
+        __nanosleep(64);
+      }
+      if (it <= spin_limit) ok = (size > ld_volatile(best + gidx)) ? 1 : 2;
+    }
+  }
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (ok == 0) return false;
+  if (ok == 1) {
+    int32_t *base = wit + (voff ? voff[gidx] : 0);
+    write(lane, base);
+    __syncwarp();
+    __threadfence();
+  }
+  if (lane == 0) {
+    if (ok == 1) {
+      *(volatile int32_t *)(best + gidx) = size;
+      __threadfence();
+    }
+    atomicExch(lock + gidx, 0);
+  }
+  __syncwarp();
+  return ok == 1;
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).
+// Bounded spin: on timeout the error word is set and the caller must return.
+__device__ __forceinline__ void grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks, int32_t *err,
+                                             long long spin_limit) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned g0 = *(volatile unsigned *)gen;
+    __threadfence();
+    if (atomicAdd(count, 1u) == nblocks - 1) {
+      *(volatile unsigned *)count = 0;
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      long long it = 0;
+      while (*(volatile unsigned *)gen == g0) {
+        if (++it > spin_limit) { atomicExch(err, kDevTimeout); break; }
+        __nanosleep(20);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+}  // namespace dev
+}  // namespace mc
+#endif

@@ -1,0 +1,338 @@
+// Initial pruning and the oriented search graph (Section 4.2; Algorithm 2,
+// line 4: vertices with K(v) < |H| are removed explicitly).
+//
+// The kept vertices are renumbered in peel (degeneracy) order, and each keeps
+// only the neighbours that come later in that order.  A root u of the search
+// then sees exactly the candidates a sequential run of Algorithm 2 would see
+// when it reaches u: the neighbours not yet searched (the set X of Section 4.3
+// is "every vertex earlier in the order").  Every clique is searched once,
+// from its earliest member, and a vertex has at most K(v) later neighbours.
+// Rows start at multiples of 4 entries so the search reads them with int4
+// loads (pad entries are -1).
+#include <cub/cub.cuh>
+
+#include "mc_internal.cuh"
+#include "scan.cuh"
+
+namespace mc {
+
+__global__ void scan_blocks_kernel(int64_t nb, int64_t *bsum) {
+  __shared__ int64_t wsum[32];
+  __shared__ int64_t carry;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < nb; base += blockDim.x) {
+    int64_t i = base + threadIdx.x;
+    int64_t x = (i < nb) ? bsum[i] : 0;
+    int64_t incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int64_t t = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+        int64_t s = wsum[w];
+        wsum[w] = t;
+        t += s;
+      }
+    }
+    __syncthreads();
+    int64_t excl = carry + wsum[wid] + incl - x;
+    if (i < nb) bsum[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = excl + x;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bsum[nb] = carry;
+}
+
+namespace {
+
+struct KeepF {
+  const int32_t *order, *core, *gid, *best;
+  __device__ int64_t operator()(int64_t i) const {
+    int v = order[i];
+    int g = gid ? gid[v] : 0;
+    return core[v] >= best[g] ? 1 : 0;
+  }
+};
+struct KeepG {
+  const int32_t *order, *core, *gid;
+  int32_t *nid, *oold, *ocore, *ogid;
+  __device__ void operator()(int64_t i, int64_t excl, int64_t val) const {
+    int v = order[i];
+    if (val) {
+      nid[v] = (int32_t)excl;
+      oold[excl] = v;
+      ocore[excl] = core[v];
+      if (ogid) ogid[excl] = gid[v];
+    } else {
+      nid[v] = -1;
+    }
+  }
+};
+
+// out-degree in the oriented pruned graph (warp per vertex)
+__global__ void outdeg_kernel(int64_t np, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                              const int32_t *__restrict__ oold, const int32_t *__restrict__ nid,
+                              int32_t *__restrict__ odeg, int32_t *__restrict__ maxout) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int lmax = 0;
+  for (int64_t j = w0; j < np; j += nw) {
+    int v = oold[j];
+    int c = 0;
+    for (int64_t e = rp[v] + lane; e < rp[v + 1]; e += 32) c += (nid[ci[e]] > (int32_t)j) ? 1 : 0;
+    c = dev::warp_sum(c);
+    if (lane == 0) odeg[j] = c;
+    lmax = max(lmax, c);
+  }
+  if (lane == 0) atomicMax(maxout, lmax);
+}
+
+struct PadF {
+  const int32_t *odeg;
+  __device__ int64_t operator()(int64_t j) const { return (int64_t)((odeg[j] + 3) & ~3); }
+};
+struct RowG {
+  int64_t *orow;
+  __device__ void operator()(int64_t j, int64_t excl, int64_t) const { orow[j] = excl; }
+};
+
+__global__ void fill_kernel(int64_t np, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const int32_t *__restrict__ oold, const int32_t *__restrict__ nid,
+                            const int64_t *__restrict__ orow, const int32_t *__restrict__ odeg,
+                            int32_t *__restrict__ ocol, int64_t total) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int64_t j = w0; j < np; j += nw) {
+    int v = oold[j];
+    int64_t out = orow[j];
+    int64_t e1 = rp[v + 1];
+    int put = 0;
+    for (int64_t eb = rp[v]; eb < e1; eb += 32) {
+      int64_t e = eb + lane;
+      int y = (e < e1) ? nid[ci[e]] : -1;
+      bool k = y > (int32_t)j;
+      unsigned m = __ballot_sync(0xffffffffu, k);
+      if (k) ocol[out + put + __popc(m & lt)] = y;
+      put += __popc(m);
+    }
+    int padded = (odeg[j] + 3) & ~3;
+    for (int t = put + lane; t < padded; t += 32) ocol[out + t] = -1;
+  }
+  (void)total;
+}
+
+__global__ void orow_end_kernel(int64_t np, int64_t *orow, const int64_t *total) { orow[np] = *total; }
+
+// root flags and classes
+struct RootInfo {
+  const int32_t *odeg, *ogid, *best;
+  int32_t warp_max;
+  __device__ int cls(int64_t j) const {
+    int g = ogid ? ogid[j] : 0;
+    int d = odeg[j];
+    if (d < best[g] || d == 0) return -1;  // |P| >= omega~ is needed for a larger clique
+    return d <= warp_max ? 0 : (d <= 1024 ? 1 : 2);
+  }
+};
+
+// index space t -> pruned vertex j for the root order
+struct PermDesc {  // ordering 0: decreasing rank (dense core first)
+  int64_t np;
+  __device__ int64_t operator()(int64_t t) const { return np - 1 - t; }
+};
+struct PermTable {  // ordering 1/2: explicit table
+  const int32_t *tab;
+  __device__ int64_t operator()(int64_t t) const { return tab[t]; }
+};
+
+template <class Perm>
+struct ClassF {
+  RootInfo ri;
+  Perm perm;
+  int c;
+  __device__ int64_t operator()(int64_t t) const { return ri.cls(perm(t)) == c ? 1 : 0; }
+};
+template <class Perm>
+struct ClassG {
+  Perm perm;
+  int32_t *out;
+  __device__ void operator()(int64_t t, int64_t excl, int64_t val) const {
+    if (val) out[excl] = (int32_t)perm(t);
+  }
+};
+
+// native order: kept vertices by increasing original id
+struct NativeF {
+  const int32_t *nid;
+  __device__ int64_t operator()(int64_t v) const { return nid[v] >= 0 ? 1 : 0; }
+};
+struct NativeG {
+  const int32_t *nid;
+  int32_t *tab;
+  __device__ void operator()(int64_t v, int64_t excl, int64_t val) const {
+    if (val) tab[excl] = nid[v];
+  }
+};
+
+__global__ void gather_scores_kernel(int64_t np, const int32_t *__restrict__ oold, const float *__restrict__ score,
+                                     float *__restrict__ key, int32_t *__restrict__ idx) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < np; j += (int64_t)gridDim.x * blockDim.x) {
+    key[j] = score[oold[j]];
+    idx[j] = (int32_t)j;
+  }
+}
+
+}  // namespace
+
+int launch_prune(mc_graph *g, int ordering, const float *scores, int32_t warp_max, Pruned *out,
+                 long long spin_limit) {
+  (void)spin_limit;
+  const int64_t n = g->n;
+  void *p;
+  MC_TRY(ws_get(g, "pr.nid", (n + 1) * sizeof(int32_t), &p));
+  int32_t *nid = (int32_t *)p;
+  MC_TRY(ws_get(g, "pr.oold", (n + 1) * sizeof(int32_t), &p));
+  int32_t *oold = (int32_t *)p;
+  MC_TRY(ws_get(g, "pr.ocore", (n + 1) * sizeof(int32_t), &p));
+  int32_t *ocore = (int32_t *)p;
+  int32_t *ogid = nullptr;
+  if (g->gid) {
+    MC_TRY(ws_get(g, "pr.ogid", (n + 1) * sizeof(int32_t), &p));
+    ogid = (int32_t *)p;
+  }
+  MC_TRY(ws_get(g, "pr.small", 16 * sizeof(int64_t), &p));
+  int64_t *dsm = (int64_t *)p;  // [0] n', [1] arcs, [2] maxout(int32 in low), [3..5] class counts
+  MC_CUDA_TRY(cudaMemsetAsync(dsm, 0, 16 * sizeof(int64_t), g->stream));
+
+  KeepF kf{g->order, g->core, g->gid, g->best};
+  KeepG kg{g->order, g->core, g->gid, nid, oold, ocore, ogid};
+  MC_TRY(device_scan(g, n, kf, kg, dsm + 0, "pr.scan"));
+  int64_t *h = (int64_t *)g->h_small;
+  MC_CUDA_TRY(cudaMemcpyAsync(h, dsm, sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream));
+  MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  const int64_t np = h[0];
+  out->n = np;
+  out->oold = oold;
+  out->ocore = ocore;
+  out->ogid = ogid;
+  out->nroots_small = out->nroots_block = out->nroots_big = 0;
+  out->arcs = 0;
+  out->max_out = 0;
+  if (np == 0) return MC_OK;
+
+  MC_TRY(ws_get(g, "pr.odeg", (np + 1) * sizeof(int32_t), &p));
+  int32_t *odeg = (int32_t *)p;
+  int32_t *maxout = (int32_t *)(dsm + 2);
+  const int blocks = (int)std::min<int64_t>((np * 32 + 255) / 256, (int64_t)g->sm_count * 16);
+  outdeg_kernel<<<blocks, 256, 0, g->stream>>>(np, g->row_ptr, g->col_idx, oold, nid, odeg, maxout);
+  g_launches++;
+  MC_CUDA_TRY(cudaGetLastError());
+  MC_TRY(ws_get(g, "pr.orow", (np + 1) * sizeof(int64_t), &p));
+  int64_t *orow = (int64_t *)p;
+  MC_TRY(device_scan(g, np, PadF{odeg}, RowG{orow}, dsm + 1, "pr.scan"));
+  orow_end_kernel<<<1, 1, 0, g->stream>>>(np, orow, dsm + 1);
+  g_launches++;
+  // worst case: every edge kept once plus row padding
+  const size_t arcs_cap = (size_t)(g->nnz / 2 + 4 * np + 4);
+  MC_TRY(ws_get(g, "pr.ocol", arcs_cap * sizeof(int32_t), &p));
+  int32_t *ocol = (int32_t *)p;
+  fill_kernel<<<blocks, 256, 0, g->stream>>>(np, g->row_ptr, g->col_idx, oold, nid, orow, odeg, ocol, 0);
+  g_launches++;
+  MC_CUDA_TRY(cudaGetLastError());
+
+  // roots in processing order, split by class
+  MC_TRY(ws_get(g, "pr.roots", (3 * np + 3) * sizeof(int32_t), &p));
+  int32_t *roots = (int32_t *)p;
+  RootInfo ri{odeg, ogid, g->best, warp_max};
+  int32_t *tab = nullptr;
+  if (ordering == 1 || ordering == 2) {
+    MC_TRY(ws_get(g, "pr.tab", (np + 1) * sizeof(int32_t), &p));
+    tab = (int32_t *)p;
+  }
+  if (ordering == 2) {
+    MC_TRY(device_scan(g, n, NativeF{nid}, NativeG{nid, tab}, nullptr, "pr.scan"));
+  } else if (ordering == 1) {
+    if (!scores) return MC_ERR_ARG;
+    MC_TRY(ws_get(g, "pr.skey", (2 * np + 2) * sizeof(float), &p));
+    float *skey = (float *)p;
+    MC_TRY(ws_get(g, "pr.sidx", (np + 1) * sizeof(int32_t), &p));
+    int32_t *sidx = (int32_t *)p;
+    gather_scores_kernel<<<blocks, 256, 0, g->stream>>>(np, oold, scores, skey, sidx);
+    g_launches++;
+    size_t tmp = 0;
+    cub::DeviceRadixSort::SortPairsDescending(nullptr, tmp, skey, skey + np + 1, sidx, tab, (int)np, 0, 32,
+                                              g->stream);
+    MC_TRY(ws_get(g, "pr.cubtmp", tmp + 16, &p));
+    MC_CUDA_TRY(cub::DeviceRadixSort::SortPairsDescending(p, tmp, skey, skey + np + 1, sidx, tab, (int)np, 0, 32,
+                                                          g->stream));
+    g_launches++;
+  }
+  for (int c = 0; c < 3; c++) {
+    int32_t *dst = roots + (int64_t)c * np;
+    if (ordering == 0) {
+      MC_TRY(device_scan(g, np, ClassF<PermDesc>{ri, PermDesc{np}, c}, ClassG<PermDesc>{PermDesc{np}, dst},
+                         dsm + 3 + c, "pr.scan"));
+    } else {
+      MC_TRY(device_scan(g, np, ClassF<PermTable>{ri, PermTable{tab}, c}, ClassG<PermTable>{PermTable{tab}, dst},
+                         dsm + 3 + c, "pr.scan"));
+    }
+  }
+  MC_CUDA_TRY(cudaMemcpyAsync(h, dsm, 6 * sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream));
+  MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  out->arcs = h[1];
+  out->max_out = (int32_t)(h[2] & 0xffffffff);
+  out->nroots_small = h[3];
+  out->nroots_block = h[4];
+  out->nroots_big = h[5];
+  out->orow = orow;
+  out->ocol = ocol;
+  out->roots = roots;
+  out->roots_small = roots;
+  out->roots_block = roots + np;
+  out->roots_big = roots + 2 * np;
+  out->odeg = odeg;
+  return MC_OK;
+}
+
+namespace {
+__global__ void iota_kernel(int64_t n, const float *__restrict__ s, float *__restrict__ key, int32_t *__restrict__ idx) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    key[i] = s[i];
+    idx[i] = (int32_t)i;
+  }
+}
+}  // namespace
+
+int top_scores(mc_graph *g, const float *scores, int64_t k, int32_t *out) {
+  const int64_t n = g->n;
+  void *p;
+  MC_TRY(ws_get(g, "ts.key", (2 * n + 2) * sizeof(float), &p));
+  float *key = (float *)p;
+  MC_TRY(ws_get(g, "ts.idx", (2 * n + 2) * sizeof(int32_t), &p));
+  int32_t *idx = (int32_t *)p;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)g->sm_count * 8);
+  iota_kernel<<<blocks, 256, 0, g->stream>>>(n, scores, key, idx);
+  g_launches++;
+  size_t tmp = 0;
+  cub::DeviceRadixSort::SortPairsDescending(nullptr, tmp, key, key + n + 1, idx, idx + n + 1, (int)n, 0, 32,
+                                            g->stream);
+  MC_TRY(ws_get(g, "ts.tmp", tmp + 16, &p));
+  MC_CUDA_TRY(cub::DeviceRadixSort::SortPairsDescending(p, tmp, key, key + n + 1, idx, idx + n + 1, (int)n, 0, 32,
+                                                        g->stream));
+  g_launches++;
+  MC_CUDA_TRY(cudaMemcpyAsync(out, idx + n + 1, k * sizeof(int32_t), cudaMemcpyDeviceToDevice, g->stream));
+  return MC_OK;
+}
+
+}  // namespace mc

@@ -1,0 +1,893 @@
+// Neighbourhood branch and bound: InitialBranch and Branch of Algorithm 2
+// (Section 4.3), with the incumbent shared by every worker as soon as it
+// changes (Section 4.5).
+//
+// For a root u of the oriented pruned graph the candidate set is
+//   P = { w in N+(u) : K(w) >= omega }           (N_R(u) of Section 4.3)
+// and the search looks for a clique larger than omega containing u:
+//   1. |P| < omega                    -> return (degree bound, Fact 2 (3))
+//   2. bitset adjacency of G[P]       (the small-graph adjacency matrix of
+//      Section 4.4, built from the later-neighbour rows of P's members)
+//   3. (omega-1)-core of G[P]: exactly the vertices with neighbourhood core
+//      number K_N >= |H| when u is counted (lines 15-18 of InitialBranch;
+//      the tight form of the test); fewer than omega left -> return
+//   4. greedy colouring, L colours; 1 + L <= omega -> return (Fact 2 (1))
+//   5. Branch({u}, P): depth-first, each node colours its candidates
+//      greedily in index order (independent-set extraction with ballot and
+//      popc over bit rows) and branches on the vertices whose colour can still
+//      beat omega; a maximal clique larger than omega raises the incumbent.
+// Bit positions are P sorted by decreasing rank, so "index order" colours the
+// latest vertices of the degeneracy order first (the degeneracy-order
+// colouring of InitialBranch) and every node uses the same natural order.
+//
+// Workers, split by the out-degree of the root (an upper bound on |P|):
+//   warp class   |N+(u)| <= 128: one warp per root, matrix in shared memory;
+//   block class  |N+(u)| <= 1024: one block per root, matrix (<= 128 KB) in
+//                shared memory, the block's 16 warps share the root's search
+//                tree through a shared-memory task pool (a busy warp hands the
+//                shallowest untried branch to an idle one);
+//   big class    larger: as the block class with the matrix in global memory.
+// Every spin-wait is bounded; on timeout the device error word is set.
+#include <algorithm>
+#include <climits>
+
+#include "mc_internal.cuh"
+
+namespace mc {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int kBW = 16;  // warps per block-class block
+constexpr int kBT = kBW * 32;
+constexpr int kSW = 8;   // warps per warp-class block
+constexpr int kWarpCap = 128;
+constexpr int kPoolCap = 16;
+
+struct SA {
+  const int64_t *orow;
+  const int32_t *ocol, *ocore, *oold, *ogid;
+  const int32_t *roots;
+  int64_t nroots;
+  int32_t *best, *lock, *wit;
+  const int64_t *voff;
+  int32_t *err;
+  long long spin;
+  int32_t *next;            // root grab counter
+  uint32_t *stack;          // per-warp DFS stacks
+  int64_t stack_stride;     // words per warp stack
+  uint32_t *gmat;           // per-block global matrix (big class)
+  int64_t gmat_stride;      // words per block matrix
+  int32_t neigh_cores;
+  unsigned long long *counters;  // colored, branched, nodes, donations
+};
+
+template <int WPL>
+struct Bits {
+  uint32_t w[WPL];
+};
+
+template <int WPL>
+__device__ __forceinline__ void bzero(Bits<WPL> &b) {
+#pragma unroll
+  for (int k = 0; k < WPL; k++) b.w[k] = 0;
+}
+template <int WPL>
+__device__ __forceinline__ bool bany(const Bits<WPL> &b) {
+  uint32_t x = 0;
+#pragma unroll
+  for (int k = 0; k < WPL; k++) x |= b.w[k];
+  return __any_sync(FULL, x != 0);
+}
+template <int WPL>
+__device__ __forceinline__ int bcount(const Bits<WPL> &b) {
+  int c = 0;
+#pragma unroll
+  for (int k = 0; k < WPL; k++) c += __popc(b.w[k]);
+  return dev::warp_sum(c);
+}
+template <int WPL>
+__device__ __forceinline__ int blowest(const Bits<WPL> &b) {
+#pragma unroll
+  for (int k = 0; k < WPL; k++) {
+    unsigned m = __ballot_sync(FULL, b.w[k] != 0);
+    if (m) {
+      int l = __ffs(m) - 1;
+      uint32_t x = __shfl_sync(FULL, b.w[k], l);
+      return ((k * 32 + l) << 5) + __ffs(x) - 1;
+    }
+  }
+  return -1;
+}
+template <int WPL>
+__device__ __forceinline__ int bhighest(const Bits<WPL> &b) {
+#pragma unroll
+  for (int k = WPL - 1; k >= 0; k--) {
+    unsigned m = __ballot_sync(FULL, b.w[k] != 0);
+    if (m) {
+      int l = 31 - __clz(m);
+      uint32_t x = __shfl_sync(FULL, b.w[k], l);
+      return ((k * 32 + l) << 5) + 31 - __clz(x);
+    }
+  }
+  return -1;
+}
+template <int WPL>
+__device__ __forceinline__ void bclear(Bits<WPL> &b, int v) {
+  const int lane = threadIdx.x & 31, wi = v >> 5;
+  const uint32_t m = ~(1u << (v & 31));
+#pragma unroll
+  for (int k = 0; k < WPL; k++)
+    if ((wi >> 5) == k && (wi & 31) == lane) b.w[k] &= m;
+}
+template <int WPL>
+__device__ __forceinline__ void bset(Bits<WPL> &b, int v) {
+  const int lane = threadIdx.x & 31, wi = v >> 5;
+  const uint32_t m = 1u << (v & 31);
+#pragma unroll
+  for (int k = 0; k < WPL; k++)
+    if ((wi >> 5) == k && (wi & 31) == lane) b.w[k] |= m;
+}
+template <bool SM>
+__device__ __forceinline__ uint32_t rw(const uint32_t *A, int64_t i) {
+  if (SM) return A[i];
+  return __ldcg(A + i);
+}
+// b &= row v  (words >= W are zero)
+template <int WPL, bool SM>
+__device__ __forceinline__ void band_row(Bits<WPL> &b, const uint32_t *A, int Ws, int W, int v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < WPL; k++) {
+    int w = k * 32 + lane;
+    b.w[k] = (w < W) ? (b.w[k] & rw<SM>(A, (int64_t)v * Ws + w)) : 0u;
+  }
+}
+template <int WPL, bool SM>
+__device__ __forceinline__ void bandnot_row(Bits<WPL> &b, const uint32_t *A, int Ws, int W, int v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < WPL; k++) {
+    int w = k * 32 + lane;
+    if (w < W) b.w[k] &= ~rw<SM>(A, (int64_t)v * Ws + w);
+  }
+}
+
+// Greedy colouring of P in index order by independent-set extraction: colour
+// class c takes, in index order, every remaining vertex with no neighbour
+// already in class c.  (This is exactly the sequential greedy colouring.)
+// B receives the vertices with colour > kmin.  Returns the colour count.
+template <int WPL, bool SM>
+__device__ int color_ise(const uint32_t *A, int Ws, int W, const Bits<WPL> &P, int kmin, Bits<WPL> &B) {
+  Bits<WPL> U = P;
+  bzero(B);
+  int col = 0;
+  while (bany(U)) {
+    col++;
+    Bits<WPL> Q = U;
+    for (;;) {
+      int v = blowest(Q);
+      if (v < 0) break;
+      bclear(Q, v);
+      bclear(U, v);
+      if (col > kmin) bset(B, v);
+      bandnot_row<WPL, SM>(Q, A, Ws, W, v);
+    }
+  }
+  return col;
+}
+
+__device__ __forceinline__ int read_best(const int32_t *best, int g) {
+  int x = 0;
+  if ((threadIdx.x & 31) == 0) x = *(const volatile int32_t *)(best + g);
+  return __shfl_sync(FULL, x, 0);
+}
+
+__device__ __forceinline__ int hash_slot(int key, int mask) { return (int)(((unsigned)key * 2654435761u) >> 7) & mask; }
+
+__device__ __forceinline__ int hash_find(const int *hk, const short *hv, int mask, int key) {
+  int s = hash_slot(key, mask);
+  for (;;) {
+    int k = hk[s];
+    if (k == key) return hv[s];
+    if (k < 0) return -1;
+    s = (s + 1) & mask;
+  }
+}
+
+__device__ __forceinline__ void hash_insert(int *hk, short *hv, int mask, int key, int val) {
+  int s = hash_slot(key, mask);
+  for (;;) {
+    int prev = atomicCAS(hk + s, -1, key);
+    if (prev == -1 || prev == key) {
+      hv[s] = (short)val;
+      return;
+    }
+    s = (s + 1) & mask;
+  }
+}
+
+// bitonic sort (descending) of a[0..npow2) in shared memory by `nthr`
+// cooperating threads (thread index t); BLOCK selects the barrier.
+template <bool BLOCK>
+__device__ void bitonic_desc(int *a, int npow2, int t, int nthr) {
+  for (int k = 2; k <= npow2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = t; i < npow2; i += nthr) {
+        int ixj = i ^ j;
+        if (ixj > i) {
+          int x = a[i], y = a[ixj];
+          bool desc = (i & k) == 0;
+          if (desc ? (x < y) : (x > y)) {
+            a[i] = y;
+            a[ixj] = x;
+          }
+        }
+      }
+      if (BLOCK) __syncthreads(); else __syncwarp();
+    }
+  }
+}
+
+// Write the clique {u} + C (+ v) in original ids.  All lanes.
+template <int WPL>
+__device__ void write_clique(int32_t *base, const Bits<WPL> &C, int v, const int32_t *Pidx, const int32_t *oold,
+                             int u) {
+  const int lane = threadIdx.x & 31;
+  Bits<WPL> X = C;
+  if (v >= 0) bset(X, v);
+  int cnt = 0;
+#pragma unroll
+  for (int k = 0; k < WPL; k++) cnt += __popc(X.w[k]);
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += y;
+  }
+  int pos = 1 + incl - cnt;
+#pragma unroll
+  for (int k = 0; k < WPL; k++) {
+    uint32_t x = X.w[k];
+    while (x) {
+      int b = __ffs(x) - 1;
+      x &= x - 1;
+      int idx = ((k * 32 + lane) << 5) + b;
+      base[pos++] = oold[Pidx[idx]];
+    }
+  }
+  if (lane == 0) base[0] = oold[u];
+}
+
+// Shared-memory task pool of a block worker.
+template <int WPL>
+struct Pool {
+  int lock, count, idle, beat;
+  int csize[kPoolCap];
+  uint32_t C[kPoolCap][32 * WPL];
+  uint32_t P[kPoolCap][32 * WPL];
+};
+
+template <int WPL>
+__device__ bool pool_lock(Pool<WPL> *pl, int32_t *err, long long spin) {
+  long long it = 0;
+  while (atomicCAS(&pl->lock, 0, 1) != 0) {
+    if (++it > spin) {
+      atomicExch(err, kDevTimeout);
+      return false;
+    }
+    __nanosleep(32);
+  }
+  __threadfence_block();
+  return true;
+}
+template <int WPL>
+__device__ void pool_unlock(Pool<WPL> *pl) {
+  __threadfence_block();
+  atomicExch(&pl->lock, 0);
+}
+
+struct Root {
+  int u, g;
+  const int32_t *Pidx;
+};
+
+// Depth-first Branch from one level (csize0 = |C| including the root u).
+// Stack levels above the start hold (P, B, omega-at-colouring, chosen).
+// If `pool` is not null, untried branches are handed to idle warps.
+template <int WPL, bool SM>
+__device__ void dfs(const SA &a, const Root &r, const uint32_t *A, int Ws, int W, uint32_t *stk, int csize0,
+                    Bits<WPL> P, Bits<WPL> B, Bits<WPL> C, int wat, Pool<WPL> *pool, unsigned long long &nodes,
+                    unsigned long long &donations) {
+  const int lane = threadIdx.x & 31;
+  const int stride = 64 * WPL + 2;
+  int d = 0, csize = csize0;
+  for (;;) {
+    if (*(volatile int32_t *)a.err) return;
+    int om = read_best(a.best, r.g);
+    if (om > wat) {
+      color_ise<WPL, SM>(A, Ws, W, P, om - csize, B);
+      wat = om;
+    }
+    int v = bhighest(B);
+    if (v < 0) {
+      if (d == 0) return;
+      d--;
+      uint32_t *lv = stk + (int64_t)d * stride;
+#pragma unroll
+      for (int k = 0; k < WPL; k++) {
+        P.w[k] = lv[k * 32 + lane];
+        B.w[k] = lv[32 * WPL + k * 32 + lane];
+      }
+      wat = (int)lv[64 * WPL];
+      int ch = (int)lv[64 * WPL + 1];
+      bclear(C, ch);
+      csize--;
+      continue;
+    }
+    bclear(B, v);
+    bclear(P, v);
+    Bits<WPL> NP = P;
+    band_row<WPL, SM>(NP, A, Ws, W, v);
+    nodes++;
+    if (!bany(NP)) {
+      if (csize + 1 > om) {
+        const Bits<WPL> Cc = C;
+        dev::raise_incumbent(a.best, a.lock, a.wit, a.voff, r.g, csize + 1, a.err, a.spin,
+                             [&](int, int32_t *base) { write_clique<WPL>(base, Cc, v, r.Pidx, a.oold, r.u); });
+      }
+      continue;
+    }
+    if (csize + 1 + bcount(NP) <= om) continue;
+    Bits<WPL> NB;
+    color_ise<WPL, SM>(A, Ws, W, NP, om - csize - 1, NB);
+    if (!bany(NB)) continue;  // csize + 1 + L <= omega
+    // descend: save this level
+    uint32_t *lv = stk + (int64_t)d * stride;
+#pragma unroll
+    for (int k = 0; k < WPL; k++) {
+      lv[k * 32 + lane] = P.w[k];
+      lv[32 * WPL + k * 32 + lane] = B.w[k];
+    }
+    if (lane == 0) {
+      lv[64 * WPL] = (uint32_t)wat;
+      lv[64 * WPL + 1] = (uint32_t)v;
+    }
+    d++;
+    bset(C, v);
+    csize++;
+    P = NP;
+    B = NB;
+    wat = om;
+
+    // hand the shallowest untried branch to an idle warp of the block
+    if (pool) {
+      if (lane == 0) atomicAdd(&pool->beat, 1);  // progress signal for waiting warps
+      int hungry = 0;
+      if (lane == 0) {
+        int idle = *(volatile int *)&pool->idle, cnt = *(volatile int *)&pool->count;
+        hungry = idle > 0 && cnt < idle && cnt < kPoolCap;
+      }
+      hungry = __shfl_sync(FULL, hungry, 0);
+      if (hungry) {
+        __syncwarp();
+        // shallowest stored level with an untried branch (levels 0..d-1 are in memory)
+        int lev = -1;
+        Bits<WPL> Bl, Pl;
+        for (int l = 0; l < d; l++) {
+          uint32_t *q = stk + (int64_t)l * stride;
+#pragma unroll
+          for (int k = 0; k < WPL; k++) Bl.w[k] = q[32 * WPL + k * 32 + lane];
+          if (bany(Bl)) {
+            lev = l;
+            break;
+          }
+        }
+        if (lev >= 0) {
+          uint32_t *q = stk + (int64_t)lev * stride;
+#pragma unroll
+          for (int k = 0; k < WPL; k++) Pl.w[k] = q[k * 32 + lane];
+          int x = bhighest(Bl);
+          bclear(Bl, x);
+          bclear(Pl, x);
+#pragma unroll
+          for (int k = 0; k < WPL; k++) {
+            q[k * 32 + lane] = Pl.w[k];
+            q[32 * WPL + k * 32 + lane] = Bl.w[k];
+          }
+          // clique at level lev: C minus the vertices chosen at levels >= lev
+          Bits<WPL> Cl = C;
+          for (int l = lev; l < d; l++) bclear(Cl, (int)stk[(int64_t)l * stride + 64 * WPL + 1]);
+          bset(Cl, x);
+          Bits<WPL> TP = Pl;
+          band_row<WPL, SM>(TP, A, Ws, W, x);
+          int tcs = csize0 + lev + 1;
+          int om2 = read_best(a.best, r.g);
+          if (bany(TP) && tcs + bcount(TP) > om2) {
+            int ok = 0;
+            if (lane == 0) {
+              if (pool_lock(pool, a.err, a.spin)) {
+                if (pool->count < kPoolCap) ok = 1 + pool->count++;
+                else pool_unlock(pool);
+              }
+            }
+            ok = __shfl_sync(FULL, ok, 0);
+            if (ok) {
+              int slot = ok - 1;
+#pragma unroll
+              for (int k = 0; k < WPL; k++) {
+                pool->C[slot][k * 32 + lane] = Cl.w[k];
+                pool->P[slot][k * 32 + lane] = TP.w[k];
+              }
+              if (lane == 0) {
+                pool->csize[slot] = tcs;
+                pool_unlock(pool);
+              }
+              donations++;
+            } else {
+              // pool full: search the branch here, later, by restoring it
+              bset(Bl, x);
+              bset(Pl, x);
+#pragma unroll
+              for (int k = 0; k < WPL; k++) {
+                q[k * 32 + lane] = Pl.w[k];
+                q[32 * WPL + k * 32 + lane] = Bl.w[k];
+              }
+            }
+          } else if (!bany(TP) && tcs > om2) {
+            // nothing left to add: {u} + Cl is maximal and beats the incumbent
+            const Bits<WPL> Cc = Cl;
+            dev::raise_incumbent(a.best, a.lock, a.wit, a.voff, r.g, tcs, a.err, a.spin,
+                                 [&](int, int32_t *base) { write_clique<WPL>(base, Cc, -1, r.Pidx, a.oold, r.u); });
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+}
+
+// Load P = {w in N+(u) : K(w) >= om} into Pidx (unsorted).  Cooperative over
+// nthr threads; *cnt is a shared counter (pre-zeroed).  Reads rows as int4.
+__device__ __forceinline__ void load_P(const SA &a, int u, int om, int *Pidx, int cap, int *cnt, int t, int nthr) {
+  const int64_t e0 = a.orow[u], e1 = a.orow[u + 1];
+  const int4 *row = reinterpret_cast<const int4 *>(a.ocol + e0);
+  const int64_t nq = (e1 - e0) >> 2;
+  for (int64_t q = t; q < nq; q += nthr) {
+    int4 y = __ldg(row + q);
+    int ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      if (ys[j] >= 0 && __ldg(a.ocore + ys[j]) >= om) {
+        int p = atomicAdd(cnt, 1);
+        if (p < cap) Pidx[p] = ys[j];
+      }
+    }
+  }
+}
+
+// Matrix rows of P: for each member x (index i), every later neighbour y of x
+// that is in P (index j) sets bits (i, j) and (j, i).
+__device__ __forceinline__ void build_rows(const SA &a, const int *Pidx, int p, const int *hk, const short *hv,
+                                           int hmask, uint32_t *A, int Ws, int wid, int nw) {
+  const int lane = threadIdx.x & 31;
+  for (int i = wid; i < p; i += nw) {
+    const int x = Pidx[i];
+    const int64_t e0 = a.orow[x], e1 = a.orow[x + 1];
+    const int4 *row = reinterpret_cast<const int4 *>(a.ocol + e0);
+    const int64_t nq = (e1 - e0) >> 2;
+    for (int64_t q = lane; q < nq; q += 32) {
+      int4 y = __ldg(row + q);
+      int ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        if (ys[j] < 0) continue;
+        int b = hash_find(hk, hv, hmask, ys[j]);
+        if (b >= 0) {
+          atomicOr(A + (int64_t)i * Ws + (b >> 5), 1u << (b & 31));
+          atomicOr(A + (int64_t)b * Ws + (i >> 5), 1u << (i & 31));
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------ warp class ---
+
+struct WarpSmem {
+  int Pidx[kWarpCap];
+  int hk[2 * kWarpCap];
+  short hv[2 * kWarpCap];
+  uint32_t A[kWarpCap * 5];
+  uint32_t al[4];
+  int cnt;
+};
+
+__global__ void __launch_bounds__(kSW * 32) search_warp_kernel(SA a) {
+  __shared__ WarpSmem sm[kSW];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  WarpSmem &S = sm[wib];
+  const int64_t gw = (int64_t)blockIdx.x * kSW + wib;
+  uint32_t *stk = a.stack + gw * a.stack_stride;
+  unsigned long long colored = 0, branched = 0, nodes = 0, don = 0;
+  const int hmask = 2 * kWarpCap - 1;
+  for (;;) {
+    __syncwarp();
+    int idx = 0;
+    if (lane == 0) idx = atomicAdd(a.next, 1);
+    idx = __shfl_sync(FULL, idx, 0);
+    if (idx >= a.nroots || *(volatile int32_t *)a.err) break;
+    const int u = a.roots[idx];
+    const int g = a.ogid ? a.ogid[u] : 0;
+    int om = read_best(a.best, g);
+    if (a.ocore[u] < om) continue;
+    if (lane == 0) S.cnt = 0;
+    for (int i = lane; i < 2 * kWarpCap; i += 32) S.hk[i] = -1;
+    for (int i = lane; i < kWarpCap; i += 32) S.Pidx[i] = INT_MIN;
+    __syncwarp();
+    load_P(a, u, om, S.Pidx, kWarpCap, &S.cnt, lane, 32);
+    __syncwarp();
+    const int p = S.cnt;
+    if (p > kWarpCap) {
+      if (lane == 0) atomicExch(a.err, kDevCheck);
+      break;
+    }
+    if (p < om || p == 0) continue;
+    int np2 = 32;
+    while (np2 < p) np2 <<= 1;
+    bitonic_desc<false>(S.Pidx, np2, lane, 32);
+    for (int i = lane; i < p; i += 32) hash_insert(S.hk, S.hv, hmask, S.Pidx[i], i);
+    const int W = (p + 31) >> 5, Ws = W | 1;
+    for (int i = lane; i < p * Ws; i += 32) S.A[i] = 0;
+    __syncwarp();
+    build_rows(a, S.Pidx, p, S.hk, S.hv, hmask, S.A, Ws, 0, 1);
+    __syncwarp();
+    // alive set = all p vertices; (omega-1)-core of G[P]
+    if (lane < 4) S.al[lane] = (lane < W) ? ((lane == W - 1 && (p & 31)) ? ((1u << (p & 31)) - 1u) : FULL) : 0u;
+    __syncwarp();
+    om = read_best(a.best, g);
+    if (a.neigh_cores) {
+      for (;;) {
+        // lanes own rows k*32 + lane; row i's live bit is bit (i & 31) of word i >> 5
+        uint32_t rm[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          if (k < W) {
+            int i = k * 32 + lane;
+            bool live = i < p && ((S.al[k] >> lane) & 1u);
+            int deg = 0;
+            if (live)
+              for (int w = 0; w < W; w++) deg += __popc(S.A[i * Ws + w] & S.al[w]);
+            rm[k] = __ballot_sync(FULL, live && deg < om - 1);
+          }
+        }
+        __syncwarp();
+        bool ch = (rm[0] | rm[1] | rm[2] | rm[3]) != 0;
+        if (lane < 4) {
+          uint32_t mine = lane == 0 ? rm[0] : lane == 1 ? rm[1] : lane == 2 ? rm[2] : rm[3];
+          S.al[lane] &= ~mine;
+        }
+        __syncwarp();
+        if (!ch) break;
+      }
+    }
+    Bits<1> al;
+    al.w[0] = (lane < 4) ? S.al[lane] : 0u;
+    if (a.neigh_cores && bcount(al) < om) continue;
+    colored++;
+    Bits<1> B;
+    color_ise<1, true>(S.A, Ws, W, al, om - 1, B);
+    if (!bany(B)) continue;
+    branched++;
+    Bits<1> C;
+    bzero(C);
+    Root r{u, g, S.Pidx};
+    dfs<1, true>(a, r, S.A, Ws, W, stk, 1, al, B, C, om, (Pool<1> *)nullptr, nodes, don);
+  }
+  if (lane == 0) {
+    atomicAdd(a.counters + 0, colored);
+    atomicAdd(a.counters + 1, branched);
+    atomicAdd(a.counters + 2, nodes);
+  }
+}
+
+// ----------------------------------------------------------- block class ---
+
+template <int WPL, bool SM>
+struct BlockLayout {
+  static constexpr int PCAP = 1024 * WPL;
+  static constexpr int HCAP = 2 * PCAP;
+  static constexpr int WMAX = 32 * WPL;
+  static constexpr int WSMAX = WMAX + 1;
+  // bytes: Pidx, hk, hv, alive/rm words, pool, control, matrix
+  static constexpr size_t off_P = 0;
+  static constexpr size_t off_hk = off_P + PCAP * 4;
+  static constexpr size_t off_hv = off_hk + HCAP * 4;
+  static constexpr size_t off_al = off_hv + HCAP * 2;
+  static constexpr size_t off_rm = off_al + WMAX * 4;
+  static constexpr size_t off_pool = off_rm + WMAX * 4;
+  static constexpr size_t off_ctl = off_pool + ((sizeof(Pool<WPL>) + 15) / 16) * 16;
+  static constexpr size_t off_A = off_ctl + 64;
+  static constexpr size_t bytes = off_A + (SM ? (size_t)PCAP * WSMAX * 4 : 0);
+};
+
+template <int WPL, bool SM>
+__global__ void __launch_bounds__(kBT) search_block_kernel(SA a) {
+  using L = BlockLayout<WPL, SM>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  int *Pidx = (int *)(smem + L::off_P);
+  int *hk = (int *)(smem + L::off_hk);
+  short *hv = (short *)(smem + L::off_hv);
+  uint32_t *al = (uint32_t *)(smem + L::off_al);
+  uint32_t *rm = (uint32_t *)(smem + L::off_rm);
+  Pool<WPL> *pool = (Pool<WPL> *)(smem + L::off_pool);
+  int *ctl = (int *)(smem + L::off_ctl);  // [0] root idx, [1] omega, [2] count, [3] flag, [4] go
+  uint32_t *A = SM ? (uint32_t *)(smem + L::off_A) : (a.gmat + (int64_t)blockIdx.x * a.gmat_stride);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  uint32_t *stk = a.stack + ((int64_t)blockIdx.x * kBW + wid) * a.stack_stride;
+  unsigned long long colored = 0, branched = 0, nodes = 0, don = 0;
+  const int hmask = L::HCAP - 1;
+
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) {
+      ctl[0] = atomicAdd(a.next, 1);
+      ctl[2] = 0;
+    }
+    __syncthreads();
+    const int idx = ctl[0];
+    if (idx >= a.nroots || *(volatile int32_t *)a.err) break;
+    const int u = a.roots[idx];
+    const int g = a.ogid ? a.ogid[u] : 0;
+    if (tid == 0) ctl[1] = *(volatile int32_t *)(a.best + g);
+    __syncthreads();
+    int om = ctl[1];
+    if (a.ocore[u] < om) continue;
+    for (int i = tid; i < L::HCAP; i += kBT) hk[i] = -1;
+    for (int i = tid; i < L::PCAP; i += kBT) Pidx[i] = INT_MIN;
+    __syncthreads();
+    load_P(a, u, om, Pidx, L::PCAP, &ctl[2], tid, kBT);
+    __syncthreads();
+    const int p = ctl[2];
+    if (p > L::PCAP) {
+      if (tid == 0) atomicExch(a.err, kDevUnsupported);
+      break;
+    }
+    if (p < om || p == 0) continue;
+    int np2 = 32;
+    while (np2 < p) np2 <<= 1;
+    bitonic_desc<true>(Pidx, np2, tid, kBT);
+    for (int i = tid; i < p; i += kBT) hash_insert(hk, hv, hmask, Pidx[i], i);
+    const int W = (p + 31) >> 5, Ws = W | 1;
+    for (int64_t i = tid; i < (int64_t)p * Ws; i += kBT) A[i] = 0;
+    if (!SM) __threadfence();
+    __syncthreads();
+    build_rows(a, Pidx, p, hk, hv, hmask, A, Ws, wid, kBW);
+    if (!SM) __threadfence();
+    __syncthreads();
+    for (int w = tid; w < L::WMAX; w += kBT)
+      al[w] = (w < W) ? ((w == W - 1 && (p & 31)) ? ((1u << (p & 31)) - 1u) : FULL) : 0u;
+    if (tid == 0) ctl[1] = *(volatile int32_t *)(a.best + g);
+    __syncthreads();
+    om = ctl[1];
+    if (a.neigh_cores) {
+      // (omega-1)-core of G[P]: drop rows with fewer than omega-1 live neighbours
+      for (;;) {
+        for (int k = wid; k < W; k += kBW) {
+          int i = k * 32 + lane;
+          int deg = 0;
+          bool live = i < p && ((al[k] >> lane) & 1u);
+          if (live)
+            for (int w = 0; w < W; w++) deg += __popc(rw<SM>(A, (int64_t)i * Ws + w) & al[w]);
+          unsigned m = __ballot_sync(FULL, live && deg < om - 1);
+          if (lane == 0) rm[k] = m;
+        }
+        if (tid == 0) ctl[3] = 0;
+        __syncthreads();
+        for (int k = tid; k < W; k += kBT)
+          if (rm[k]) {
+            al[k] &= ~rm[k];
+            ctl[3] = 1;
+          }
+        __syncthreads();
+        if (!ctl[3]) break;
+        __syncthreads();
+      }
+    }
+    // colouring test and the search, started by warp 0
+    Root r{u, g, Pidx};
+    Bits<WPL> P, B, C;
+    bzero(C);
+    int cs = 1, wat = om;
+    bool have = false;
+    if (wid == 0) {
+#pragma unroll
+      for (int k = 0; k < WPL; k++) P.w[k] = al[k * 32 + lane];
+      int go = 0;
+      if (!a.neigh_cores || bcount(P) >= om) {
+        colored++;
+        color_ise<WPL, SM>(A, Ws, W, P, om - 1, B);
+        go = bany(B) ? 1 : 0;
+        if (go) branched++;
+      }
+      have = go != 0;
+      if (lane == 0) {
+        ctl[4] = go;
+        pool->lock = 0;
+        pool->count = 0;
+        pool->idle = kBW - 1;
+        pool->beat = 0;
+      }
+    }
+    __syncthreads();
+    if (!ctl[4]) continue;
+    long long waited = 0;
+    int lastbeat = -1;
+    for (;;) {
+      if (have) {
+        dfs<WPL, SM>(a, r, A, Ws, W, stk, cs, P, B, C, wat, pool, nodes, don);
+        have = false;
+        if (lane == 0) {
+          if (pool_lock(pool, a.err, a.spin)) {
+            pool->idle++;
+            pool_unlock(pool);
+          }
+        }
+        __syncwarp();
+      }
+      int got = 0;
+      if (lane == 0) {
+        if (pool_lock(pool, a.err, a.spin)) {
+          if (pool->count > 0) {
+            got = pool->count--;
+            pool->idle--;
+          } else if (pool->idle == kBW) {
+            got = -1;
+          }
+          if (got <= 0) pool_unlock(pool);
+        } else {
+          got = -1;
+        }
+      }
+      got = __shfl_sync(FULL, got, 0);
+      if (got < 0) break;
+      if (got == 0) {
+        int beat = *(volatile int *)&pool->beat;
+        if (beat != lastbeat) {
+          lastbeat = beat;
+          waited = 0;
+        }
+        if (++waited > a.spin || *(volatile int32_t *)a.err) {
+          if (lane == 0) atomicExch(a.err, kDevTimeout);
+          break;
+        }
+        __nanosleep(128);
+        continue;
+      }
+      // copy the task while still holding the lock (lane 0 holds it)
+      const int slot = got - 1;
+#pragma unroll
+      for (int k = 0; k < WPL; k++) {
+        C.w[k] = pool->C[slot][k * 32 + lane];
+        P.w[k] = pool->P[slot][k * 32 + lane];
+      }
+      cs = pool->csize[slot];
+      __syncwarp();
+      if (lane == 0) pool_unlock(pool);
+      __syncwarp();
+      int om2 = read_best(a.best, g);
+      color_ise<WPL, SM>(A, Ws, W, P, om2 - cs, B);
+      wat = om2;
+      have = bany(B);
+      if (!have && lane == 0) {
+        if (pool_lock(pool, a.err, a.spin)) {
+          pool->idle++;
+          pool_unlock(pool);
+        }
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+  if (lane == 0) {
+    atomicAdd(a.counters + 0, colored);
+    atomicAdd(a.counters + 1, branched);
+    atomicAdd(a.counters + 2, nodes);
+    atomicAdd(a.counters + 3, don);
+  }
+}
+
+}  // namespace
+
+int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, long long spin_limit, SearchCounters *cnt) {
+  void *p;
+  MC_TRY(ws_get(g, "se.ctr", 16 * sizeof(unsigned long long), &p));
+  unsigned long long *ctr = (unsigned long long *)p;
+  int32_t *next = (int32_t *)(ctr + 8);
+  MC_CUDA_TRY(cudaMemsetAsync(ctr, 0, 16 * sizeof(unsigned long long), g->stream));
+  SA a{};
+  a.orow = pg.orow;
+  a.ocol = pg.ocol;
+  a.ocore = pg.ocore;
+  a.oold = pg.oold;
+  a.ogid = pg.ogid;
+  a.best = g->best;
+  a.lock = g->lock;
+  a.wit = g->wit;
+  a.voff = g->gid ? g->voff : nullptr;
+  a.err = g->err;
+  a.spin = spin_limit;
+  a.neigh_cores = no_neigh_cores ? 0 : 1;
+  a.counters = ctr;
+
+  // block class first (largest trees), then big, then warp class
+  if (pg.nroots_block > 0) {
+    using L = BlockLayout<1, true>;
+    const size_t smem = L::bytes;
+    MC_CUDA_TRY(cudaFuncSetAttribute(search_block_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    int per_sm = 0;
+    MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_block_kernel<1, true>, kBT, smem));
+    if (per_sm < 1) return MC_ERR_CUDA;
+    int blocks = (int)std::min<int64_t>(pg.nroots_block, (int64_t)g->sm_count * per_sm);
+    const int pmax = std::min(pg.max_out, 1024);
+    a.stack_stride = (int64_t)(pmax + 2) * (64 + 2);
+    MC_TRY(ws_get(g, "se.stk_b", (size_t)blocks * kBW * a.stack_stride * 4, &p));
+    a.stack = (uint32_t *)p;
+    a.gmat = nullptr;
+    a.roots = pg.roots_block;
+    a.nroots = pg.nroots_block;
+    a.next = next + 0;
+    search_block_kernel<1, true><<<blocks, kBT, smem, g->stream>>>(a);
+    g_launches++;
+    MC_CUDA_TRY(cudaGetLastError());
+  }
+  if (pg.nroots_big > 0) {
+    if (pg.max_out > 4096) return MC_ERR_UNSUPPORTED;
+    using L = BlockLayout<4, false>;
+    const size_t smem = L::bytes;
+    MC_CUDA_TRY(cudaFuncSetAttribute(search_block_kernel<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    int blocks = (int)std::min<int64_t>(pg.nroots_big, (int64_t)g->sm_count);
+    const int pmax = pg.max_out;
+    a.stack_stride = (int64_t)(pmax + 2) * (64 * 4 + 2);
+    MC_TRY(ws_get(g, "se.stk_g", (size_t)blocks * kBW * a.stack_stride * 4, &p));
+    a.stack = (uint32_t *)p;
+    const int Wm = (pmax + 31) / 32;
+    a.gmat_stride = (int64_t)pmax * (Wm | 1) + 64;
+    MC_TRY(ws_get(g, "se.gmat", (size_t)blocks * a.gmat_stride * 4, &p));
+    a.gmat = (uint32_t *)p;
+    a.roots = pg.roots_big;
+    a.nroots = pg.nroots_big;
+    a.next = next + 1;
+    search_block_kernel<4, false><<<blocks, kBT, smem, g->stream>>>(a);
+    g_launches++;
+    MC_CUDA_TRY(cudaGetLastError());
+  }
+  if (pg.nroots_small > 0) {
+    int per_sm = 0;
+    MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_warp_kernel, kSW * 32, 0));
+    if (per_sm < 1) return MC_ERR_CUDA;
+    int blocks = (int)std::min<int64_t>((pg.nroots_small + kSW - 1) / kSW, (int64_t)g->sm_count * per_sm);
+    const int pmax = std::min(pg.max_out, kWarpCap);
+    a.stack_stride = (int64_t)(pmax + 2) * (64 + 2);
+    MC_TRY(ws_get(g, "se.stk_w", (size_t)blocks * kSW * a.stack_stride * 4, &p));
+    a.stack = (uint32_t *)p;
+    a.roots = pg.roots_small;
+    a.nroots = pg.nroots_small;
+    a.next = next + 2;
+    search_warp_kernel<<<blocks, kSW * 32, 0, g->stream>>>(a);
+    g_launches++;
+    MC_CUDA_TRY(cudaGetLastError());
+  }
+  unsigned long long *h = (unsigned long long *)g->h_small;
+  MC_CUDA_TRY(cudaMemcpyAsync(h, ctr, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, g->stream));
+  MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  cnt->roots_colored = h[0];
+  cnt->roots_branched = h[1];
+  cnt->nodes = h[2];
+  cnt->donations = h[3];
+  return MC_OK;
+}
+
+}  // namespace mc

@@ -1,0 +1,52 @@
+"""The C ABI library builds for sm_103a, loads, and exports every function
+that include/mc.h declares (no GPU needed: nothing is called)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for f in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(mc_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_header_declares_the_method_calls():
+    names = declared_functions()
+    for want in ("mc_load_csr", "mc_core_numbers", "mc_heuristic_clique", "mc_max_clique", "mc_free",
+                 "mc_strerror", "mc_max_clique_batch", "mc_load_batch"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1302_6256_gb300 import _build
+    path = _build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_strerror_and_version_without_gpu():
+    import paper_1302_6256_gb300 as mc
+    L = mc.load_library()
+    assert L.mc_strerror(mc.MC_ERR_BUFFER).decode() == "output buffer too small"
+    assert L.mc_version() >= 100
+
+
+def test_no_cpu_fallback_in_product_package():
+    """The package never imports the oracle or the generators."""
+    pkg = os.path.join(ROOT, "paper_1302_6256_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in src and "from oracle" not in src, f
+                assert "orc_" not in src, f

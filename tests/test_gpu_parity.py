@@ -1,0 +1,226 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Core numbers and omega are unique, so they must match bit for bit; every
+witness must be a clique of size omega (several maximum cliques may exist, so
+witnesses are checked for validity, not compared).  The deterministic
+heuristic must return exactly the oracle's clique.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def mc():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    import paper_1302_6256_gb300 as m
+    m.load_library()
+    return m
+
+
+_REF = {}
+
+
+def ref_omega(g):
+    """Oracle omega, computed once per graph."""
+    if g.name not in _REF:
+        _REF[g.name] = oracle.max_clique(g)[0]
+    return _REF[g.name]
+
+
+def load(mc, g, device=True, flags=None):
+    if flags is None:
+        flags = mc.MC_VALIDATE
+    if device:
+        return mc.mc_load_csr(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col_idx).cuda(), flags)
+    return mc.mc_load_csr(g.row_ptr, g.col_idx, flags)
+
+
+def small_graphs():
+    out = [gg.empty(0), gg.empty(1), gg.empty(7), gg.complete(2), gg.complete(33), gg.cycle(3), gg.cycle(10),
+           gg.path(9), gg.star(50), gg.petersen(), gg.complete_bipartite(5, 8), gg.turan(40, 6), gg.turan(130, 9),
+           gg.disjoint_cliques([4, 17, 9, 17]), gg.mycielski(5), gg.mycielski(7)]
+    for s in range(12):
+        out.append(gg.random_small(5 + s, 0.2 + 0.06 * s, 500 + s))
+    return out
+
+
+def medium_graphs():
+    """Sizes that span warp-class (|N+| <= 128) and block-class roots, ragged
+    bit words, and several tiles."""
+    return [
+        gg.erdos_renyi(200, 0.5, planted=0, seed=11),
+        gg.erdos_renyi(400, 0.3, planted=20, seed=12),
+        gg.erdos_renyi(300, 0.6, planted=0, seed=13),
+        gg.erdos_renyi(400, 0.5, planted=0, seed=19),
+        gg.erdos_renyi(3000, 0.01, planted=25, seed=14),
+        gg.chung_lu(20000, 2.3, 12.0, 800.0, planted=18, seed=15),
+        gg.rmat(14, 16, planted=30, seed=16),
+        gg.rmat(16, 16, planted=35, seed=17),
+        gg.relabel(gg.turan(300, 33), 3),
+    ]
+
+
+@pytest.mark.parametrize("g", small_graphs() + medium_graphs(), ids=lambda g: g.name)
+def test_core_numbers_bit_exact(mc, g):
+    h = load(mc, g)
+    core, kmax = mc.mc_core_numbers(h)
+    ref = oracle.core_numbers(g)
+    assert np.array_equal(core, ref)
+    assert kmax == (int(ref.max()) if g.n else 0)
+
+
+@pytest.mark.parametrize("g", small_graphs() + medium_graphs(), ids=lambda g: g.name)
+def test_max_clique_matches_oracle(mc, g):
+    h = load(mc, g)
+    om, wit, st = mc.mc_max_clique(h)
+    assert om == ref_omega(g)
+    assert len(wit) == om and oracle.is_clique(g, wit)
+    assert list(wit) == sorted(wit)
+    assert st["verified"] == 1
+
+
+@pytest.mark.parametrize("g", medium_graphs(), ids=lambda g: g.name)
+def test_heuristic_deterministic_bit_exact(mc, g):
+    h = load(mc, g)
+    H = mc.mc_heuristic_clique(h, mode=1)
+    ref = oracle.heuristic_clique(g, mode=1)
+    assert np.array_equal(H, ref)
+
+
+@pytest.mark.parametrize("g", medium_graphs()[:6], ids=lambda g: g.name)
+def test_heuristic_racy_is_valid(mc, g):
+    h = load(mc, g)
+    om = ref_omega(g)
+    H = mc.mc_heuristic_clique(h, mode=0)
+    assert 1 <= len(H) <= om and oracle.is_clique(g, H)
+
+
+@pytest.mark.parametrize("opts", [dict(ordering=2), dict(no_neigh_cores=True), dict(heuristic=1),
+                                  dict(heuristic=2), dict(warp_max=16), dict(warp_max=1)],
+                         ids=lambda o: ",".join("%s=%s" % kv for kv in o.items()))
+def test_options_keep_omega(mc, opts):
+    for g in medium_graphs()[:6]:
+        h = load(mc, g)
+        om, wit, _ = mc.mc_max_clique(h, **opts)
+        assert om == ref_omega(g), g.name
+        assert oracle.is_clique(g, wit)
+
+
+def test_host_pointers_and_repeat_calls(mc):
+    g = gg.chung_lu(5000, 2.4, 10.0, 500.0, planted=14, seed=21)
+    h = load(mc, g, device=False)
+    ref = oracle.max_clique(g)[0]
+    for _ in range(3):
+        om, wit, _ = mc.mc_max_clique(h)
+        assert om == ref and oracle.is_clique(g, wit)
+
+
+def test_device_witness_buffer(mc):
+    g = gg.erdos_renyi(500, 0.2, planted=16, seed=22)
+    h = load(mc, g)
+    out = torch.zeros(600, dtype=torch.int32, device="cuda")
+    om, wit, _ = mc.mc_max_clique(h, witness_out=out)
+    assert om == oracle.max_clique(g)[0]
+    assert oracle.is_clique(g, wit.cpu().numpy())
+
+
+def test_batch_matches_oracle(mc):
+    b = gg.er_batch(48, seed=3)
+    h = mc.mc_load_batch(torch.from_numpy(b.voff).cuda(), torch.from_numpy(b.row_ptr).cuda(),
+                         torch.from_numpy(b.col_idx).cuda(), mc.MC_VALIDATE)
+    om, wits, st = mc.mc_max_clique_batch(h)
+    for i, g in enumerate(b.graphs):
+        ref = oracle.max_clique(g)[0]
+        assert om[i] == ref, (i, g.name)
+        assert len(wits[i]) == om[i] and oracle.is_clique(g, wits[i])
+    core, _ = mc.mc_core_numbers(h)
+    ref_core = np.concatenate([oracle.core_numbers(g) for g in b.graphs])
+    assert np.array_equal(core, ref_core)
+
+
+def test_batch_equals_single_calls(mc):
+    b = gg.er_batch(16, seed=9)
+    h = mc.mc_load_batch(b.voff, b.row_ptr, b.col_idx)
+    om, _, _ = mc.mc_max_clique_batch(h)
+    for i, g in enumerate(b.graphs):
+        assert om[i] == mc.mc_max_clique(load(mc, g))[0]
+
+
+def test_invalid_graph_rejected(mc):
+    # asymmetric: 0->1 without 1->0
+    rp = np.array([0, 1, 1], np.int64)
+    ci = np.array([1], np.int32)
+    with pytest.raises(mc.MCError) as e:
+        mc.mc_load_csr(rp, ci, mc.MC_VALIDATE)
+    assert e.value.code == mc.MC_ERR_INVALID_GRAPH
+    # self loop
+    rp = np.array([0, 2, 3], np.int64)
+    ci = np.array([0, 1, 0], np.int32)
+    with pytest.raises(mc.MCError):
+        mc.mc_load_csr(rp, ci, mc.MC_VALIDATE)
+
+
+def test_buffer_too_small_reports_size(mc):
+    g = gg.complete(20)
+    h = load(mc, g)
+    with pytest.raises(mc.MCError) as e:
+        mc.mc_max_clique(h, witness_out=np.zeros(5, np.int32))
+    assert e.value.code == mc.MC_ERR_BUFFER
+
+
+def test_spin_limit_timeout_is_reported_and_context_survives(mc):
+    """A device wait that runs out returns MC_ERR_TIMEOUT (no fault), and the
+    next call on the same context works."""
+    g = gg.rmat(14, 16, planted=20, seed=5)
+    h = load(mc, g)
+    with pytest.raises(mc.MCError) as e:
+        mc.mc_max_clique(h, spin_limit=1)
+    assert e.value.code == mc.MC_ERR_TIMEOUT
+    h2 = load(mc, g)
+    om, wit, _ = mc.mc_max_clique(h2)
+    assert om == oracle.max_clique(g)[0]
+
+
+def test_chung_lu_20k_golden(mc):
+    from graphgen import workloads as W
+    gold = json.load(open(os.path.join(HERE, "golden", "chung-lu-20k.json")))
+    g = W.chung_lu_20k()
+    assert g.n == gold["n"] and g.m == gold["m"]
+    h = load(mc, g)
+    core, kmax = mc.mc_core_numbers(h)
+    import hashlib
+    assert hashlib.sha256(core.astype("<i4").tobytes()).hexdigest() == gold["core_sha256"]
+    om, wit, _ = mc.mc_max_clique(h)
+    assert om == gold["omega"]
+    assert oracle.is_clique(g, wit)
+
+
+def test_rmat_s22_golden(mc):
+    """The benchmark's workload at full size, in the benchmark's launch
+    configuration: omega and the core-number hash against the stored oracle run."""
+    path = os.path.join(HERE, "golden", "rmat-s22.json")
+    if not os.path.exists(path):
+        pytest.skip("oracle golden file for rmat-s22 not generated")
+    from graphgen import workloads as W
+    import hashlib
+    gold = json.load(open(path))
+    g = W.rmat_s22()
+    assert g.n == gold["n"] and g.m == gold["m"]
+    h = load(mc, g, flags=0)
+    core, kmax = mc.mc_core_numbers(h)
+    assert hashlib.sha256(core.astype("<i4").tobytes()).hexdigest() == gold["core_sha256"]
+    om, wit, st = mc.mc_max_clique(h)
+    assert om == gold["omega"]
+    assert oracle.is_clique(g, wit)
