@@ -229,6 +229,8 @@ static int run_max_clique(mc_graph *g, const mc_options *opt, mc_stats *st) {
   st->n = g->n;
   st->edges = g->nnz / 2;
   MC_CUDA_TRY(cudaEventRecord(g->ev[0], g->stream));
+  // every solve recomputes the core numbers (Algorithm 2, line 2)
+  g->cores_valid = false;
   MC_TRY(ensure_cores(g, spin));
   MC_CUDA_TRY(cudaEventRecord(g->ev[1], g->stream));
   MC_CUDA_TRY(cudaMemsetAsync(g->best, 0, g->count * 4, g->stream));
@@ -256,6 +258,8 @@ static int run_max_clique(mc_graph *g, const mc_options *opt, mc_stats *st) {
   }
   if (o.heuristic != 2 && g->n > 0) MC_TRY(launch_heuristic(g, o.heuristic, spin, d_seeds, nseeds));
   MC_CUDA_TRY(cudaEventRecord(g->ev[2], g->stream));
+  int32_t *h_heur = (int32_t *)((char *)g->h_small + 1024);
+  MC_CUDA_TRY(cudaMemcpyAsync(h_heur, g->best, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
   Pruned pg;
   if (g->n > 0) MC_TRY(launch_prune(g, o.ordering, d_scores, warp_max, &pg, spin));
   MC_CUDA_TRY(cudaEventRecord(g->ev[3], g->stream));
@@ -286,6 +290,8 @@ static int run_max_clique(mc_graph *g, const mc_options *opt, mc_stats *st) {
   st->nodes = (int64_t)sc.nodes;
   st->donations = (int64_t)sc.donations;
   st->max_core = g->max_core;
+  g->heur0 = *h_heur;  // the stream has been synchronised since the copy
+  st->heuristic_size = g->heur0;
   // all witnesses must verify
   std::vector<int32_t> ok(g->count);
   MC_CUDA_TRY(cudaMemcpy(ok.data(), d_ok, g->count * 4, cudaMemcpyDeviceToHost));

@@ -6,7 +6,8 @@
 // then grows C = {v} greedily: the next member is the remaining candidate of
 // largest core number (ties: larger degree, then smaller id), and the
 // candidates are filtered to that member's neighbours (binary search in its
-// sorted CSR row).  Taking the first remaining candidate each time is the
+// sorted CSR row, or a warp-cooperative merge when the candidate list is long
+// compared with the row).  Taking the first remaining candidate each time is the
 // same as Algorithm 1's scan "add u if C + u is still a clique" in that order.
 //
 // mode 0 (Algorithm 1 as printed, run by all warps at once): the running
@@ -47,6 +48,7 @@ struct HA {
   unsigned long long *detkey;  // per graph (mode 1)
   const int32_t *seeds;
   int64_t nseeds;
+  int64_t begin, limit;  // start vertices [begin, limit) of the visiting order in this launch
 };
 
 struct Key {
@@ -113,13 +115,48 @@ __device__ int grow(const HA &a, int v, int thr, int stop_at, int32_t *cand, int
     if (lane == 0) cl[size] = w;
     size++;
     __syncwarp();
-    // keep the candidates adjacent to w (in-place compaction, reads ahead of writes)
+    // keep the candidates adjacent to w (in-place compaction, reads ahead of
+    // writes).  Few candidates against a long row: binary search per
+    // candidate; otherwise a warp-cooperative merge of the two sorted lists.
     int out = 0;
     Key nb = none;
+    const int64_t r0 = a.rp[w], r1 = a.rp[w + 1];
+    const bool merge = (int64_t)cnt * 16 >= (r1 - r0);
+    int64_t pos = r0;
     for (int base = 0; base < cnt; base += 32) {
-      int i = base + lane;
-      int x = (i < cnt) ? cand[i] : -1;
-      bool keep = x >= 0 && x != w && in_row(a, w, x);
+      const int i = base + lane;
+      const int x = (i < cnt) ? cand[i] : INT_MAX;
+      bool keep = false;
+      if (!merge) {
+        keep = i < cnt && x != w && in_row(a, w, x);
+      } else {
+        const int last = min(31, cnt - 1 - base);
+        const int xmin = __shfl_sync(FULL, x, 0), xmax = __shfl_sync(FULL, x, last);
+        // skip whole windows of the row below this tile
+        while (pos < r1) {
+          const int64_t e = min(pos + 31, r1 - 1);
+          if (a.ci[e] >= xmin) break;
+          pos = e + 1;
+        }
+        int64_t wp = pos;
+        while (wp < r1) {
+          const int y = (wp + lane < r1) ? a.ci[wp + lane] : INT_MAX;
+          int l = -1;  // largest window index with y <= x
+#pragma unroll
+          for (int st = 32; st >= 1; st >>= 1) {
+            const int t = l + st;
+            const int yt = __shfl_sync(FULL, y, t & 31);
+            if (t < 32 && yt <= x) l = t;
+          }
+          const int yl = __shfl_sync(FULL, y, l & 31);
+          if (l >= 0 && yl == x) keep = true;
+          const int ymax = __shfl_sync(FULL, y, 31);
+          if (ymax >= xmax) break;
+          wp += 32;
+        }
+        pos = wp;
+        keep = keep && i < cnt && x != w;
+      }
       unsigned m = __ballot_sync(FULL, keep);
       __syncwarp();
       if (keep) {
@@ -142,10 +179,10 @@ __global__ void __launch_bounds__(kHT) heuristic_kernel(HA a) {
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int32_t *cand = a.cand + gw * a.cand_stride;
   int32_t *cl = a.cl + gw * a.cl_stride;
-  const int64_t total = a.n + a.nseeds;
+  const int64_t total = a.limit;
   for (;;) {
     int64_t i = 0;
-    if (lane == 0) i = atomicAdd(a.next, 1);
+    if (lane == 0) i = a.begin + atomicAdd(a.next, 1);
     i = __shfl_sync(FULL, (long long)i, 0);
     if (i >= total || *(volatile int32_t *)a.err) break;
     const int v = (i < a.nseeds) ? a.seeds[i] : a.order[a.n - 1 - (i - a.nseeds)];
@@ -245,6 +282,9 @@ int launch_heuristic(mc_graph *g, int mode, long long spin_limit, const int32_t 
   a.seeds = seeds;
   a.nseeds = seeds ? nseeds : 0;
   const int blocks = (int)((warps * 32 + kHT - 1) / kHT);
+  const int64_t total = g->n + a.nseeds;
+  a.begin = 0;
+  a.limit = total;
   heuristic_kernel<<<blocks, kHT, 0, g->stream>>>(a);
   g_launches++;
   MC_CUDA_TRY(cudaGetLastError());

@@ -3,14 +3,17 @@
 // vertex whose remaining degree is at most k).
 //
 // One cooperative persistent launch processes all levels:
-//   scan    every vertex with remaining degree == k joins the level-k frontier
-//           (warp-aggregated appends); if none does, k jumps to the smallest
-//           remaining degree;
-//   process a warp takes a frontier vertex, reads its row with coalesced
-//           loads and decrements each neighbour whose degree is still above
-//           k; a neighbour whose degree falls to k joins the frontier and is
-//           processed by the same warp (warp-local chain in shared memory,
-//           overflow to a global work list handled in a further sub-round).
+//   scan    every live vertex with remaining degree == k joins the level-k
+//           frontier (warp-aggregated appends); vertices of larger degree are
+//           compacted into the next live list, so later scans only touch what
+//           is left; if nothing joins, k jumps to the smallest remaining degree;
+//   process each frontier vertex becomes one work item per 512-edge chunk of
+//           its row; the items appended before a grid barrier are split
+//           statically over all warps (rows under 32 edges one lane per
+//           item, longer chunks one warp per item, coalesced), and every neighbour whose
+//           degree is still above k is decremented; a neighbour whose degree
+//           falls to k joins the frontier and its items form the next
+//           sub-round of the same level, until a sub-round appends nothing.
 // The append order is a degeneracy order: every vertex has at most K(v)
 // neighbours appended after it.  It becomes the search's vertex ranking.
 #include "mc_internal.cuh"
@@ -22,25 +25,28 @@ namespace mc {
 
 namespace {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
-constexpr int kLocalCap = 128;
+constexpr int kChunk = 512;  // edges per work item
 
 struct KcoreCtl {
   unsigned bar_count, bar_gen;
-  int otail;     // vertices appended to the peel order
-  int ptail;     // vertices appended to the global work list
-  int ctr[3];    // work-list grab counters, rotated per sub-round
-  int minrem[3]; // smallest remaining degree, rotated per level scan
-  int snap[2][2]; // (otail, ptail) captured by the last block into each barrier
+  int otail;          // vertices appended to the peel order
+  int live_n[2];      // live-list sizes (ping-pong)
+  int pad;
+  long long wtail;    // work items appended
+  int minrem[3];      // smallest remaining degree, rotated per level scan
+  long long snap[2][3];  // (otail, wtail, live) captured by the last block into each barrier
 };
 
-// Grid barrier that also snapshots (otail, ptail) at the moment every block
-// has arrived, so all blocks act on the same values even though fast blocks
-// append again right after the barrier.  Bounded spin (error word on timeout).
+__device__ __forceinline__ long long ld_vol64(const long long *p) { return *(const volatile long long *)p; }
+
+// Grid barrier that also snapshots (otail, wtail) when every block has
+// arrived.  Bounded spin: on timeout the error word is set.
 __device__ __forceinline__ void barrier_snap(KcoreCtl *ctl, unsigned nblocks, int32_t *err, long long spin_limit,
-                                             int *otail_out, int *ptail_out) {
-  __shared__ int s_o, s_p;
+                                             long long *otail_out, long long *wtail_out, const int *live_src,
+                                             long long *live_out) {
+  __shared__ long long s_o, s_w, s_l;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned g0 = *(volatile unsigned *)&ctl->bar_gen;
@@ -48,7 +54,8 @@ __device__ __forceinline__ void barrier_snap(KcoreCtl *ctl, unsigned nblocks, in
     if (atomicAdd(&ctl->bar_count, 1u) == nblocks - 1) {
       __threadfence();
       ctl->snap[(g0 + 1) & 1][0] = *(volatile int *)&ctl->otail;
-      ctl->snap[(g0 + 1) & 1][1] = *(volatile int *)&ctl->ptail;
+      ctl->snap[(g0 + 1) & 1][1] = ld_vol64(&ctl->wtail);
+      ctl->snap[(g0 + 1) & 1][2] = live_src ? *(volatile const int *)live_src : 0;
       *(volatile unsigned *)&ctl->bar_count = 0;
       __threadfence();
       atomicAdd(&ctl->bar_gen, 1u);
@@ -56,16 +63,18 @@ __device__ __forceinline__ void barrier_snap(KcoreCtl *ctl, unsigned nblocks, in
       long long it = 0;
       while (*(volatile unsigned *)&ctl->bar_gen == g0) {
         if (++it > spin_limit) { atomicExch(err, kDevTimeout); break; }
-        __nanosleep(20);
+        __nanosleep(16);
       }
     }
     __threadfence();
-    s_o = *(volatile int *)&ctl->snap[(g0 + 1) & 1][0];
-    s_p = *(volatile int *)&ctl->snap[(g0 + 1) & 1][1];
+    s_o = ld_vol64(&ctl->snap[(g0 + 1) & 1][0]);
+    s_w = ld_vol64(&ctl->snap[(g0 + 1) & 1][1]);
+    s_l = ld_vol64(&ctl->snap[(g0 + 1) & 1][2]);
   }
   __syncthreads();
   *otail_out = s_o;
-  *ptail_out = s_p;
+  *wtail_out = s_w;
+  if (live_out) *live_out = s_l;
 }
 
 __global__ void degree_init_kernel(int64_t n, const int64_t *__restrict__ rp, int32_t *__restrict__ deg,
@@ -80,130 +89,167 @@ __global__ void degree_init_kernel(int64_t n, const int64_t *__restrict__ rp, in
   if ((threadIdx.x & 31) == 0) atomicMax(maxdeg, local);
 }
 
-__global__ void __launch_bounds__(kThreads) kcore_peel_kernel(int64_t n, const int64_t *__restrict__ rp,
-                                                              const int32_t *__restrict__ ci, int32_t *deg,
-                                                              int32_t *core, int32_t *order, int32_t *pend,
-                                                              KcoreCtl *ctl, int32_t *err, long long spin_limit) {
-  __shared__ int lstack[kWarps][kLocalCap];
-  __shared__ int lcount[kWarps];
+// Append the lanes' new frontier vertices (flag nf, vertex u): core, peel
+// order and one work item per chunk of the row.  All lanes call.
+__device__ __forceinline__ void append_frontier(bool nf, int u, int k, const int64_t *__restrict__ rp, int32_t *core,
+                                                int32_t *order, long long *wq, KcoreCtl *ctl) {
+  const int lane = threadIdx.x & 31;
+  const unsigned m = __ballot_sync(0xffffffffu, nf);
+  if (!m) return;
+  const unsigned lt = (1u << lane) - 1u;
+  int nch = 0;
+  if (nf) {
+    int64_t d = rp[u + 1] - rp[u];
+    nch = (int)((d + kChunk - 1) / kChunk);
+  }
+  int incl = nch;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int tot = __shfl_sync(0xffffffffu, incl, 31);
+  int ob = 0;
+  long long wb = 0;
+  if (lane == 0) {
+    ob = atomicAdd(&ctl->otail, __popc(m));
+    if (tot) wb = (long long)atomicAdd((unsigned long long *)&ctl->wtail, (unsigned long long)tot);
+  }
+  ob = __shfl_sync(0xffffffffu, ob, 0);
+  wb = __shfl_sync(0xffffffffu, wb, 0);
+  if (nf) {
+    core[u] = k;
+    order[ob + __popc(m & lt)] = u;
+    long long at = wb + incl - nch;
+    for (int c = 0; c < nch; c++) wq[at + c] = ((long long)u << 32) | (unsigned)c;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, const int64_t *__restrict__ rp,
+                                                                 const int32_t *__restrict__ ci, int32_t *deg,
+                                                                 int32_t *core, int32_t *order, int32_t *live0,
+                                                                 int32_t *live1, long long *wq, KcoreCtl *ctl,
+                                                                 int32_t *err, long long spin_limit) {
   __shared__ int bmin;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gwarp = (int64_t)blockIdx.x * kWarps + wib;
   const int64_t nwarps = (int64_t)gridDim.x * kWarps;
   const unsigned nblocks = gridDim.x;
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
-  const unsigned lt_mask = (1u << lane) - 1u;
+  const unsigned lt = (1u << lane) - 1u;
 
-  int k = 0, phead = 0;
-  unsigned level = 0, round = 0;
-  if (lane == 0) lcount[wib] = 0;
-  __syncwarp();
-  int otail_now = 0, ptail_now = 0;
+  int k = 0;
+  unsigned level = 0;
+  long long otail_now = 0, wtail_now = 0, wstart = 0;
+  int64_t live_count = n;  // level 0 scans every vertex (identity list)
+  int32_t *lin = live0, *lout = live1;
 
   for (;;) {
-    // ---------------- scan: frontier of level k ----------------
+    // ---------------- scan: frontier of level k, compaction of the rest ----
     if (threadIdx.x == 0) bmin = INT_MAX;
-    if (leader) ctl->minrem[(level + 1) % 3] = INT_MAX;
+    if (leader) {
+      ctl->minrem[(level + 1) % 3] = INT_MAX;
+      ctl->live_n[(level + 1) & 1] = 0;
+    }
     __syncthreads();
     int lmin = INT_MAX;
-    for (int64_t base = gwarp * 32; base < n; base += nwarps * 32) {
-      int64_t v = base + lane;
-      int d = (v < n) ? __ldcg(deg + v) : INT_MIN;
-      bool hit = d == k;
-      if (d > k) lmin = min(lmin, d);
-      unsigned m = __ballot_sync(0xffffffffu, hit);
-      if (m) {
-        int cnt = __popc(m), ob = 0, pb = 0;
-        if (lane == 0) { ob = atomicAdd(&ctl->otail, cnt); pb = atomicAdd(&ctl->ptail, cnt); }
-        ob = __shfl_sync(0xffffffffu, ob, 0);
-        pb = __shfl_sync(0xffffffffu, pb, 0);
-        if (hit) {
-          int r = __popc(m & lt_mask);
-          core[v] = k;
-          order[ob + r] = (int)v;
-          pend[pb + r] = (int)v;
-        }
+    int *lout_n = &ctl->live_n[level & 1];
+    for (int64_t base = gwarp * 32; base < live_count; base += nwarps * 32) {
+      int64_t i = base + lane;
+      int v = -1, d = INT_MIN;
+      if (i < live_count) {
+        v = (level == 0) ? (int)i : lin[i];
+        d = __ldcg(deg + v);
       }
+      const bool keep = d > k;
+      if (keep) lmin = min(lmin, d);
+      const unsigned km = __ballot_sync(0xffffffffu, keep);
+      if (km) {
+        int ob = 0;
+        if (lane == 0) ob = atomicAdd(lout_n, __popc(km));
+        ob = __shfl_sync(0xffffffffu, ob, 0);
+        if (keep) lout[ob + __popc(km & lt)] = v;
+      }
+      append_frontier(d == k, v, k, rp, core, order, wq, ctl);
     }
     lmin = -dev::warp_max(-lmin);
     if (lane == 0 && lmin != INT_MAX) atomicMin(&bmin, lmin);
     __syncthreads();
     if (threadIdx.x == 0 && bmin != INT_MAX) atomicMin(&ctl->minrem[level % 3], bmin);
-    barrier_snap(ctl, nblocks, err, spin_limit, &otail_now, &ptail_now);
+    long long live_next = 0;
+    barrier_snap(ctl, nblocks, err, spin_limit, &otail_now, &wtail_now, lout_n, &live_next);
     if (*(volatile int32_t *)err) return;
+    live_count = live_next;
+    { int32_t *t = lin; lin = lout; lout = t; }
 
-    if (ptail_now == phead) {
-      // empty level: every remaining vertex has degree > k
-      if (otail_now >= n) break;
+    if (otail_now >= n) break;
+    if (wtail_now == wstart) {
+      // nothing at level k (no frontier, or only isolated vertices)
       int mk = *(volatile int *)&ctl->minrem[level % 3];
       level++;
-      if (mk == INT_MAX) break;  // unreachable: some vertex remains
+      if (mk == INT_MAX) break;  // unreachable while vertices remain
       k = mk;
       continue;
     }
-    level++;
 
-    // ---------------- process sub-rounds ----------------
-    while (phead < ptail_now) {
-      if (leader) ctl->ctr[(round + 1) % 3] = 0;
-      for (;;) {
-        int cur;
-        int lc = lcount[wib];
-        if (lc > 0) {
-          cur = lstack[wib][lc - 1];
-          __syncwarp();
-          if (lane == 0) lcount[wib] = lc - 1;
-          __syncwarp();
-        } else {
-          int idx = 0;
-          if (lane == 0) idx = phead + atomicAdd(&ctl->ctr[round % 3], 1);
-          idx = __shfl_sync(0xffffffffu, idx, 0);
-          if (idx >= ptail_now) break;
-          cur = pend[idx];
+    // ---------------- process: sub-rounds over fixed item ranges ----------
+    // Items [s0, e0) were appended before the last barrier; those appended
+    // while processing them form the next sub-round.  Warps take groups of
+    // 32 items statically: rows shorter than 32 edges are walked one lane per
+    // item (lanes in step, so appends stay warp-aggregated), longer chunks by
+    // the whole warp.
+    long long s0 = wstart, e0 = wtail_now;
+    while (s0 < e0) {
+      // pass A: items of fewer than 32 edges, 32 per warp, one lane each
+      for (long long gb = s0 + gwarp * 32; gb < e0; gb += nwarps * 32) {
+        const long long t = gb + lane;
+        const bool valid = t < e0;
+        const long long item = valid ? __ldcg(wq + t) : -1LL;
+        int64_t b0 = 0;
+        int len = 0;
+        if (valid) {
+          const int v = (int)(item >> 32), c = (int)(item & 0xffffffff);
+          b0 = rp[v] + (int64_t)c * kChunk;
+          len = (int)(min(rp[v + 1], b0 + kChunk) - b0);
         }
-        const int64_t e0 = rp[cur], e1 = rp[cur + 1];
-        for (int64_t eb = e0; eb < e1; eb += 32) {
-          int64_t e = eb + lane;
+        const bool small = valid && len < 32;
+        const int maxlen = dev::warp_max(small ? len : 0);
+        for (int j = 0; j < maxlen; j++) {
           bool nf = false;
           int u = -1;
-          if (e < e1) {
-            u = ci[e];
-            if (__ldcg(deg + u) > k) {
-              int old = atomicSub(deg + u, 1);
-              nf = (old == k + 1);
-            }
+          if (small && j < len) {
+            u = ci[b0 + j];
+            if (__ldcg(deg + u) > k) nf = (atomicSub(deg + u, 1) == k + 1);
           }
-          unsigned m = __ballot_sync(0xffffffffu, nf);
-          if (m) {
-            int cnt = __popc(m), ob = 0;
-            if (lane == 0) ob = atomicAdd(&ctl->otail, cnt);
-            ob = __shfl_sync(0xffffffffu, ob, 0);
-            int lc2 = lcount[wib];
-            int room = kLocalCap - lc2;
-            int take = min(room, cnt);
-            int pb = 0;
-            if (lane == 0 && cnt > take) pb = atomicAdd(&ctl->ptail, cnt - take);
-            pb = __shfl_sync(0xffffffffu, pb, 0);
-            if (nf) {
-              int r = __popc(m & lt_mask);
-              core[u] = k;
-              order[ob + r] = u;
-              if (r < take) lstack[wib][lc2 + r] = u;
-              else pend[pb + (r - take)] = u;
-            }
-            __syncwarp();
-            if (lane == 0) lcount[wib] = lc2 + take;
-            __syncwarp();
-          }
+          append_frontier(nf, u, k, rp, core, order, wq, ctl);
         }
       }
-      int next_ptail;
-      barrier_snap(ctl, nblocks, err, spin_limit, &otail_now, &next_ptail);
+      // pass B: longer chunks, one warp each (coalesced row reads)
+      for (long long t = s0 + gwarp; t < e0; t += nwarps) {
+        const long long item = __ldcg(wq + t);
+        const int v = (int)(item >> 32), c = (int)(item & 0xffffffff);
+        const int64_t b0 = rp[v] + (int64_t)c * kChunk;
+        const int len = (int)(min(rp[v + 1], b0 + kChunk) - b0);
+        if (len < 32) continue;
+        for (int eb = 0; eb < len; eb += 32) {
+          bool nf = false;
+          int u = -1;
+          if (eb + lane < len) {
+            u = ci[b0 + eb + lane];
+            if (__ldcg(deg + u) > k) nf = (atomicSub(deg + u, 1) == k + 1);
+          }
+          append_frontier(nf, u, k, rp, core, order, wq, ctl);
+        }
+      }
+      long long e1 = 0;
+      barrier_snap(ctl, nblocks, err, spin_limit, &otail_now, &e1, nullptr, nullptr);
       if (*(volatile int32_t *)err) return;
-      round++;
-      phead = ptail_now;
-      ptail_now = next_ptail;
+      s0 = e0;
+      e0 = e1;
+      wtail_now = e1;
     }
+    wstart = wtail_now;
+    level++;
     if (otail_now >= n) break;
     k++;
   }
@@ -230,12 +276,16 @@ int launch_core_numbers(mc_graph *g, long long spin_limit) {
   void *p;
   MC_TRY(ws_get(g, "kc.deg", n * sizeof(int32_t), &p));
   int32_t *deg = (int32_t *)p;
-  MC_TRY(ws_get(g, "kc.pend", n * sizeof(int32_t), &p));
-  int32_t *pend = (int32_t *)p;
+  MC_TRY(ws_get(g, "kc.live", 2 * n * sizeof(int32_t) + 64, &p));
+  int32_t *live0 = (int32_t *)p, *live1 = live0 + n;
+  const int64_t wcap = n + g->nnz / kChunk + 64;
+  MC_TRY(ws_get(g, "kc.wq", wcap * sizeof(long long), &p));
+  long long *wq = (long long *)p;
   MC_TRY(ws_get(g, "kc.ctl", sizeof(KcoreCtl) + 64, &p));
   KcoreCtl *ctl = (KcoreCtl *)p;
   int32_t *maxdeg = (int32_t *)((char *)p + sizeof(KcoreCtl) + 16);
   MC_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(KcoreCtl) + 64, g->stream));
+  MC_CUDA_TRY(cudaMemsetAsync(wq, 0xff, wcap * sizeof(long long), g->stream));
 
   int ib = (int)std::min<int64_t>((n + 255) / 256, (int64_t)g->sm_count * 8);
   degree_init_kernel<<<ib, 256, 0, g->stream>>>(n, g->row_ptr, deg, maxdeg);
@@ -245,7 +295,7 @@ int launch_core_numbers(mc_graph *g, long long spin_limit) {
   int per_sm = 0;
   MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kcore_peel_kernel, kThreads, 0));
   if (per_sm < 1) return MC_ERR_CUDA;
-  int blocks = g->sm_count * std::min(per_sm, 2);
+  int blocks = g->sm_count;
   int64_t need = (n + kThreads - 1) / kThreads;
   if (need < blocks) blocks = (int)std::max<int64_t>(1, need);
   int64_t n_arg = n;
@@ -253,7 +303,7 @@ int launch_core_numbers(mc_graph *g, long long spin_limit) {
   const int32_t *ci = g->col_idx;
   int32_t *core = g->core, *order = g->order, *err = g->err;
   long long sl = spin_limit;
-  void *args[] = {&n_arg, (void *)&rp, (void *)&ci, &deg, &core, &order, &pend, &ctl, &err, &sl};
+  void *args[] = {&n_arg, (void *)&rp, (void *)&ci, &deg, &core, &order, &live0, &live1, &wq, &ctl, &err, &sl};
   MC_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)kcore_peel_kernel, dim3(blocks), dim3(kThreads), args, 0,
                                           g->stream));
   g_launches++;
@@ -271,3 +321,4 @@ int launch_core_numbers(mc_graph *g, long long spin_limit) {
 }
 
 }  // namespace mc
+

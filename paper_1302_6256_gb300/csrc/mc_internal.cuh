@@ -68,6 +68,7 @@ struct mc_graph {
   // core numbers cache
   bool cores_valid = false;
   int32_t max_core = 0;
+  int32_t heur0 = 0;  // heuristic clique size of graph 0 in the last solve
   int32_t *core = nullptr, *order = nullptr, *pos = nullptr;  // n each (device)
   // incumbent, one per graph: size, lock, witness area (vertex-offset indexed)
   int32_t *best = nullptr, *lock = nullptr, *wit = nullptr;
