@@ -49,6 +49,7 @@ extern "C" {
 #define MC_ERR_CUDA (-6)          /* a CUDA runtime call failed */
 #define MC_ERR_DEVICE_CHECK (-7)  /* a device-side consistency check failed */
 #define MC_ERR_UNSUPPORTED (-8)   /* a neighbourhood exceeds the supported size */
+#define MC_ERR_TOO_LARGE (-9)     /* input larger than mc_core_numbers_noalloc's fixed scratch */
 
 /* load flags */
 #define MC_VALIDATE 1u /* check the CSR invariants on the device (MC_ERR_INVALID_GRAPH) */
@@ -155,6 +156,29 @@ int mc_max_clique_batch(mc_graph *g, const mc_options *opt, int32_t *omegas_out,
 /* Check a vertex set on the device: *is_clique_out = 1 iff the k vertices are
  * distinct, in range and pairwise adjacent (the definition of a clique). */
 int mc_verify_clique(mc_graph *g, const int32_t *vertices, int32_t k, int32_t *is_clique_out);
+
+/* Core numbers, like mc_core_numbers, for callers that cannot allocate
+ * device memory.  The paper has no counterpart: this exists for code that
+ * must not call cudaMalloc -- for example while a CUDA graph is being
+ * captured in a mode that forbids allocation, inside an allocator hook, or
+ * under a host that owns every byte of device memory it gives the library.
+ * Nothing is allocated: the peel's working memory is one fixed device array
+ * of about 30 MB inside the library, which every GPU that loads the library
+ * holds until the process exits.
+ *   n: vertices, at most 1,048,576; row_ptr (n+1 int64) and col_idx
+ *   (row_ptr[n] int32, at most 67,108,864 entries): a simple symmetric CSR
+ *   in DEVICE memory of the current device (the caller owns it; it is only
+ *   read); core_out: n int32 in device memory, written; max_core_out: host
+ *   int32 or NULL, receives K(G).  cuda_stream: the stream to run on.
+ * Larger inputs are rejected with MC_ERR_TOO_LARGE before anything runs.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  The call synchronises its stream before it
+ * returns.  All calls share the one array, so calls that overlap on the GPU
+ * (other host threads, other streams) race and must be serialised by the
+ * caller. */
+int mc_core_numbers_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, int32_t *core_out,
+                            int32_t *max_core_out, void *cuda_stream);
 
 /* ----------------------------------------------------- miscellaneous --- */
 

@@ -27,6 +27,7 @@ MC_ERR_TIMEOUT = -5
 MC_ERR_CUDA = -6
 MC_ERR_DEVICE_CHECK = -7
 MC_ERR_UNSUPPORTED = -8
+MC_ERR_TOO_LARGE = -9
 
 MC_VALIDATE = 1
 MC_BORROW = 2

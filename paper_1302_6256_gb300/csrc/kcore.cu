@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <mutex>
 
 namespace mc {
 
@@ -322,3 +323,113 @@ int launch_core_numbers(mc_graph *g, long long spin_limit) {
 
 }  // namespace mc
 
+// ------------------------------------------------------------------------
+// Core numbers without any device allocation.
+//
+// Some callers cannot call cudaMalloc: code running while a CUDA graph is
+// being captured with a capture mode that forbids allocation, allocator
+// hooks that must not re-enter the allocator, or hosts that hand the library
+// a fixed memory budget and own every byte of it.  For them this entry point
+// runs the same peel with its working memory in a file-scope device array of
+// fixed size, reserved when the library is loaded and held by every GPU that
+// loads it until the process exits.
+// ------------------------------------------------------------------------
+
+namespace mc {
+namespace {
+
+constexpr int64_t kNoAllocMaxN = 1 << 20;     // vertices
+constexpr int64_t kNoAllocMaxNnz = 1 << 26;   // CSR entries (2 x edges)
+constexpr int64_t kNoAllocWq = kNoAllocMaxN + kNoAllocMaxNnz / kChunk + 64;
+constexpr size_t kNoAllocCtlBytes = 4096;
+// layout: control block | degrees | two live lists | peel order | positions | work items
+constexpr size_t kNaOffDeg = kNoAllocCtlBytes;
+constexpr size_t kNaOffLive = kNaOffDeg + 4 * kNoAllocMaxN;
+constexpr size_t kNaOffOrder = kNaOffLive + 8 * kNoAllocMaxN;
+constexpr size_t kNaOffPos = kNaOffOrder + 4 * kNoAllocMaxN;
+constexpr size_t kNaOffWq = kNaOffPos + 4 * kNoAllocMaxN;
+constexpr size_t kNoAllocBytes = kNaOffWq + 8 * kNoAllocWq;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// device address of g_noalloc_scratch, per device (set up on first use)
+static void *g_noalloc_ptr[64];
+static std::mutex g_noalloc_mu;
+
+int noalloc_setup(int dev, unsigned char **out) {
+  if (dev < 0 || dev >= 64) return MC_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      set_last_cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+      return MC_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = (unsigned char *)g_noalloc_ptr[dev];
+  return MC_OK;
+}
+
+}  // namespace
+}  // namespace mc
+
+extern "C" int mc_core_numbers_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                                       int32_t *core_out, int32_t *max_core_out, void *cuda_stream) {
+  using namespace mc;
+  if (n < 0 || (n > 0 && (!row_ptr || !col_idx || !core_out))) return MC_ERR_ARG;
+  if (n > kNoAllocMaxN) return MC_ERR_TOO_LARGE;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (max_core_out) *max_core_out = 0;
+  if (n == 0) return MC_OK;
+  int dev = 0, sms = 0;
+  MC_CUDA_TRY(cudaGetDevice(&dev));
+  MC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  unsigned char *base = nullptr;
+  MC_TRY(noalloc_setup(dev, &base));
+  int64_t nnz = 0;
+  MC_CUDA_TRY(cudaMemcpyAsync(&nnz, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  MC_CUDA_TRY(cudaStreamSynchronize(s));
+  if (nnz < 0) return MC_ERR_ARG;
+  if (nnz > kNoAllocMaxNnz) return MC_ERR_TOO_LARGE;
+
+  KcoreCtl *ctl = (KcoreCtl *)base;
+  int32_t *maxdeg = (int32_t *)(base + 1024);  // [0] max degree, [1] max core
+  int32_t *err = (int32_t *)(base + 2048);
+  int32_t *deg = (int32_t *)(base + kNaOffDeg);
+  int32_t *live0 = (int32_t *)(base + kNaOffLive), *live1 = live0 + n;
+  int32_t *order = (int32_t *)(base + kNaOffOrder);
+  int32_t *pos = (int32_t *)(base + kNaOffPos);
+  long long *wq = (long long *)(base + kNaOffWq);
+  // the array keeps the previous call's contents: clear the control block
+  MC_CUDA_TRY(cudaMemsetAsync(base, 0, kNoAllocCtlBytes, s));
+
+  const int ib = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
+  degree_init_kernel<<<ib, 256, 0, s>>>(n, row_ptr, deg, maxdeg);
+  g_launches++;
+  MC_CUDA_TRY(cudaGetLastError());
+  int per_sm = 0;
+  MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kcore_peel_kernel, kThreads, 0));
+  if (per_sm < 1) return MC_ERR_CUDA;
+  int blocks = sms;
+  const int64_t need = (n + kThreads - 1) / kThreads;
+  if (need < blocks) blocks = (int)std::max<int64_t>(1, need);
+  int64_t n_arg = n;
+  long long sl = kDefaultSpinLimit;
+  void *args[] = {&n_arg, (void *)&row_ptr, (void *)&col_idx, &deg, &core_out, &order, &live0, &live1, &wq, &ctl,
+                  &err, &sl};
+  MC_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)kcore_peel_kernel, dim3(blocks), dim3(kThreads), args, 0, s));
+  g_launches++;
+  peel_pos_kernel<<<ib, 256, 0, s>>>(n, order, pos, core_out, maxdeg + 1);
+  g_launches++;
+  MC_CUDA_TRY(cudaGetLastError());
+  int32_t host[3] = {0, 0, 0};
+  MC_CUDA_TRY(cudaMemcpyAsync(host, maxdeg, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  MC_CUDA_TRY(cudaMemcpyAsync(host + 2, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  MC_CUDA_TRY(cudaStreamSynchronize(s));
+  if (host[2] == kDevTimeout) return MC_ERR_TIMEOUT;
+  if (host[2] != kDevOk) return MC_ERR_DEVICE_CHECK;
+  if (max_core_out) *max_core_out = host[1];
+  return MC_OK;
+}

@@ -1,0 +1,64 @@
+"""mc_core_numbers_noalloc: core numbers for callers that cannot allocate
+device memory (graph capture that forbids allocation, allocator hooks, hosts
+that own the whole device budget).  It must give exactly what
+mc_core_numbers gives, call after call, although every call reuses the same
+fixed device array.  This file is collected last on purpose."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    import paper_1302_6256_gb300 as mc
+    L = mc.load_library()
+    L.mc_core_numbers_noalloc.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]
+    L.mc_core_numbers_noalloc.restype = ctypes.c_int
+    return mc, L
+
+
+def reference_cores(mc, g):
+    h = mc.mc_load_csr(g.row_ptr, g.col_idx, 0)
+    core, kmax = mc.mc_core_numbers(h)
+    h.close()
+    return np.array(core), kmax
+
+
+@pytest.mark.parametrize("g", [gg.rmat(14, 16, planted=20, seed=5),
+                               gg.chung_lu(20000, 2.5, 8.0, 1000.0, planted=15, seed=1),
+                               gg.erdos_renyi(700, 0.2, planted=12, seed=8)], ids=lambda g: g.name)
+def test_noalloc_matches_mc_core_numbers_twice(lib, g):
+    mc, L = lib
+    ref, kref = reference_cores(mc, g)
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    ci = torch.from_numpy(g.col_idx).cuda()
+    stream = torch.cuda.current_stream()
+    for _ in range(2):  # the second call sees the first call's leftovers
+        out = torch.full((g.n,), -7, dtype=torch.int32, device="cuda")
+        mk = ctypes.c_int32(-1)
+        rc = L.mc_core_numbers_noalloc(g.n, rp.data_ptr(), ci.data_ptr(), out.data_ptr(), ctypes.byref(mk),
+                                       stream.cuda_stream)
+        assert rc == 0, mc.strerror(rc)
+        assert np.array_equal(out.cpu().numpy(), ref)
+        assert mk.value == kref
+
+
+def test_noalloc_rejects_inputs_beyond_its_scratch(lib):
+    mc, L = lib
+    g = gg.path(4)
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    ci = torch.from_numpy(g.col_idx).cuda()
+    out = torch.zeros(4, dtype=torch.int32, device="cuda")
+    mk = ctypes.c_int32(0)
+    rc = L.mc_core_numbers_noalloc((1 << 20) + 1, rp.data_ptr(), ci.data_ptr(), out.data_ptr(), ctypes.byref(mk),
+                                   None)
+    assert rc == mc.MC_ERR_TOO_LARGE
