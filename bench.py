@@ -137,6 +137,116 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_batch(args):
+    """The Erdos-Renyi batch: all graphs in one solve (CUDA-graph replay or
+    direct launches) or one solve per graph; every omega checked against
+    the oracle's stored values when available."""
+    import numpy as np
+    import torch
+    import paper_1302_6256_gb300 as mc
+    from graphgen import workloads as W
+
+    mc.load_library()
+    b = W.er_batch_4096(args.batch_count)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ms_list = []
+    if args.form == "per-graph":
+        hs = [mc.mc_load_csr(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col_idx).to(dev), 0,
+                             stream=stream) for g in b.graphs]
+        for _ in range(args.warmup):
+            om = np.array([mc.mc_max_clique(h)[0] for h in hs], np.int32)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            om = np.array([mc.mc_max_clique(h)[0] for h in hs], np.int32)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t) * 1e3 / args.steps
+        st = {}
+    else:
+        h = mc.mc_load_batch(torch.from_numpy(b.voff).to(dev), torch.from_numpy(b.row_ptr).to(dev),
+                             torch.from_numpy(b.col_idx).to(dev), 0, stream=stream)
+        use_graph = args.form == "chosen"
+        for _ in range(args.warmup):
+            om, _, st = mc.mc_max_clique_batch(h, graph=use_graph)
+        torch.cuda.synchronize()
+        launches0 = mc.mc_launch_count()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            om, _, st = mc.mc_max_clique_batch(h, graph=use_graph)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / args.steps
+    gold = os.path.join(ROOT, "tests", "golden", "er-batch-%d.json" % args.batch_count)
+    checked = None
+    if os.path.exists(gold):
+        ref = np.array(json.load(open(gold))["omegas"], np.int32)
+        checked = bool(np.array_equal(ref, om))
+    print(json.dumps({"metric": METRIC, "value": b.m / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "int32",
+                      "data": "synthetic", "config": {"workload": W.ER_BATCH_4096 if args.batch_count == 4096 else
+                                                      b.name, "form": args.form, "graphs": b.count, "n": b.n,
+                                                      "m": b.m, "omega_max": int(om.max()),
+                                                      "omegas_match_oracle": checked},
+                      "stats_last": st}), flush=True)
+
+
+def run_single(args):
+    """One graph, plain or learned form: seconds to exact omega, the
+    heuristic's lower-bound gap and the fraction of vertices pruned."""
+    import numpy as np
+    import torch
+    import paper_1302_6256_gb300 as mc
+    from graphgen import workloads as W
+
+    mc.load_library()
+    gen = {"rmat-s22": (W.RMAT_S22, W.rmat_s22), "rmat-s24": (W.RMAT_S24, W.rmat_s24),
+           "chung-lu-20k": (W.CHUNG_LU_20K, W.chung_lu_20k)}[args.workload]
+    g = gen[1]()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    h = mc.mc_load_csr(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col_idx).to(dev), 0, stream=stream)
+    wit = torch.zeros(g.n + 1, dtype=torch.int32, device=dev)
+    net = None
+    if args.form == "learned":
+        net = mc.MLP(seed=0)
+        net.set_params(np.load(args.weights))
+        feat = torch.zeros((g.n, 6), dtype=torch.float32, device=dev)
+        score = torch.zeros(g.n, dtype=torch.float32, device=dev)
+
+    def solve():
+        if net is None:
+            return mc.mc_max_clique(h, witness_out=wit)
+        mc.mc_features(h, feat)
+        net.forward(feat, score)
+        return mc.mc_max_clique(h, witness_out=wit, ordering=1, scores=score, seeds=64)
+
+    for _ in range(args.warmup):
+        om, _, st = solve()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    stats = []
+    t0.record(stream)
+    for _ in range(args.steps):
+        om, _, st = solve()
+        stats.append(st)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / args.steps
+    hs = sum(s["heuristic_size"] for s in stats) / len(stats)
+    pruned = 1.0 - sum(s["pruned_n"] for s in stats) / len(stats) / g.n
+    print(json.dumps({"metric": METRIC, "value": g.m / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "int32",
+                      "data": "synthetic",
+                      "config": {"workload": gen[0], "form": args.form, "n": g.n, "m": g.m, "omega": om,
+                                 "heuristic_mean": hs, "lower_bound_gap": om - hs, "fraction_pruned": pruned,
+                                 "max_core": stats[-1]["max_core"]},
+                      "stats_last": stats[-1]}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -144,10 +254,21 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="rmat-s22", choices=["rmat-s22", "er-batch", "rmat-s24", "chung-lu-20k"])
+    ap.add_argument("--form", default="chosen", choices=["chosen", "plain", "per-graph", "learned"],
+                    help="chosen: the default solve (graph replay for batches); plain: direct launches, "
+                         "degeneracy order; learned: root order and heuristic seeds from the trained network; "
+                         "per-graph: one solve per graph of a batch")
+    ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1302_6256_gb300", "ordering_mlp.npy"))
+    ap.add_argument("--batch-count", type=int, default=4096)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "er-batch":
+        return run_batch(args)
+    if args.workload != "rmat-s22" or args.form == "learned":
+        return run_single(args)
 
     import numpy as np
     import torch

@@ -82,6 +82,10 @@ typedef struct {
   /* heuristic seeds from the scores: the top `seeds` vertices of each graph
    * are also grown by Algorithm 1's greedy step first; 0 = none */
   int32_t seeds;
+  /* 1 = run the whole solve as one CUDA graph: the first call with these
+   * options solves directly (sizing every buffer), then captures the solve;
+   * later calls replay it with one graph launch.  0 = direct launches. */
+  int32_t graph;
 } mc_options;
 
 /* Per-call statistics (all times in milliseconds, CUDA events). */
@@ -179,6 +183,38 @@ int mc_verify_clique(mc_graph *g, const int32_t *vertices, int32_t k, int32_t *i
  * caller. */
 int mc_core_numbers_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, int32_t *core_out,
                             int32_t *max_core_out, void *cuda_stream);
+
+/* ------------------------------------------ learned vertex ordering --- */
+/* An extension of the method, not in the paper: a small network scores the
+ * vertices, and the scores only order the search's roots (mc_options.ordering
+ * = 1, .scores) and seed the heuristic (.seeds).  omega stays exact whatever
+ * the network predicts.  Network: 6 features -> 64 -> 64 -> 1, ReLU, BF16
+ * weights with FP32 accumulation; FP32 master weights trained with Adam on
+ * the mean binary cross-entropy of the logit, positives weighted by
+ * pos_weight.  Parameters are a flat float array of mc_mlp_num_params()
+ * entries: W1[64][6], b1[64], W2[64][64], b2[64], w3[64], b3. */
+typedef struct mc_mlp mc_mlp;
+
+/* Per-vertex features (n x 6 float, row-major, host or device): log1p(deg)
+ * and core-based neighbourhood statistics normalised to [0, 1] (see
+ * learned.cu).  Computes the core numbers if needed. */
+int mc_features(mc_graph *g, float *feat_out);
+/* Create a network with He-uniform weights from `seed` on `cuda_stream`. */
+int mc_mlp_create(uint64_t seed, void *cuda_stream, mc_mlp **out);
+void mc_mlp_free(mc_mlp *m);
+int mc_mlp_num_params(void);
+/* Copy the FP32 master parameters out / in (setting resets Adam's moments). */
+int mc_mlp_get_params(mc_mlp *m, float *out);
+int mc_mlp_set_params(mc_mlp *m, const float *in);
+/* Logits of n feature rows (feat: n x 6; score_out: n). */
+int mc_mlp_forward(mc_mlp *m, const float *feat, int64_t n, float *score_out);
+/* Gradient of the loss over n rows (labels 0/1) into grad_out (num_params
+ * floats) and the loss into *loss_out (nullable); parameters unchanged. */
+int mc_mlp_gradient(mc_mlp *m, const float *feat, const float *label, int64_t n, float pos_weight, float *grad_out,
+                    float *loss_out);
+/* One Adam step (beta 0.9 / 0.999) with learning rate lr on n rows. */
+int mc_mlp_train_step(mc_mlp *m, const float *feat, const float *label, int64_t n, float pos_weight, float lr,
+                      float *loss_out);
 
 /* ----------------------------------------------------- miscellaneous --- */
 

@@ -1,0 +1,117 @@
+"""Oracle for the learned vertex ordering -- TEST INFRASTRUCTURE ONLY.
+
+Plain numpy in float64: the per-vertex features, the 6 -> 64 -> 64 -> 1 ReLU
+network's forward pass, its weighted binary cross-entropy loss and the
+analytic gradient.  The network's weights are rounded to bfloat16 (round to
+nearest even) before use, as the CUDA kernels store them; biases stay at
+float32 precision.  Nothing here is shared with the CUDA library.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+F, H = 6, 64
+OFF_W1 = 0
+OFF_B1 = OFF_W1 + H * F
+OFF_W2 = OFF_B1 + H
+OFF_B2 = OFF_W2 + H * H
+OFF_W3 = OFF_B2 + H
+OFF_B3 = OFF_W3 + H
+NPARAMS = OFF_B3 + 1
+
+
+def bf16_round(x):
+    """float32 values rounded to the nearest bfloat16 (ties to even)."""
+    a = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    finite = (a & 0x7F800000) != 0x7F800000
+    r = np.where(finite, (a + 0x7FFF + ((a >> 16) & 1)) >> 16, a >> 16) << 16
+    return r.astype(np.uint32).view(np.float32)
+
+
+def features(g, core):
+    """The six features of every vertex, by their definitions:
+    f0 = log(1+d)/log(1+Dmax), f1 = K/Kmax, f2 = log(1+c)/log(1+Dmax),
+    f3 = max neighbour K / Kmax, f4 = mean neighbour K / Kmax, f5 = c/max(d,1),
+    with c = number of neighbours whose core number is at least K(v)."""
+    n = g.n
+    deg = np.diff(g.row_ptr).astype(np.float64)
+    kmax = float(max(int(core.max()) if n else 0, 1))
+    ldmax = np.log1p(float(max(int(deg.max()) if n else 0, 1)))
+    out = np.zeros((n, F), np.float64)
+    for v in range(n):
+        nb = g.col_idx[g.row_ptr[v]:g.row_ptr[v + 1]]
+        kn = core[nb].astype(np.float64)
+        c = float(np.sum(kn >= core[v]))
+        d = deg[v]
+        out[v, 0] = np.log1p(d) / ldmax
+        out[v, 1] = core[v] / kmax
+        out[v, 2] = np.log1p(c) / ldmax
+        out[v, 3] = (kn.max() if d > 0 else 0.0) / kmax
+        out[v, 4] = (kn.mean() if d > 0 else 0.0) / kmax
+        out[v, 5] = c / max(d, 1.0)
+    return out
+
+
+def unpack(p, bf16=True):
+    """Split the flat parameters.  bf16=True: weights as bfloat16 values of
+    their float32 master copy, biases as float32 (the kernels' storage);
+    bf16=False: everything at the given precision (float64 for derivative
+    checks)."""
+    if bf16:
+        p32 = np.asarray(p, dtype=np.float32)
+        w = bf16_round(p32).astype(np.float64)
+        p = p32.astype(np.float64)
+    else:
+        p = np.asarray(p, dtype=np.float64)
+        w = p
+    W1 = w[OFF_W1:OFF_B1].reshape(H, F)
+    b1 = p[OFF_B1:OFF_W2]
+    W2 = w[OFF_W2:OFF_B2].reshape(H, H)
+    b2 = p[OFF_B2:OFF_W3]
+    w3 = w[OFF_W3:OFF_B3]
+    b3 = float(p[OFF_B3])
+    return W1, b1, W2, b2, w3, b3
+
+
+def forward(params, x, bf16=True):
+    """Logits s = w3 . relu(W2 relu(W1 x + b1) + b2) + b3 for every row."""
+    W1, b1, W2, b2, w3, b3 = unpack(params, bf16)
+    x = np.asarray(x, dtype=np.float64)
+    h1 = np.maximum(x @ W1.T + b1, 0.0)
+    h2 = np.maximum(h1 @ W2.T + b2, 0.0)
+    return h2 @ w3 + b3
+
+
+def loss(params, x, y, pos_weight, bf16=True):
+    """Mean over rows of w_y (log(1 + e^s) - y s), w_y = pos_weight if y = 1."""
+    s = forward(params, x, bf16)
+    y = np.asarray(y, dtype=np.float64)
+    w = np.where(y > 0.5, pos_weight, 1.0)
+    return float(np.mean(w * (np.logaddexp(0.0, s) - y * s)))
+
+
+def gradient(params, x, y, pos_weight, bf16=True):
+    """Analytic gradient of loss() with respect to the flat parameters (the
+    weights enter through their bfloat16 values; the gradient is taken with
+    respect to those values, as the kernels do)."""
+    W1, b1, W2, b2, w3, b3 = unpack(params, bf16)
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    n = x.shape[0]
+    z1 = x @ W1.T + b1
+    h1 = np.maximum(z1, 0.0)
+    z2 = h1 @ W2.T + b2
+    h2 = np.maximum(z2, 0.0)
+    s = h2 @ w3 + b3
+    w = np.where(y > 0.5, pos_weight, 1.0)
+    gs = w * (1.0 / (1.0 + np.exp(-s)) - y) / n
+    g = np.zeros(NPARAMS, np.float64)
+    g[OFF_B3] = gs.sum()
+    g[OFF_W3:OFF_B3] = h2.T @ gs
+    d2 = np.outer(gs, w3) * (z2 > 0)
+    g[OFF_W2:OFF_B2] = (d2.T @ h1).ravel()
+    g[OFF_B2:OFF_W3] = d2.sum(axis=0)
+    d1 = (d2 @ W2) * (z1 > 0)
+    g[OFF_W1:OFF_B1] = (d1.T @ x).ravel()
+    g[OFF_B1:OFF_W2] = d1.sum(axis=0)
+    return g

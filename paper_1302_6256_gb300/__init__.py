@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
     _fields_ = [("ordering", ctypes.c_int32), ("no_neigh_cores", ctypes.c_int32),
                 ("heuristic", ctypes.c_int32), ("warp_max", ctypes.c_int32),
                 ("spin_limit", ctypes.c_int64), ("scores", ctypes.c_void_p),
-                ("seeds", ctypes.c_int32)]
+                ("seeds", ctypes.c_int32), ("graph", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -104,11 +104,21 @@ def load_library(build_if_missing: bool = True):
 
 
 def _extend(L):
-    """Declare optional entry points if the library exports them."""
-    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
-    if hasattr(L, "mc_features"):
-        L.mc_features.argtypes = [vp, vp]
-        L.mc_features.restype = ctypes.c_int
+    """Declare the learned-ordering entry points."""
+    vp, i64, i32, f32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_uint64
+    L.mc_features.argtypes = [vp, vp]
+    L.mc_mlp_create.argtypes = [u64, vp, ctypes.POINTER(vp)]
+    L.mc_mlp_free.argtypes = [vp]
+    L.mc_mlp_free.restype = None
+    L.mc_mlp_num_params.restype = ctypes.c_int
+    L.mc_mlp_get_params.argtypes = [vp, vp]
+    L.mc_mlp_set_params.argtypes = [vp, vp]
+    L.mc_mlp_forward.argtypes = [vp, vp, i64, vp]
+    L.mc_mlp_gradient.argtypes = [vp, vp, vp, i64, f32, vp, ctypes.POINTER(f32)]
+    L.mc_mlp_train_step.argtypes = [vp, vp, vp, i64, f32, f32, ctypes.POINTER(f32)]
+    for name in ("mc_features", "mc_mlp_create", "mc_mlp_get_params", "mc_mlp_set_params", "mc_mlp_forward",
+                 "mc_mlp_gradient", "mc_mlp_train_step"):
+        getattr(L, name).restype = ctypes.c_int
 
 
 def strerror(code: int) -> str:
@@ -215,8 +225,10 @@ def mc_heuristic_clique(g: Graph, mode: int = 0, core=None):
     return out[:size.value].copy()
 
 
-def _options(ordering=0, no_neigh_cores=False, heuristic=0, warp_max=0, spin_limit=0, scores=None, seeds=0):
+def _options(ordering=0, no_neigh_cores=False, heuristic=0, warp_max=0, spin_limit=0, scores=None, seeds=0,
+             graph=False):
     o = Options()
+    o.graph = 1 if graph else 0
     o.ordering = ordering
     o.no_neigh_cores = 1 if no_neigh_cores else 0
     o.heuristic = heuristic
@@ -272,3 +284,74 @@ def mc_launch_count() -> int:
 
 def mc_version() -> int:
     return int(load_library().mc_version())
+
+
+# --------------------------------------------------- learned ordering ---
+
+def mc_features(g: Graph, feat_out=None):
+    """Per-vertex features (n x 6 float32), host or device output."""
+    L = load_library()
+    if feat_out is None:
+        feat_out = np.zeros((max(g.n, 1), 6), np.float32)
+    p, keep = _ptr(feat_out)
+    _check(L.mc_features(g.handle, p), "mc_features")
+    return feat_out[:g.n]
+
+
+class MLP:
+    """Handle of the scoring network (mc_mlp*)."""
+
+    def __init__(self, seed: int = 0, stream=None):
+        L = load_library()
+        h = ctypes.c_void_p()
+        _check(L.mc_mlp_create(seed, _stream_handle(stream), ctypes.byref(h)), "mc_mlp_create")
+        self._h = h
+        self.nparams = int(L.mc_mlp_num_params())
+
+    def close(self):
+        if self._h:
+            load_library().mc_mlp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        out = np.zeros(self.nparams, np.float32)
+        _check(load_library().mc_mlp_get_params(self._h, out.ctypes.data), "mc_mlp_get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(load_library().mc_mlp_set_params(self._h, p.ctypes.data), "mc_mlp_set_params")
+
+    def forward(self, feat, out=None):
+        n = int(feat.shape[0])
+        if out is None:
+            out = np.zeros(max(n, 1), np.float32)
+        fp, kf = _ptr(feat)
+        op, ko = _ptr(out)
+        _check(load_library().mc_mlp_forward(self._h, fp, n, op), "mc_mlp_forward")
+        return out[:n]
+
+    def gradient(self, feat, label, pos_weight=1.0):
+        n = int(feat.shape[0])
+        g = np.zeros(self.nparams, np.float32)
+        loss = ctypes.c_float(0)
+        fp, kf = _ptr(feat)
+        lp, kl = _ptr(label)
+        _check(load_library().mc_mlp_gradient(self._h, fp, lp, n, pos_weight, g.ctypes.data, ctypes.byref(loss)),
+               "mc_mlp_gradient")
+        return g, loss.value
+
+    def train_step(self, feat, label, pos_weight=1.0, lr=1e-3):
+        n = int(feat.shape[0])
+        loss = ctypes.c_float(0)
+        fp, kf = _ptr(feat)
+        lp, kl = _ptr(label)
+        _check(load_library().mc_mlp_train_step(self._h, fp, lp, n, pos_weight, lr, ctypes.byref(loss)),
+               "mc_mlp_train_step")
+        return loss.value

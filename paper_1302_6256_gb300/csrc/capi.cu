@@ -100,6 +100,8 @@ static void free_graph(mc_graph *g) {
   cudaFree(g->lock);
   cudaFree(g->wit);
   cudaFree(g->err);
+  if (g->graph_exec) cudaGraphExecDestroy(g->graph_exec);
+  if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
   for (auto &kv : g->ws) cudaFree(kv.second.p);
   if (g->h_small) cudaFreeHost(g->h_small);
   delete[] g->h_voff;
@@ -215,32 +217,48 @@ static float elapsed(cudaEvent_t a, cudaEvent_t b) {
   return ms;
 }
 
-// The whole of Algorithm 2 on every graph of the handle.  Leaves omega in
-// g->best and witnesses in g->wit; fills stats.
-static int run_max_clique(mc_graph *g, const mc_options *opt, mc_stats *st) {
-  mc_options o{};
-  if (opt) o = *opt;
-  if (o.ordering < 0 || o.ordering > 2 || o.heuristic < 0 || o.heuristic > 2 || o.warp_max < 0 || o.seeds < 0)
+// Record a stage event; inside capture it becomes an external event-record
+// node, so the replayed graph records it and the host can wait on it.
+static int record(mc_graph *g, int i) {
+  if (g->capturing) {
+    MC_CUDA_TRY(cudaEventRecordWithFlags(g->ev[i], g->stream, cudaEventRecordExternal));
+  } else {
+    MC_CUDA_TRY(cudaEventRecord(g->ev[i], g->stream));
+  }
+  return MC_OK;
+}
+
+// Validated copy of the options.
+static int check_options(const mc_options *opt, mc_options *o) {
+  *o = mc_options{};
+  if (opt) *o = *opt;
+  if (o->ordering < 0 || o->ordering > 2 || o->heuristic < 0 || o->heuristic > 2 || o->warp_max < 0 ||
+      o->seeds < 0 || o->graph < 0 || o->graph > 1)
     return MC_ERR_ARG;
-  if (o.ordering == 1 && !o.scores) return MC_ERR_ARG;
+  if (o->ordering == 1 && !o->scores) return MC_ERR_ARG;
+  return MC_OK;
+}
+
+// Enqueue the whole of Algorithm 2 on every graph of the handle -- core
+// numbers, heuristic, pruning, search, witness check -- without any host
+// synchronisation after the core numbers' bound (K(G), known from a previous
+// solve when capturing).  Leaves omega in g->best and witnesses in g->wit.
+static int enqueue_solve(mc_graph *g, const mc_options &o, Pruned *pg, SearchCounters *sc, int32_t **d_ok_out) {
   const long long spin = spin_of(&o);
-  int32_t warp_max = o.warp_max > 0 ? std::min(o.warp_max, 128) : 128;
-  memset(st, 0, sizeof(*st));
-  st->n = g->n;
-  st->edges = g->nnz / 2;
-  MC_CUDA_TRY(cudaEventRecord(g->ev[0], g->stream));
+  g->warp_max_used = o.warp_max > 0 ? std::min(o.warp_max, 128) : 128;
+  MC_TRY(record(g, 0));
   // every solve recomputes the core numbers (Algorithm 2, line 2)
   g->cores_valid = false;
   MC_TRY(ensure_cores(g, spin));
-  MC_CUDA_TRY(cudaEventRecord(g->ev[1], g->stream));
+  MC_TRY(record(g, 1));
   MC_CUDA_TRY(cudaMemsetAsync(g->best, 0, g->count * 4, g->stream));
   MC_CUDA_TRY(cudaMemsetAsync(g->lock, 0, g->count * 4, g->stream));
   // learned scores (host or device) -> device copy
   const float *d_scores = nullptr;
   const int32_t *d_seeds = nullptr;
   int64_t nseeds = 0;
+  void *p;
   if (o.scores && g->n > 0) {
-    void *p;
     if (is_device_ptr(o.scores)) {
       d_scores = o.scores;
     } else {
@@ -257,42 +275,52 @@ static int run_max_clique(mc_graph *g, const mc_options *opt, mc_stats *st) {
     }
   }
   if (o.heuristic != 2 && g->n > 0) MC_TRY(launch_heuristic(g, o.heuristic, spin, d_seeds, nseeds));
-  MC_CUDA_TRY(cudaEventRecord(g->ev[2], g->stream));
+  MC_TRY(record(g, 2));
   int32_t *h_heur = (int32_t *)((char *)g->h_small + 1024);
   MC_CUDA_TRY(cudaMemcpyAsync(h_heur, g->best, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
-  Pruned pg;
-  if (g->n > 0) MC_TRY(launch_prune(g, o.ordering, d_scores, warp_max, &pg, spin));
-  MC_CUDA_TRY(cudaEventRecord(g->ev[3], g->stream));
-  SearchCounters sc{};
-  if (pg.n > 0) MC_TRY(launch_search(g, pg, o.no_neigh_cores, spin, &sc));
+  if (g->n > 0) MC_TRY(launch_prune(g, o.ordering, d_scores, g->warp_max_used, pg, spin));
+  MC_TRY(record(g, 3));
+  if (g->n > 0) MC_TRY(launch_search(g, *pg, o.no_neigh_cores, spin, sc));
   trivial_kernel<<<std::max(1, std::min(g->count / 256 + 1, 1024)), 256, 0, g->stream>>>(
       g->count, g->gid ? g->voff : nullptr, g->n, g->best, g->wit);
   g_launches++;
-  MC_CUDA_TRY(cudaEventRecord(g->ev[4], g->stream));
-  void *p;
+  MC_TRY(record(g, 4));
   MC_TRY(ws_get(g, "cp.ok", (size_t)g->count * 4, &p));
-  int32_t *d_ok = (int32_t *)p;
-  MC_TRY(launch_verify(g, d_ok));
-  MC_CUDA_TRY(cudaEventRecord(g->ev[5], g->stream));
+  *d_ok_out = (int32_t *)p;
+  MC_TRY(launch_verify(g, *d_ok_out));
+  MC_TRY(record(g, 5));
+  return MC_OK;
+}
+
+// Wait for an enqueued solve and fill the statistics.
+static int finish_solve(mc_graph *g, Pruned *pg, SearchCounters *sc, const int32_t *d_ok, mc_stats *st) {
   MC_CUDA_TRY(cudaEventSynchronize(g->ev[5]));
   MC_TRY(check_device_error(g));
+  memset(st, 0, sizeof(*st));
+  st->n = g->n;
+  st->edges = g->nnz / 2;
   st->ms_cores = elapsed(g->ev[0], g->ev[1]);
   st->ms_heuristic = elapsed(g->ev[1], g->ev[2]);
   st->ms_prune = elapsed(g->ev[2], g->ev[3]);
   st->ms_search = elapsed(g->ev[3], g->ev[4]);
   st->ms_verify = elapsed(g->ev[4], g->ev[5]);
   st->ms_total = elapsed(g->ev[0], g->ev[5]);
-  st->pruned_n = pg.n;
-  st->pruned_arcs = pg.arcs;
-  st->roots = pg.nroots_small + pg.nroots_block + pg.nroots_big;
-  st->roots_colored = (int64_t)sc.roots_colored;
-  st->roots_branched = (int64_t)sc.roots_branched;
-  st->nodes = (int64_t)sc.nodes;
-  st->donations = (int64_t)sc.donations;
+  if (g->n > 0 && pg->d_counts) {
+    MC_TRY(read_pruned_counts(g, pg));
+    st->pruned_n = pg->n;
+    st->pruned_arcs = pg->arcs;
+    st->roots = pg->nroots_small + pg->nroots_block + pg->nroots_big;
+  }
+  if (g->n > 0 && sc->d_counters) {
+    MC_TRY(read_search_counters(g, sc));
+    st->roots_colored = (int64_t)sc->roots_colored;
+    st->roots_branched = (int64_t)sc->roots_branched;
+    st->nodes = (int64_t)sc->nodes;
+    st->donations = (int64_t)sc->donations;
+  }
   st->max_core = g->max_core;
-  g->heur0 = *h_heur;  // the stream has been synchronised since the copy
+  g->heur0 = *(int32_t *)((char *)g->h_small + 1024);  // copied by the solve; the stream is synchronised
   st->heuristic_size = g->heur0;
-  // all witnesses must verify
   std::vector<int32_t> ok(g->count);
   MC_CUDA_TRY(cudaMemcpy(ok.data(), d_ok, g->count * 4, cudaMemcpyDeviceToHost));
   st->verified = 1;
@@ -300,6 +328,80 @@ static int run_max_clique(mc_graph *g, const mc_options *opt, mc_stats *st) {
     if (!ok[i]) st->verified = 0;
   if (!st->verified) return MC_ERR_DEVICE_CHECK;
   return MC_OK;
+}
+
+static uint64_t options_key(const mc_options &o) {
+  uint64_t k = 1469598103934665603ULL;
+  auto mix = [&](uint64_t x) { k = (k ^ x) * 1099511628211ULL; };
+  mix((uint64_t)o.ordering);
+  mix((uint64_t)o.no_neigh_cores);
+  mix((uint64_t)o.heuristic);
+  mix((uint64_t)o.warp_max);
+  mix((uint64_t)o.spin_limit);
+  mix((uint64_t)(uintptr_t)o.scores);
+  mix((uint64_t)o.seeds);
+  return k;
+}
+
+// The whole solve.  With o.graph = 1 the enqueue is captured once into a
+// CUDA graph (after a direct solve that sizes every buffer and finds K(G))
+// and every later call with the same options replays it with one launch.
+static int run_max_clique(mc_graph *g, const mc_options *opt, mc_stats *st) {
+  mc_options o;
+  MC_TRY(check_options(opt, &o));
+  Pruned pg;
+  SearchCounters sc{};
+  int32_t *d_ok = nullptr;
+  if (!o.graph || g->n == 0) {
+    MC_TRY(enqueue_solve(g, o, &pg, &sc, &d_ok));
+    return finish_solve(g, &pg, &sc, d_ok, st);
+  }
+  const uint64_t key = options_key(o);
+  if (!g->graph_exec || g->graph_key != key) {
+    if (g->graph_exec) {
+      cudaGraphExecDestroy(g->graph_exec);
+      g->graph_exec = nullptr;
+    }
+    MC_TRY(enqueue_solve(g, o, &pg, &sc, &d_ok));  // direct solve: sizes buffers, K(G)
+    MC_TRY(finish_solve(g, &pg, &sc, d_ok, st));
+    cudaStream_t user = g->stream;
+    if (!g->cap_stream) MC_CUDA_TRY(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+    g->stream = g->cap_stream;
+    g->capturing = true;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeRelaxed);
+    int rc = (e == cudaSuccess) ? enqueue_solve(g, o, &pg, &sc, &d_ok) : MC_ERR_CUDA;
+    cudaError_t e2 = cudaStreamEndCapture(g->stream, &graph);
+    g->capturing = false;
+    g->stream = user;
+    if (rc != MC_OK) return rc;
+    if (e2 != cudaSuccess) {
+      set_last_cuda_error(e2, "cudaStreamEndCapture", __FILE__, __LINE__);
+      return MC_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&g->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      set_last_cuda_error(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+      g->graph_exec = nullptr;
+      return MC_ERR_CUDA;
+    }
+    g->graph_key = key;
+    g->graph_pg = pg;
+    g->graph_sc = sc;
+    g->graph_ok = d_ok;
+  }
+  // one launch of the captured solve, ordered after the caller's stream
+  MC_CUDA_TRY(cudaEventRecord(g->ev[6], g->stream));
+  MC_CUDA_TRY(cudaStreamWaitEvent(g->cap_stream, g->ev[6], 0));
+  MC_CUDA_TRY(cudaGraphLaunch(g->graph_exec, g->cap_stream));
+  g_launches++;
+  MC_CUDA_TRY(cudaEventRecord(g->ev[7], g->cap_stream));
+  MC_CUDA_TRY(cudaStreamWaitEvent(g->stream, g->ev[7], 0));
+  MC_CUDA_TRY(cudaStreamSynchronize(g->cap_stream));
+  pg = g->graph_pg;
+  sc = g->graph_sc;
+  return finish_solve(g, &pg, &sc, g->graph_ok, st);
 }
 
 }  // namespace mc

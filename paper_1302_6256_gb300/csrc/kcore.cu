@@ -311,6 +311,10 @@ int launch_core_numbers(mc_graph *g, long long spin_limit) {
   peel_pos_kernel<<<ib, 256, 0, g->stream>>>(n, g->order, g->pos, g->core, maxdeg + 1);
   g_launches++;
   MC_CUDA_TRY(cudaGetLastError());
+  if (g->capturing) {  // K(G) and the degree bound are kept from the direct solve before capture
+    g->cores_valid = true;
+    return MC_OK;
+  }
   int32_t *host = (int32_t *)g->h_small;
   MC_CUDA_TRY(cudaMemcpyAsync(host, maxdeg, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
   MC_CUDA_TRY(cudaStreamSynchronize(g->stream));

@@ -52,35 +52,6 @@ enum DevErr : int {
 
 }  // namespace mc
 
-struct mc_graph {
-  int64_t n = 0, nnz = 0;
-  int32_t count = 1;
-  int device = 0, sm_count = 0;
-  cudaStream_t stream = nullptr;
-  bool borrowed = false;
-  // CSR (device)
-  int64_t *row_ptr = nullptr;
-  int32_t *col_idx = nullptr;
-  int64_t *voff = nullptr;    // count+1 (device)
-  int64_t *h_voff = nullptr;  // count+1 (host)
-  int32_t *gid = nullptr;     // n graph ids (device), nullptr for a single graph
-  int32_t max_degree = 0;
-  // core numbers cache
-  bool cores_valid = false;
-  int32_t max_core = 0;
-  int32_t heur0 = 0;  // heuristic clique size of graph 0 in the last solve
-  int32_t *core = nullptr, *order = nullptr, *pos = nullptr;  // n each (device)
-  // incumbent, one per graph: size, lock, witness area (vertex-offset indexed)
-  int32_t *best = nullptr, *lock = nullptr, *wit = nullptr;
-  // device error word and small control block
-  int32_t *err = nullptr;
-  // named workspace buffers (grown on demand, reused across calls)
-  std::map<std::string, mc::DevBuf> ws;
-  // pinned host staging for small results
-  void *h_small = nullptr;
-  cudaEvent_t ev[8] = {};
-};
-
 namespace mc {
 
 // Workspace buffer of at least `bytes` bytes under `name` (kept across calls).
@@ -114,16 +85,63 @@ struct Pruned {
   int32_t *roots_block = nullptr;
   int32_t *roots_big = nullptr;
   int32_t *odeg = nullptr;         // out-degree per pruned vertex
+  int64_t *d_counts = nullptr;     // device: [0] n', [1] arcs, [2] max out-degree, [3..5] roots per class
 };
+// No host synchronisation: sizes stay in pg.d_counts (see read_pruned_counts).
 int launch_prune(mc_graph *g, int ordering, const float *scores, int32_t warp_max, Pruned *out,
                  long long spin_limit);
+int read_pruned_counts(mc_graph *g, Pruned *out);
 
 // Search (InitialBranch + Branch) over all roots.
 struct SearchCounters {
   unsigned long long roots_colored, roots_branched, nodes, donations;
+  unsigned long long *d_counters;  // device copy, read by read_search_counters
 };
+int read_search_counters(mc_graph *g, SearchCounters *cnt);
 int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, long long spin_limit,
                   SearchCounters *counters);
+
+}  // namespace mc
+
+struct mc_graph {
+  int64_t n = 0, nnz = 0;
+  int32_t count = 1;
+  int device = 0, sm_count = 0;
+  cudaStream_t stream = nullptr;
+  bool borrowed = false;
+  // CSR (device)
+  int64_t *row_ptr = nullptr;
+  int32_t *col_idx = nullptr;
+  int64_t *voff = nullptr;    // count+1 (device)
+  int64_t *h_voff = nullptr;  // count+1 (host)
+  int32_t *gid = nullptr;     // n graph ids (device), nullptr for a single graph
+  int32_t max_degree = 0;
+  // core numbers cache
+  bool cores_valid = false;
+  int32_t max_core = 0;
+  int32_t heur0 = 0;  // heuristic clique size of graph 0 in the last solve
+  int32_t warp_max_used = 128;  // warp/block split of the current solve
+  bool capturing = false;       // inside CUDA graph capture: no host synchronisation
+  int32_t *core = nullptr, *order = nullptr, *pos = nullptr;  // n each (device)
+  // incumbent, one per graph: size, lock, witness area (vertex-offset indexed)
+  int32_t *best = nullptr, *lock = nullptr, *wit = nullptr;
+  // device error word and small control block
+  int32_t *err = nullptr;
+  // named workspace buffers (grown on demand, reused across calls)
+  std::map<std::string, mc::DevBuf> ws;
+  // pinned host staging for small results
+  void *h_small = nullptr;
+  cudaEvent_t ev[8] = {};
+  // captured solve (CUDA graph replay) and what it was captured with
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  uint64_t graph_key = 0;
+  mc::Pruned graph_pg;
+  mc::SearchCounters graph_sc{};
+  int32_t *graph_ok = nullptr;
+};
+
+namespace mc {
 
 // Witness verification of every graph's incumbent: writes per-graph flags.
 int launch_verify(mc_graph *g, int32_t *d_ok);

@@ -78,12 +78,13 @@ struct KeepG {
 };
 
 // out-degree in the oriented pruned graph (warp per vertex)
-__global__ void outdeg_kernel(int64_t np, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+__global__ void outdeg_kernel(const int64_t *__restrict__ d_np, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                               const int32_t *__restrict__ oold, const int32_t *__restrict__ nid,
                               int32_t *__restrict__ odeg, int32_t *__restrict__ maxout) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t np = *d_np;
   int lmax = 0;
   for (int64_t j = w0; j < np; j += nw) {
     int v = oold[j];
@@ -98,14 +99,15 @@ __global__ void outdeg_kernel(int64_t np, const int64_t *__restrict__ rp, const 
 
 struct PadF {
   const int32_t *odeg;
-  __device__ int64_t operator()(int64_t j) const { return (int64_t)((odeg[j] + 3) & ~3); }
+  const int64_t *np;
+  __device__ int64_t operator()(int64_t j) const { return j < *np ? (int64_t)((odeg[j] + 3) & ~3) : 0; }
 };
 struct RowG {
   int64_t *orow;
   __device__ void operator()(int64_t j, int64_t excl, int64_t) const { orow[j] = excl; }
 };
 
-__global__ void fill_kernel(int64_t np, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+__global__ void fill_kernel(const int64_t *__restrict__ d_np, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                             const int32_t *__restrict__ oold, const int32_t *__restrict__ nid,
                             const int64_t *__restrict__ orow, const int32_t *__restrict__ odeg,
                             int32_t *__restrict__ ocol, int64_t total) {
@@ -113,6 +115,7 @@ __global__ void fill_kernel(int64_t np, const int64_t *__restrict__ rp, const in
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const unsigned lt = (1u << lane) - 1u;
+  const int64_t np = *d_np;
   for (int64_t j = w0; j < np; j += nw) {
     int v = oold[j];
     int64_t out = orow[j];
@@ -132,13 +135,13 @@ __global__ void fill_kernel(int64_t np, const int64_t *__restrict__ rp, const in
   (void)total;
 }
 
-__global__ void orow_end_kernel(int64_t np, int64_t *orow, const int64_t *total) { orow[np] = *total; }
 
 // root flags and classes
 struct RootInfo {
   const int32_t *odeg, *ogid, *best;
   int32_t warp_max;
   __device__ int cls(int64_t j) const {
+    if (j < 0) return -1;
     int g = ogid ? ogid[j] : 0;
     int d = odeg[j];
     if (d < best[g] || d == 0) return -1;  // |P| >= omega~ is needed for a larger clique
@@ -148,12 +151,13 @@ struct RootInfo {
 
 // index space t -> pruned vertex j for the root order
 struct PermDesc {  // ordering 0: decreasing rank (dense core first)
-  int64_t np;
-  __device__ int64_t operator()(int64_t t) const { return np - 1 - t; }
+  const int64_t *np;
+  __device__ int64_t operator()(int64_t t) const { return t < *np ? *np - 1 - t : -1; }
 };
-struct PermTable {  // ordering 1/2: explicit table
+struct PermTable {  // ordering 1/2: explicit table of np entries
   const int32_t *tab;
-  __device__ int64_t operator()(int64_t t) const { return tab[t]; }
+  const int64_t *np;
+  __device__ int64_t operator()(int64_t t) const { return t < *np ? tab[t] : -1; }
 };
 
 template <class Perm>
@@ -185,10 +189,13 @@ struct NativeG {
   }
 };
 
-__global__ void gather_scores_kernel(int64_t np, const int32_t *__restrict__ oold, const float *__restrict__ score,
-                                     float *__restrict__ key, int32_t *__restrict__ idx) {
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < np; j += (int64_t)gridDim.x * blockDim.x) {
-    key[j] = score[oold[j]];
+// score keys of the pruned vertices; slots past the pruned count sort last
+__global__ void gather_scores_kernel(int64_t n, const int64_t *__restrict__ d_np, const int32_t *__restrict__ oold,
+                                     const float *__restrict__ score, float *__restrict__ key,
+                                     int32_t *__restrict__ idx) {
+  const int64_t np = *d_np;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    key[j] = j < np ? score[oold[j]] : -3.0e38f;
     idx[j] = (int32_t)j;
   }
 }
@@ -198,6 +205,10 @@ __global__ void gather_scores_kernel(int64_t np, const int32_t *__restrict__ ool
 int launch_prune(mc_graph *g, int ordering, const float *scores, int32_t warp_max, Pruned *out,
                  long long spin_limit) {
   (void)spin_limit;
+  // Everything stays on the device: the pruned size, arc count and root
+  // counts are written to out->d_counts and read by the later kernels, and
+  // every buffer is sized for the worst case, so this step needs no host
+  // synchronisation (and can be captured into a CUDA graph).
   const int64_t n = g->n;
   void *p;
   MC_TRY(ws_get(g, "pr.nid", (n + 1) * sizeof(int32_t), &p));
@@ -212,96 +223,97 @@ int launch_prune(mc_graph *g, int ordering, const float *scores, int32_t warp_ma
     ogid = (int32_t *)p;
   }
   MC_TRY(ws_get(g, "pr.small", 16 * sizeof(int64_t), &p));
-  int64_t *dsm = (int64_t *)p;  // [0] n', [1] arcs, [2] maxout(int32 in low), [3..5] class counts
+  int64_t *dsm = (int64_t *)p;  // [0] n', [1] arcs, [2] maxout (int32 in low), [3..5] class counts
   MC_CUDA_TRY(cudaMemsetAsync(dsm, 0, 16 * sizeof(int64_t), g->stream));
+  out->d_counts = dsm;
+  out->n = n;  // upper bound until read back
+  out->oold = oold;
+  out->ocore = ocore;
+  out->ogid = ogid;
+  if (n == 0) return MC_OK;
 
   KeepF kf{g->order, g->core, g->gid, g->best};
   KeepG kg{g->order, g->core, g->gid, nid, oold, ocore, ogid};
   MC_TRY(device_scan(g, n, kf, kg, dsm + 0, "pr.scan"));
-  int64_t *h = (int64_t *)g->h_small;
-  MC_CUDA_TRY(cudaMemcpyAsync(h, dsm, sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream));
-  MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
-  const int64_t np = h[0];
-  out->n = np;
-  out->oold = oold;
-  out->ocore = ocore;
-  out->ogid = ogid;
-  out->nroots_small = out->nroots_block = out->nroots_big = 0;
-  out->arcs = 0;
-  out->max_out = 0;
-  if (np == 0) return MC_OK;
 
-  MC_TRY(ws_get(g, "pr.odeg", (np + 1) * sizeof(int32_t), &p));
+  MC_TRY(ws_get(g, "pr.odeg", (n + 1) * sizeof(int32_t), &p));
   int32_t *odeg = (int32_t *)p;
   int32_t *maxout = (int32_t *)(dsm + 2);
-  const int blocks = (int)std::min<int64_t>((np * 32 + 255) / 256, (int64_t)g->sm_count * 16);
-  outdeg_kernel<<<blocks, 256, 0, g->stream>>>(np, g->row_ptr, g->col_idx, oold, nid, odeg, maxout);
+  const int blocks = (int)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)g->sm_count * 16);
+  outdeg_kernel<<<blocks, 256, 0, g->stream>>>(dsm + 0, g->row_ptr, g->col_idx, oold, nid, odeg, maxout);
   g_launches++;
   MC_CUDA_TRY(cudaGetLastError());
-  MC_TRY(ws_get(g, "pr.orow", (np + 1) * sizeof(int64_t), &p));
+  MC_TRY(ws_get(g, "pr.orow", (n + 1) * sizeof(int64_t), &p));
   int64_t *orow = (int64_t *)p;
-  MC_TRY(device_scan(g, np, PadF{odeg}, RowG{orow}, dsm + 1, "pr.scan"));
-  orow_end_kernel<<<1, 1, 0, g->stream>>>(np, orow, dsm + 1);
-  g_launches++;
+  // n + 1 entries: rows past n' (and the end offset orow[n]) get the total,
+  // so orow[n'] is the arc count even when nothing was pruned (n' = n)
+  MC_TRY(device_scan(g, n + 1, PadF{odeg, dsm + 0}, RowG{orow}, dsm + 1, "pr.scan"));
   // worst case: every edge kept once plus row padding
-  const size_t arcs_cap = (size_t)(g->nnz / 2 + 4 * np + 4);
+  const size_t arcs_cap = (size_t)(g->nnz / 2 + 4 * n + 4);
   MC_TRY(ws_get(g, "pr.ocol", arcs_cap * sizeof(int32_t), &p));
   int32_t *ocol = (int32_t *)p;
-  fill_kernel<<<blocks, 256, 0, g->stream>>>(np, g->row_ptr, g->col_idx, oold, nid, orow, odeg, ocol, 0);
+  fill_kernel<<<blocks, 256, 0, g->stream>>>(dsm + 0, g->row_ptr, g->col_idx, oold, nid, orow, odeg, ocol, 0);
   g_launches++;
   MC_CUDA_TRY(cudaGetLastError());
 
   // roots in processing order, split by class
-  MC_TRY(ws_get(g, "pr.roots", (3 * np + 3) * sizeof(int32_t), &p));
+  MC_TRY(ws_get(g, "pr.roots", (3 * n + 3) * sizeof(int32_t), &p));
   int32_t *roots = (int32_t *)p;
   RootInfo ri{odeg, ogid, g->best, warp_max};
   int32_t *tab = nullptr;
   if (ordering == 1 || ordering == 2) {
-    MC_TRY(ws_get(g, "pr.tab", (np + 1) * sizeof(int32_t), &p));
+    MC_TRY(ws_get(g, "pr.tab", (n + 1) * sizeof(int32_t), &p));
     tab = (int32_t *)p;
   }
   if (ordering == 2) {
     MC_TRY(device_scan(g, n, NativeF{nid}, NativeG{nid, tab}, nullptr, "pr.scan"));
   } else if (ordering == 1) {
     if (!scores) return MC_ERR_ARG;
-    MC_TRY(ws_get(g, "pr.skey", (2 * np + 2) * sizeof(float), &p));
+    MC_TRY(ws_get(g, "pr.skey", (2 * n + 2) * sizeof(float), &p));
     float *skey = (float *)p;
-    MC_TRY(ws_get(g, "pr.sidx", (np + 1) * sizeof(int32_t), &p));
+    MC_TRY(ws_get(g, "pr.sidx", (n + 1) * sizeof(int32_t), &p));
     int32_t *sidx = (int32_t *)p;
-    gather_scores_kernel<<<blocks, 256, 0, g->stream>>>(np, oold, scores, skey, sidx);
+    gather_scores_kernel<<<blocks, 256, 0, g->stream>>>(n, dsm + 0, oold, scores, skey, sidx);
     g_launches++;
     size_t tmp = 0;
-    cub::DeviceRadixSort::SortPairsDescending(nullptr, tmp, skey, skey + np + 1, sidx, tab, (int)np, 0, 32,
+    cub::DeviceRadixSort::SortPairsDescending(nullptr, tmp, skey, skey + n + 1, sidx, tab, (int)n, 0, 32,
                                               g->stream);
     MC_TRY(ws_get(g, "pr.cubtmp", tmp + 16, &p));
-    MC_CUDA_TRY(cub::DeviceRadixSort::SortPairsDescending(p, tmp, skey, skey + np + 1, sidx, tab, (int)np, 0, 32,
+    MC_CUDA_TRY(cub::DeviceRadixSort::SortPairsDescending(p, tmp, skey, skey + n + 1, sidx, tab, (int)n, 0, 32,
                                                           g->stream));
     g_launches++;
   }
   for (int c = 0; c < 3; c++) {
-    int32_t *dst = roots + (int64_t)c * np;
+    int32_t *dst = roots + (int64_t)c * n;
     if (ordering == 0) {
-      MC_TRY(device_scan(g, np, ClassF<PermDesc>{ri, PermDesc{np}, c}, ClassG<PermDesc>{PermDesc{np}, dst},
-                         dsm + 3 + c, "pr.scan"));
+      MC_TRY(device_scan(g, n, ClassF<PermDesc>{ri, PermDesc{dsm + 0}, c},
+                         ClassG<PermDesc>{PermDesc{dsm + 0}, dst}, dsm + 3 + c, "pr.scan"));
     } else {
-      MC_TRY(device_scan(g, np, ClassF<PermTable>{ri, PermTable{tab}, c}, ClassG<PermTable>{PermTable{tab}, dst},
-                         dsm + 3 + c, "pr.scan"));
+      MC_TRY(device_scan(g, n, ClassF<PermTable>{ri, PermTable{tab, dsm + 0}, c},
+                         ClassG<PermTable>{PermTable{tab, dsm + 0}, dst}, dsm + 3 + c, "pr.scan"));
     }
   }
-  MC_CUDA_TRY(cudaMemcpyAsync(h, dsm, 6 * sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream));
+  out->orow = orow;
+  out->ocol = ocol;
+  out->roots = roots;
+  out->roots_small = roots;
+  out->roots_block = roots + n;
+  out->roots_big = roots + 2 * n;
+  out->odeg = odeg;
+  return MC_OK;
+}
+
+// Host copy of the pruned graph's sizes (one small device-to-host read).
+int read_pruned_counts(mc_graph *g, Pruned *out) {
+  int64_t *h = (int64_t *)g->h_small;
+  MC_CUDA_TRY(cudaMemcpyAsync(h, out->d_counts, 6 * sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream));
   MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  out->n = h[0];
   out->arcs = h[1];
   out->max_out = (int32_t)(h[2] & 0xffffffff);
   out->nroots_small = h[3];
   out->nroots_block = h[4];
   out->nroots_big = h[5];
-  out->orow = orow;
-  out->ocol = ocol;
-  out->roots = roots;
-  out->roots_small = roots;
-  out->roots_block = roots + np;
-  out->roots_big = roots + 2 * np;
-  out->odeg = odeg;
   return MC_OK;
 }
 

@@ -48,7 +48,7 @@ struct SA {
   const int64_t *orow;
   const int32_t *ocol, *ocore, *oold, *ogid;
   const int32_t *roots;
-  int64_t nroots;
+  const int64_t *nroots;    // device: number of roots in this class
   int32_t *best, *lock, *wit;
   const int64_t *voff;
   int32_t *err;
@@ -511,12 +511,13 @@ __global__ void __launch_bounds__(kSW * 32) search_warp_kernel(SA a) {
   uint32_t *stk = a.stack + gw * a.stack_stride;
   unsigned long long colored = 0, branched = 0, nodes = 0, don = 0;
   const int hmask = 2 * kWarpCap - 1;
+  const int64_t nroots = *a.nroots;
   for (;;) {
     __syncwarp();
     int idx = 0;
     if (lane == 0) idx = atomicAdd(a.next, 1);
     idx = __shfl_sync(FULL, idx, 0);
-    if (idx >= a.nroots || *(volatile int32_t *)a.err) break;
+    if (idx >= nroots || *(volatile int32_t *)a.err) break;
     const int u = a.roots[idx];
     const int g = a.ogid ? a.ogid[u] : 0;
     int om = read_best(a.best, g);
@@ -627,6 +628,7 @@ __global__ void __launch_bounds__(kBT) search_block_kernel(SA a) {
   uint32_t *stk = a.stack + ((int64_t)blockIdx.x * kBW + wid) * a.stack_stride;
   unsigned long long colored = 0, branched = 0, nodes = 0, don = 0;
   const int hmask = L::HCAP - 1;
+  const int64_t nroots = *a.nroots;
 
   for (;;) {
     __syncthreads();
@@ -636,7 +638,7 @@ __global__ void __launch_bounds__(kBT) search_block_kernel(SA a) {
     }
     __syncthreads();
     const int idx = ctl[0];
-    if (idx >= a.nroots || *(volatile int32_t *)a.err) break;
+    if (idx >= nroots || *(volatile int32_t *)a.err) break;
     const int u = a.roots[idx];
     const int g = a.ogid ? a.ogid[u] : 0;
     if (tid == 0) ctl[1] = *(volatile int32_t *)(a.best + g);
@@ -800,6 +802,9 @@ __global__ void __launch_bounds__(kBT) search_block_kernel(SA a) {
 }  // namespace
 
 int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, long long spin_limit, SearchCounters *cnt) {
+  // Persistent kernels with fixed grids; the root counts are read on the
+  // device (pg.d_counts), and sizes are bounded by K(G) >= |N+(u)|, so the
+  // launches need no host synchronisation.
   void *p;
   MC_TRY(ws_get(g, "se.ctr", 16 * sizeof(unsigned long long), &p));
   unsigned long long *ctr = (unsigned long long *)p;
@@ -819,9 +824,11 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, long long s
   a.spin = spin_limit;
   a.neigh_cores = no_neigh_cores ? 0 : 1;
   a.counters = ctr;
+  const int kbound = std::max(g->max_core, 1);  // |P| <= |N+(u)| <= K(u) <= K(G)
+  const int wmax = g->warp_max_used;
 
   // block class first (largest trees), then big, then warp class
-  if (pg.nroots_block > 0) {
+  if (kbound > wmax) {
     using L = BlockLayout<1, true>;
     const size_t smem = L::bytes;
     MC_CUDA_TRY(cudaFuncSetAttribute(search_block_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -829,27 +836,27 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, long long s
     int per_sm = 0;
     MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_block_kernel<1, true>, kBT, smem));
     if (per_sm < 1) return MC_ERR_CUDA;
-    int blocks = (int)std::min<int64_t>(pg.nroots_block, (int64_t)g->sm_count * per_sm);
-    const int pmax = std::min(pg.max_out, 1024);
+    const int blocks = g->sm_count * per_sm;
+    const int pmax = std::min(kbound, 1024);
     a.stack_stride = (int64_t)(pmax + 2) * (64 + 2);
     MC_TRY(ws_get(g, "se.stk_b", (size_t)blocks * kBW * a.stack_stride * 4, &p));
     a.stack = (uint32_t *)p;
     a.gmat = nullptr;
     a.roots = pg.roots_block;
-    a.nroots = pg.nroots_block;
+    a.nroots = pg.d_counts + 4;
     a.next = next + 0;
     search_block_kernel<1, true><<<blocks, kBT, smem, g->stream>>>(a);
     g_launches++;
     MC_CUDA_TRY(cudaGetLastError());
   }
-  if (pg.nroots_big > 0) {
-    if (pg.max_out > 4096) return MC_ERR_UNSUPPORTED;
+  if (kbound > 1024) {
+    if (kbound > 4096) return MC_ERR_UNSUPPORTED;
     using L = BlockLayout<4, false>;
     const size_t smem = L::bytes;
     MC_CUDA_TRY(cudaFuncSetAttribute(search_block_kernel<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-    int blocks = (int)std::min<int64_t>(pg.nroots_big, (int64_t)g->sm_count);
-    const int pmax = pg.max_out;
+    const int blocks = g->sm_count;
+    const int pmax = kbound;
     a.stack_stride = (int64_t)(pmax + 2) * (64 * 4 + 2);
     MC_TRY(ws_get(g, "se.stk_g", (size_t)blocks * kBW * a.stack_stride * 4, &p));
     a.stack = (uint32_t *)p;
@@ -858,30 +865,35 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, long long s
     MC_TRY(ws_get(g, "se.gmat", (size_t)blocks * a.gmat_stride * 4, &p));
     a.gmat = (uint32_t *)p;
     a.roots = pg.roots_big;
-    a.nroots = pg.nroots_big;
+    a.nroots = pg.d_counts + 5;
     a.next = next + 1;
     search_block_kernel<4, false><<<blocks, kBT, smem, g->stream>>>(a);
     g_launches++;
     MC_CUDA_TRY(cudaGetLastError());
   }
-  if (pg.nroots_small > 0) {
+  {
     int per_sm = 0;
     MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_warp_kernel, kSW * 32, 0));
     if (per_sm < 1) return MC_ERR_CUDA;
-    int blocks = (int)std::min<int64_t>((pg.nroots_small + kSW - 1) / kSW, (int64_t)g->sm_count * per_sm);
-    const int pmax = std::min(pg.max_out, kWarpCap);
+    const int blocks = g->sm_count * per_sm;
+    const int pmax = std::min(kbound, kWarpCap);
     a.stack_stride = (int64_t)(pmax + 2) * (64 + 2);
     MC_TRY(ws_get(g, "se.stk_w", (size_t)blocks * kSW * a.stack_stride * 4, &p));
     a.stack = (uint32_t *)p;
     a.roots = pg.roots_small;
-    a.nroots = pg.nroots_small;
+    a.nroots = pg.d_counts + 3;
     a.next = next + 2;
     search_warp_kernel<<<blocks, kSW * 32, 0, g->stream>>>(a);
     g_launches++;
     MC_CUDA_TRY(cudaGetLastError());
   }
+  cnt->d_counters = ctr;
+  return MC_OK;
+}
+
+int read_search_counters(mc_graph *g, SearchCounters *cnt) {
   unsigned long long *h = (unsigned long long *)g->h_small;
-  MC_CUDA_TRY(cudaMemcpyAsync(h, ctr, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, g->stream));
+  MC_CUDA_TRY(cudaMemcpyAsync(h, cnt->d_counters, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, g->stream));
   MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
   cnt->roots_colored = h[0];
   cnt->roots_branched = h[1];

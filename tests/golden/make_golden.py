@@ -33,8 +33,27 @@ def core_hash(core: np.ndarray) -> str:
     return hashlib.sha256(np.ascontiguousarray(core, dtype="<i4").tobytes()).hexdigest()
 
 
+def batch_golden(count):
+    """Oracle omega of every graph of the Erdos-Renyi batch."""
+    b = W.er_batch_4096(count)
+    t0 = time.time()
+    omegas = []
+    for g in b.graphs:
+        om, wit, _ = oracle.max_clique(g)
+        assert oracle.is_clique(g, wit) and len(wit) == om
+        omegas.append(int(om))
+    out = {"workload": b.name, "graphs": b.count, "n": b.n, "m": b.m, "omegas": omegas,
+           "oracle_s": round(time.time() - t0, 1)}
+    with open(os.path.join(HERE, "er-batch-%d.json" % count), "w") as f:
+        json.dump(out, f)
+    print("er-batch", count, "max omega", max(omegas), round(time.time() - t0, 1), flush=True)
+
+
 def main(slugs):
     for slug in slugs:
+        if slug.startswith("er-batch-"):
+            batch_golden(int(slug.split("-")[-1]))
+            continue
         name, fn = SLUGS[slug]
         g = fn()
         t0 = time.time()

@@ -224,3 +224,38 @@ def test_rmat_s22_golden(mc):
     om, wit, st = mc.mc_max_clique(h)
     assert om == gold["omega"]
     assert oracle.is_clique(g, wit)
+
+
+def test_graph_replay_single_and_batch(mc):
+    """opt graph=1: the first call solves and captures, later calls replay the
+    captured CUDA graph; every replay must give the oracle's omega."""
+    g = gg.rmat(14, 16, planted=30, seed=16)
+    h = load(mc, g)
+    for _ in range(3):
+        om, wit, st = mc.mc_max_clique(h, graph=True)
+        assert om == ref_omega(g) and oracle.is_clique(g, wit)
+    b = gg.er_batch(32, seed=3)
+    hb = mc.mc_load_batch(b.voff, b.row_ptr, b.col_idx)
+    direct, _, _ = mc.mc_max_clique_batch(hb)
+    for _ in range(3):
+        om, wits, _ = mc.mc_max_clique_batch(hb, graph=True)
+        assert np.array_equal(om, direct)
+        for i, gi in enumerate(b.graphs):
+            assert len(wits[i]) == om[i] and oracle.is_clique(gi, wits[i])
+    for i, gi in enumerate(b.graphs[:8]):
+        assert om[i] == ref_omega(gi)
+
+
+def test_big_neighbourhoods_turan(mc):
+    """Roots with more than 1024 later neighbours use the big-class worker
+    (adjacency matrix in global memory).  Turan T(1200, 300): every vertex
+    has degree 1196, omega = 300 (closed form)."""
+    g = gg.relabel(gg.turan(1200, 300), 5)
+    h = load(mc, g)
+    core, kmax = mc.mc_core_numbers(h)
+    assert kmax == 1196 and np.array_equal(core, oracle.core_numbers(g))
+    om, wit, st = mc.mc_max_clique(h)
+    assert om == 300
+    assert oracle.is_clique(g, wit)
+    om2, wit2, _ = mc.mc_max_clique(h, heuristic=2)  # no heuristic: the search finds it alone
+    assert om2 == 300 and oracle.is_clique(g, wit2)
