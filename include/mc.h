@@ -86,6 +86,11 @@ typedef struct {
    * options solves directly (sizing every buffer), then captures the solve;
    * later calls replay it with one graph launch.  0 = direct launches. */
   int32_t graph;
+  /* 1 = search each block-worker neighbourhood inside the block that built
+   * it; 0 = (default) a neighbourhood that reaches Branch publishes its
+   * adjacency matrix and its first-level branches as tasks that every block
+   * takes from one queue, so one hard neighbourhood spreads over the GPU */
+  int32_t no_split;
 } mc_options;
 
 /* Per-call statistics (all times in milliseconds, CUDA events). */
@@ -99,6 +104,9 @@ typedef struct {
   int64_t roots_branched;      /* roots that reached Branch */
   int64_t nodes;               /* Branch nodes expanded */
   int64_t donations;           /* subproblems handed to other warps */
+  int64_t neighbourhood_entries; /* later-neighbour row entries read to build the
+                                    roots' adjacency matrices (Fact 3's work) */
+  int64_t tasks;               /* first-level branches published as tasks */
   int32_t max_core, heuristic_size, omega, verified;
 } mc_stats;
 
@@ -156,6 +164,14 @@ int mc_max_clique(mc_graph *g, const mc_options *opt, int32_t *omega_out, int32_
  * voff[g]); stats nullable (summed over graphs). */
 int mc_max_clique_batch(mc_graph *g, const mc_options *opt, int32_t *omegas_out, int32_t *witness_out,
                         int64_t capacity, int64_t *witness_offsets, mc_stats *stats);
+
+/* Autotuner (an extension; the paper tunes nothing on a GPU): solves the
+ * graph `repeats` times under each candidate setting of the work split
+ * between warp and block workers (warp_max 32, 64, 128) and of CUDA-graph
+ * replay (graph 0, 1), starting from `base` (NULL = defaults), and writes the
+ * fastest setting to *best_out and its mean time (ms) to *best_ms_out
+ * (nullable).  Every trial is a full exact solve. */
+int mc_autotune(mc_graph *g, const mc_options *base, int32_t repeats, mc_options *best_out, double *best_ms_out);
 
 /* Check a vertex set on the device: *is_clique_out = 1 iff the k vertices are
  * distinct, in range and pairwise adjacent (the definition of a clique). */

@@ -46,7 +46,8 @@ class Options(ctypes.Structure):
     _fields_ = [("ordering", ctypes.c_int32), ("no_neigh_cores", ctypes.c_int32),
                 ("heuristic", ctypes.c_int32), ("warp_max", ctypes.c_int32),
                 ("spin_limit", ctypes.c_int64), ("scores", ctypes.c_void_p),
-                ("seeds", ctypes.c_int32), ("graph", ctypes.c_int32)]
+                ("seeds", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("no_split", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -57,6 +58,7 @@ class Stats(ctypes.Structure):
                 ("pruned_arcs", ctypes.c_int64), ("roots", ctypes.c_int64),
                 ("roots_colored", ctypes.c_int64), ("roots_branched", ctypes.c_int64),
                 ("nodes", ctypes.c_int64), ("donations", ctypes.c_int64),
+                ("neighbourhood_entries", ctypes.c_int64), ("tasks", ctypes.c_int64),
                 ("max_core", ctypes.c_int32), ("heuristic_size", ctypes.c_int32),
                 ("omega", ctypes.c_int32), ("verified", ctypes.c_int32)]
 
@@ -116,6 +118,8 @@ def _extend(L):
     L.mc_mlp_forward.argtypes = [vp, vp, i64, vp]
     L.mc_mlp_gradient.argtypes = [vp, vp, vp, i64, f32, vp, ctypes.POINTER(f32)]
     L.mc_mlp_train_step.argtypes = [vp, vp, vp, i64, f32, f32, ctypes.POINTER(f32)]
+    L.mc_autotune.argtypes = [vp, vp, i32, vp, ctypes.POINTER(ctypes.c_double)]
+    L.mc_autotune.restype = ctypes.c_int
     for name in ("mc_features", "mc_mlp_create", "mc_mlp_get_params", "mc_mlp_set_params", "mc_mlp_forward",
                  "mc_mlp_gradient", "mc_mlp_train_step"):
         getattr(L, name).restype = ctypes.c_int
@@ -226,9 +230,10 @@ def mc_heuristic_clique(g: Graph, mode: int = 0, core=None):
 
 
 def _options(ordering=0, no_neigh_cores=False, heuristic=0, warp_max=0, spin_limit=0, scores=None, seeds=0,
-             graph=False):
+             graph=False, no_split=False):
     o = Options()
     o.graph = 1 if graph else 0
+    o.no_split = 1 if no_split else 0
     o.ordering = ordering
     o.no_neigh_cores = 1 if no_neigh_cores else 0
     o.heuristic = heuristic
@@ -355,3 +360,13 @@ class MLP:
         _check(load_library().mc_mlp_train_step(self._h, fp, lp, n, pos_weight, lr, ctypes.byref(loss)),
                "mc_mlp_train_step")
         return loss.value
+
+
+def mc_autotune(g: Graph, repeats: int = 2, **opts):
+    """Fastest (warp_max, graph) setting for this graph; returns (options dict, ms)."""
+    L = load_library()
+    base, keep = _options(**opts)
+    best = Options()
+    ms = ctypes.c_double(0)
+    _check(L.mc_autotune(g.handle, ctypes.byref(base), repeats, ctypes.byref(best), ctypes.byref(ms)), "mc_autotune")
+    return {"warp_max": best.warp_max, "graph": bool(best.graph)}, ms.value

@@ -1,0 +1,40 @@
+"""Cached autotuning of the solve's work split and graph replay.
+
+``tuned(g, key)`` returns the options ``mc_autotune`` found fastest for a
+workload, keeping results in a JSON file (``_build/autotune.json``) keyed by
+the GPU's name and the workload key, so later runs skip the trials.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+from . import _build, mc_autotune
+
+CACHE = os.path.join(_build.BUILD, "autotune.json")
+
+
+def _gpu_name() -> str:
+    try:
+        import torch
+        return torch.cuda.get_device_name(0)
+    except Exception:
+        return "unknown"
+
+
+def tuned(g, key: str, repeats: int = 2, cache: str = CACHE, **base):
+    ck = "%s|%s" % (_gpu_name(), key)
+    data = {}
+    if os.path.exists(cache):
+        try:
+            data = json.load(open(cache))
+        except Exception:
+            data = {}
+    if ck in data:
+        return data[ck]["options"], data[ck]["ms"], True
+    opts, ms = mc_autotune(g, repeats=repeats, **base)
+    data[ck] = {"options": opts, "ms": ms}
+    os.makedirs(os.path.dirname(cache), exist_ok=True)
+    with open(cache, "w") as f:
+        json.dump(data, f, indent=1)
+    return opts, ms, False

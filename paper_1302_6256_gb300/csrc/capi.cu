@@ -4,6 +4,8 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "mc_internal.cuh"
@@ -17,6 +19,46 @@ void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int 
   snprintf(g_errbuf, sizeof(g_errbuf), "%s (%s) at %s:%d", cudaGetErrorString(e), what, file, line);
 }
 
+// Device-memory pool for workspace buffers: buffers of freed graphs are kept
+// per device and handed to the next graph that needs one of a similar size,
+// so short-lived handles (one per small graph) do not pay cudaMalloc and
+// cudaFree every time.  The pool is emptied when an allocation fails.
+namespace {
+std::mutex g_pool_mu;
+std::multimap<size_t, void *> g_pool[64];
+size_t g_pool_bytes[64];
+constexpr size_t kPoolLimit = (size_t)8 << 30;  // keep at most 8 GiB cached per device
+
+void *pool_take(int dev, size_t bytes, size_t *got) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  auto &p = g_pool[dev];
+  auto it = p.lower_bound(bytes);
+  if (it == p.end() || it->first > 2 * bytes + (1 << 20)) return nullptr;
+  void *ptr = it->second;
+  *got = it->first;
+  g_pool_bytes[dev] -= it->first;
+  p.erase(it);
+  return ptr;
+}
+
+void pool_give(int dev, void *ptr, size_t bytes) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (g_pool_bytes[dev] + bytes > kPoolLimit) {
+    cudaFree(ptr);
+    return;
+  }
+  g_pool[dev].emplace(bytes, ptr);
+  g_pool_bytes[dev] += bytes;
+}
+
+void pool_flush(int dev) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  for (auto &kv : g_pool[dev]) cudaFree(kv.second);
+  g_pool[dev].clear();
+  g_pool_bytes[dev] = 0;
+}
+}  // namespace
+
 int ws_get(mc_graph *g, const char *name, size_t bytes, void **out) {
   DevBuf &b = g->ws[name];
   if (bytes == 0) bytes = 16;
@@ -27,14 +69,22 @@ int ws_get(mc_graph *g, const char *name, size_t bytes, void **out) {
   if (b.p) {
     cudaError_t e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return MC_ERR_CUDA;
-    cudaFree(b.p);
+    pool_give(g->device, b.p, b.bytes);
     b.p = nullptr;
     b.bytes = 0;
+  }
+  size_t got = 0;
+  if (void *p = pool_take(g->device, bytes, &got)) {
+    b.p = p;
+    b.bytes = got;
+    *out = p;
+    return MC_OK;
   }
   size_t want = bytes + bytes / 8;
   cudaError_t e = cudaMalloc(&b.p, want);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    pool_flush(g->device);
     e = cudaMalloc(&b.p, bytes);
     want = bytes;
   }
@@ -102,7 +152,8 @@ static void free_graph(mc_graph *g) {
   cudaFree(g->err);
   if (g->graph_exec) cudaGraphExecDestroy(g->graph_exec);
   if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
-  for (auto &kv : g->ws) cudaFree(kv.second.p);
+  for (auto &kv : g->ws)
+    if (kv.second.p) pool_give(g->device, kv.second.p, kv.second.bytes);
   if (g->h_small) cudaFreeHost(g->h_small);
   delete[] g->h_voff;
   for (auto &e : g->ev)
@@ -178,11 +229,14 @@ static int load_common(int32_t count, const int64_t *voff_in, int64_t n, const i
         cudaStreamSynchronize(g->stream) != cudaSuccess)
       return fail(MC_ERR_ARG);
     if (g->h_voff[0] != 0 || g->h_voff[count] != n) return fail(MC_ERR_ARG);
-    for (int32_t i = 0; i < count; i++)
+    for (int32_t i = 0; i < count; i++) {
       if (g->h_voff[i + 1] < g->h_voff[i]) return fail(MC_ERR_ARG);
+      g->max_graph_n = std::max<int64_t>(g->max_graph_n, g->h_voff[i + 1] - g->h_voff[i]);
+    }
   } else {
     g->h_voff[0] = 0;
     g->h_voff[1] = n;
+    g->max_graph_n = n;
   }
   if (cudaMemcpyAsync(g->voff, g->h_voff, (count + 1) * 8, cudaMemcpyHostToDevice, g->stream) != cudaSuccess)
     return fail(MC_ERR_CUDA);
@@ -233,7 +287,7 @@ static int check_options(const mc_options *opt, mc_options *o) {
   *o = mc_options{};
   if (opt) *o = *opt;
   if (o->ordering < 0 || o->ordering > 2 || o->heuristic < 0 || o->heuristic > 2 || o->warp_max < 0 ||
-      o->seeds < 0 || o->graph < 0 || o->graph > 1)
+      o->seeds < 0 || o->graph < 0 || o->graph > 1 || o->no_split < 0 || o->no_split > 1)
     return MC_ERR_ARG;
   if (o->ordering == 1 && !o->scores) return MC_ERR_ARG;
   return MC_OK;
@@ -280,7 +334,7 @@ static int enqueue_solve(mc_graph *g, const mc_options &o, Pruned *pg, SearchCou
   MC_CUDA_TRY(cudaMemcpyAsync(h_heur, g->best, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
   if (g->n > 0) MC_TRY(launch_prune(g, o.ordering, d_scores, g->warp_max_used, pg, spin));
   MC_TRY(record(g, 3));
-  if (g->n > 0) MC_TRY(launch_search(g, *pg, o.no_neigh_cores, spin, sc));
+  if (g->n > 0) MC_TRY(launch_search(g, *pg, o.no_neigh_cores, o.no_split, spin, sc));
   trivial_kernel<<<std::max(1, std::min(g->count / 256 + 1, 1024)), 256, 0, g->stream>>>(
       g->count, g->gid ? g->voff : nullptr, g->n, g->best, g->wit);
   g_launches++;
@@ -317,6 +371,8 @@ static int finish_solve(mc_graph *g, Pruned *pg, SearchCounters *sc, const int32
     st->roots_branched = (int64_t)sc->roots_branched;
     st->nodes = (int64_t)sc->nodes;
     st->donations = (int64_t)sc->donations;
+    st->neighbourhood_entries = (int64_t)sc->entries;
+    st->tasks = (int64_t)sc->tasks;
   }
   st->max_core = g->max_core;
   g->heur0 = *(int32_t *)((char *)g->h_small + 1024);  // copied by the solve; the stream is synchronised
@@ -340,6 +396,7 @@ static uint64_t options_key(const mc_options &o) {
   mix((uint64_t)o.spin_limit);
   mix((uint64_t)(uintptr_t)o.scores);
   mix((uint64_t)o.seeds);
+  mix((uint64_t)o.no_split);
   return k;
 }
 
@@ -537,6 +594,38 @@ int mc_max_clique_batch(mc_graph *g, const mc_options *opt, int32_t *omegas_out,
   }
   if (off[g->count] > 0)
     MC_CUDA_TRY(cudaMemcpy(witness_out, outv.data(), off[g->count] * 4, cudaMemcpyDefault));
+  return MC_OK;
+}
+
+int mc_autotune(mc_graph *g, const mc_options *base, int32_t repeats, mc_options *best_out, double *best_ms_out) {
+  if (!g || !best_out || repeats < 1) return MC_ERR_ARG;
+  mc_options b;
+  MC_TRY(check_options(base, &b));
+  // candidate settings: warp/block split of the roots x direct or replayed graph
+  const int32_t splits[] = {32, 64, 128};
+  double best = 1e300;
+  mc_options bo = b;
+  mc_stats st;
+  for (int gi = 0; gi < 2; gi++) {
+    for (int32_t wm : splits) {
+      mc_options o = b;
+      o.warp_max = wm;
+      o.graph = gi;
+      MC_TRY(run_max_clique(g, &o, &st));  // warm-up (and capture, for graph replay)
+      double tot = 0.0;
+      for (int r = 0; r < repeats; r++) {
+        MC_TRY(run_max_clique(g, &o, &st));
+        tot += st.ms_total;
+      }
+      const double ms = tot / repeats;
+      if (ms < best) {
+        best = ms;
+        bo = o;
+      }
+    }
+  }
+  *best_out = bo;
+  if (best_ms_out) *best_ms_out = best;
   return MC_OK;
 }
 

@@ -49,6 +49,11 @@ struct HA {
   const int32_t *seeds;
   int64_t nseeds;
   int64_t begin, limit;  // start vertices [begin, limit) of the visiting order in this launch
+  // batches peeled graph by graph: visit the j-th highest vertex of every
+  // graph before the (j+1)-th of any, so each graph's maximum is set early
+  int32_t count;
+  int64_t max_graph_n;
+  int interleave;
 };
 
 struct Key {
@@ -185,7 +190,17 @@ __global__ void __launch_bounds__(kHT) heuristic_kernel(HA a) {
     if (lane == 0) i = a.begin + atomicAdd(a.next, 1);
     i = __shfl_sync(FULL, (long long)i, 0);
     if (i >= total || *(volatile int32_t *)a.err) break;
-    const int v = (i < a.nseeds) ? a.seeds[i] : a.order[a.n - 1 - (i - a.nseeds)];
+    int v;
+    if (i < a.nseeds) {
+      v = a.seeds[i];
+    } else if (a.interleave) {
+      const int64_t r = i - a.nseeds, gi = r % a.count, j = r / a.count;
+      const int64_t v0 = a.voff[gi], v1 = a.voff[gi + 1];
+      if (j >= v1 - v0) continue;
+      v = a.order[v1 - 1 - j];
+    } else {
+      v = a.order[a.n - 1 - (i - a.nseeds)];
+    }
     const int g = a.gid ? a.gid[v] : 0;
     const int kv = a.core[v];
     if (a.mode == 0) {
@@ -281,8 +296,11 @@ int launch_heuristic(mc_graph *g, int mode, long long spin_limit, const int32_t 
   a.detkey = detkey;
   a.seeds = seeds;
   a.nseeds = seeds ? nseeds : 0;
+  a.count = g->count;
+  a.max_graph_n = g->max_graph_n;
+  a.interleave = (g->count > 1 && g->max_graph_n <= kBatchPeelCap) ? 1 : 0;
   const int blocks = (int)((warps * 32 + kHT - 1) / kHT);
-  const int64_t total = g->n + a.nseeds;
+  const int64_t total = a.interleave ? (int64_t)g->count * g->max_graph_n + a.nseeds : g->n + a.nseeds;
   a.begin = 0;
   a.limit = total;
   heuristic_kernel<<<blocks, kHT, 0, g->stream>>>(a);

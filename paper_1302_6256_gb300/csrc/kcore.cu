@@ -265,6 +265,126 @@ __global__ void peel_pos_kernel(int64_t n, const int32_t *__restrict__ order, in
   }
 }
 
+// Batches of small graphs: one block peels one whole graph at a time
+// (degrees in shared memory, shared-memory atomics, block barriers between
+// sub-rounds), blocks taking graphs from a counter.  The peel order of graph
+// g is written to order[voff[g] ..), so each graph's segment is its own
+// degeneracy order.
+constexpr int kBatchCap = (int)kBatchPeelCap;  // largest graph this kernel takes
+constexpr int kBatchThreads = 512;
+
+__global__ void __launch_bounds__(kBatchThreads) kcore_batch_kernel(int32_t count, const int64_t *__restrict__ voff,
+                                                                    const int64_t *__restrict__ rp,
+                                                                    const int32_t *__restrict__ ci,
+                                                                    int32_t *__restrict__ core,
+                                                                    int32_t *__restrict__ order, int32_t *next,
+                                                                    int32_t *maxdeg, int32_t *maxcore, int32_t *err) {
+  __shared__ int deg[kBatchCap];
+  __shared__ int q[kBatchCap];
+  __shared__ int s_g, s_tail, s_min;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = kBatchThreads / 32;
+  const unsigned lt = (1u << lane) - 1u;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) s_g = atomicAdd(next, 1);
+    __syncthreads();
+    const int g = s_g;
+    if (g >= count) break;
+    const int64_t v0 = voff[g];
+    const int ng = (int)(voff[g + 1] - v0);
+    int lmax = 0;
+    for (int i = tid; i < ng; i += kBatchThreads) {
+      deg[i] = (int)(rp[v0 + i + 1] - rp[v0 + i]);
+      lmax = max(lmax, deg[i]);
+    }
+    lmax = dev::warp_max(lmax);
+    if (lane == 0) atomicMax(maxdeg, lmax);
+    if (tid == 0) s_tail = 0;
+    __syncthreads();
+    int k = 0, head = 0, kmax_g = 0;
+    while (true) {
+      // scan: every unpeeled vertex with degree == k joins the level
+      __syncthreads();  // everyone has read s_min / s_tail of the last level
+      if (tid == 0) s_min = INT_MAX;
+      __syncthreads();
+      int lmin = INT_MAX;
+      for (int b = wid * 32; b < ng; b += kBatchThreads) {
+        const int i = b + lane;
+        const int d = (i < ng) ? deg[i] : INT_MIN;
+        const bool hit = d == k;
+        if (d > k) lmin = min(lmin, d);
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (m) {
+          int base = 0;
+          if (lane == 0) base = atomicAdd(&s_tail, __popc(m));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (hit) {
+            q[base + __popc(m & lt)] = i;
+            core[v0 + i] = k;
+          }
+        }
+      }
+      lmin = -dev::warp_max(-lmin);
+      if (lane == 0 && lmin != INT_MAX) atomicMin(&s_min, lmin);
+      __syncthreads();
+      int tail = s_tail;
+      if (tail == head) {  // nothing at level k
+        if (s_min == INT_MAX) break;  // every vertex peeled
+        k = s_min;
+        continue;
+      }
+      kmax_g = k;
+      // sub-rounds: warps walk the rows of q[head, tail); neighbours that fall
+      // to k join q for the next sub-round
+      while (head < tail) {
+        for (int j = head + wid; j < tail; j += nw) {
+          const int i = q[j];
+          const int64_t e0 = rp[v0 + i], e1 = rp[v0 + i + 1];
+          for (int64_t eb = e0; eb < e1; eb += 32) {
+            const int64_t e = eb + lane;
+            bool nf = false;
+            int u = -1;
+            if (e < e1) {
+              u = (int)(ci[e] - v0);
+              if ((unsigned)u >= (unsigned)ng) {  // an edge leaving the graph: not a valid batch
+                atomicExch(err, kDevCheck);
+                u = -1;
+              } else if (deg[u] > k) {
+                nf = (atomicSub(&deg[u], 1) == k + 1);
+              }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, nf);
+            if (m) {
+              int base = 0;
+              if (lane == 0) base = atomicAdd(&s_tail, __popc(m));
+              base = __shfl_sync(0xffffffffu, base, 0);
+              if (nf) {
+                q[base + __popc(m & lt)] = u;
+                core[v0 + u] = k;
+              }
+            }
+          }
+        }
+        __syncthreads();
+        head = tail;
+        tail = s_tail;
+        __syncthreads();
+      }
+      k++;
+    }
+    // the queue is the graph's peel order (core numbers were written on append)
+    __syncthreads();
+    for (int j = tid; j < ng; j += kBatchThreads) order[v0 + j] = (int32_t)(v0 + q[j]);
+    if (tid == 0) atomicMax(maxcore, kmax_g);
+    __syncthreads();
+  }
+}
+
+__global__ void batch_pos_kernel(int64_t n, const int32_t *__restrict__ order, int32_t *__restrict__ pos) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    pos[order[i]] = (int32_t)i;
+}
+
 }  // namespace
 
 int launch_core_numbers(mc_graph *g, long long spin_limit) {
@@ -275,6 +395,32 @@ int launch_core_numbers(mc_graph *g, long long spin_limit) {
     return MC_OK;
   }
   void *p;
+  if (g->count > 1 && g->max_graph_n <= kBatchCap) {
+    MC_TRY(ws_get(g, "kc.bctl", 64, &p));
+    int32_t *bctl = (int32_t *)p;  // [0] graph counter, [1] max degree, [2] max core
+    MC_CUDA_TRY(cudaMemsetAsync(bctl, 0, 64, g->stream));
+    int per_sm = 0;
+    MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kcore_batch_kernel, kBatchThreads, 0));
+    const int blocks = (int)std::min<int64_t>(g->count, (int64_t)g->sm_count * std::max(per_sm, 1));
+    kcore_batch_kernel<<<blocks, kBatchThreads, 0, g->stream>>>(g->count, g->voff, g->row_ptr, g->col_idx, g->core,
+                                                                g->order, bctl, bctl + 1, bctl + 2, g->err);
+    batch_pos_kernel<<<(int)std::min<int64_t>((n + 255) / 256, (int64_t)g->sm_count * 8), 256, 0, g->stream>>>(
+        n, g->order, g->pos);
+    g_launches += 2;
+    MC_CUDA_TRY(cudaGetLastError());
+    if (g->capturing) {
+      g->cores_valid = true;
+      return MC_OK;
+    }
+    int32_t *host = (int32_t *)g->h_small;
+    MC_CUDA_TRY(cudaMemcpyAsync(host, bctl + 1, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
+    MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    MC_TRY(check_device_error(g));
+    g->max_degree = host[0];
+    g->max_core = host[1];
+    g->cores_valid = true;
+    return MC_OK;
+  }
   MC_TRY(ws_get(g, "kc.deg", n * sizeof(int32_t), &p));
   int32_t *deg = (int32_t *)p;
   MC_TRY(ws_get(g, "kc.live", 2 * n * sizeof(int32_t) + 64, &p));

@@ -33,6 +33,10 @@ extern std::atomic<int64_t> g_launches;
 
 void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
 
+// Batches whose graphs all have at most this many vertices are peeled one
+// graph per block (kcore.cu); their peel order is one segment per graph.
+constexpr int64_t kBatchPeelCap = 4096;
+
 // Default device spin-wait limit (iterations of a ~100 ns back-off loop).
 constexpr long long kDefaultSpinLimit = 100000000LL;
 
@@ -94,11 +98,11 @@ int read_pruned_counts(mc_graph *g, Pruned *out);
 
 // Search (InitialBranch + Branch) over all roots.
 struct SearchCounters {
-  unsigned long long roots_colored, roots_branched, nodes, donations;
+  unsigned long long roots_colored, roots_branched, nodes, donations, entries, tasks;
   unsigned long long *d_counters;  // device copy, read by read_search_counters
 };
 int read_search_counters(mc_graph *g, SearchCounters *cnt);
-int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, long long spin_limit,
+int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_split, long long spin_limit,
                   SearchCounters *counters);
 
 }  // namespace mc
@@ -116,6 +120,7 @@ struct mc_graph {
   int64_t *h_voff = nullptr;  // count+1 (host)
   int32_t *gid = nullptr;     // n graph ids (device), nullptr for a single graph
   int32_t max_degree = 0;
+  int64_t max_graph_n = 0;  // largest graph of a batch
   // core numbers cache
   bool cores_valid = false;
   int32_t max_core = 0;

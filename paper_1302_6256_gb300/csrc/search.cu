@@ -59,8 +59,29 @@ struct SA {
   uint32_t *gmat;           // per-block global matrix (big class)
   int64_t gmat_stride;      // words per block matrix
   int32_t neigh_cores;
-  unsigned long long *counters;  // colored, branched, nodes, donations
+  unsigned long long *counters;  // colored, branched, nodes, donations, entries
+  // published roots: matrix + P list in a global arena, first-level tasks
+  uint32_t *arena;
+  long long arena_cap;           // words
+  unsigned long long *arena_used;
+  struct RootRec *recs;
+  int32_t rec_cap;
+  int32_t *nrec;
+  uint32_t *tasks;               // kTaskWords words per task
+  int32_t task_cap;
+  int32_t *ntasks;
+  int32_t *task_next;
 };
+
+struct RootRec {
+  int u, g, p, W, Ws, pad;
+  long long off;  // arena word offset: matrix (p x Ws words), then the P list (p ints)
+};
+constexpr int kTaskWords = 2 + 64;  // root record, clique size, C bits, P bits (32 words each)
+constexpr long long kArenaWords = 64ll << 20;  // 256 MB of published matrices
+constexpr int kRecCap = 1 << 16;
+constexpr int kTaskCap = 1 << 17;          // 34.6 MB of tasks
+constexpr long long kSpillNodes = 4096;    // Branch nodes a lone warp expands before it spills
 
 template <int WPL>
 struct Bits {
@@ -290,7 +311,142 @@ __device__ void pool_unlock(Pool<WPL> *pl) {
 struct Root {
   int u, g;
   const int32_t *Pidx;
+  int p;  // |P|: rows of the root's matrix
 };
+
+// Take k consecutive task slots, all or none; returns the first or -1.
+__device__ int reserve_tasks(const SA &a, int k) {
+  int cur = *(volatile int32_t *)a.ntasks;
+  for (long long it = 0; it < a.spin; it++) {
+    if (cur + k > a.task_cap) return -1;
+    const int prev = atomicCAS(a.ntasks, cur, cur + k);
+    if (prev == cur) return cur;
+    cur = prev;
+  }
+  return -1;
+}
+
+// Reserve arena room and a record for a root's matrix and P list.  Returns
+// the record index (and the arena offset) or -1 without room.
+__device__ int reserve_record(const SA &a, const Root &r, int Ws, long long *off_out) {
+  const long long need = (long long)r.p * Ws + r.p;
+  const long long off = (long long)atomicAdd(a.arena_used, (unsigned long long)need);
+  if (off + need > a.arena_cap) return -1;
+  const int rec = atomicAdd(a.nrec, 1);
+  if (rec >= a.rec_cap) return -1;
+  *off_out = off;
+  return rec;
+}
+
+// Copy a root's matrix and P list to its arena room and write its record,
+// over nthr threads starting at thread t.
+__device__ void write_record(const SA &a, const Root &r, const uint32_t *A, int Ws, int W, int rec, long long off,
+                             int t, int nthr) {
+  uint32_t *dm = a.arena + off;
+  for (int i = t; i < r.p * Ws; i += nthr) dm[i] = A[i];
+  int *dp = (int *)(dm + (int64_t)r.p * Ws);
+  for (int i = t; i < r.p; i += nthr) dp[i] = r.Pidx[i];
+  if (t == 0) {
+    RootRec rr;
+    rr.u = r.u;
+    rr.g = r.g;
+    rr.p = r.p;
+    rr.W = W;
+    rr.Ws = Ws;
+    rr.pad = 0;
+    rr.off = off;
+    a.recs[rec] = rr;
+  }
+}
+
+// One task: the branch x of a node with clique Cl (csl vertices with u) and
+// candidates Pl (x and its earlier siblings already removed).  Writes the
+// task to slot t, or an empty task when x's subproblem is decided at once
+// (raising the incumbent if {u} + Cl + x is a larger maximal clique).
+template <int WPL, bool SM>
+__device__ void emit_task(const SA &a, const Root &r, const uint32_t *A, int Ws, int W, int rec, int t,
+                          const Bits<WPL> &Cl, int csl, const Bits<WPL> &Pl, int x) {
+  const int lane = threadIdx.x & 31;
+  Bits<WPL> TP = Pl;
+  band_row<WPL, SM>(TP, A, Ws, W, x);
+  const int om = read_best(a.best, r.g);
+  int live = 1;
+  if (!bany(TP)) {
+    live = 0;
+    if (csl + 1 > om) {
+      const Bits<WPL> Cc = Cl;
+      dev::raise_incumbent(a.best, a.lock, a.wit, a.voff, r.g, csl + 1, a.err, a.spin,
+                           [&](int, int32_t *base) { write_clique<WPL>(base, Cc, x, r.Pidx, a.oold, r.u); });
+    }
+  } else if (csl + 1 + bcount(TP) <= om) {
+    live = 0;
+  }
+  uint32_t *tk = a.tasks + (int64_t)t * kTaskWords;
+  if (lane == 0) {
+    tk[0] = (uint32_t)rec;
+    tk[1] = live ? (uint32_t)(csl + 1) : 0u;  // 0 = empty task
+  }
+  Bits<WPL> Cx = Cl;
+  bset(Cx, x);
+#pragma unroll
+  for (int k = 0; k < WPL; k++) {
+    tk[2 + k * 32 + lane] = Cx.w[k];
+    tk[34 + k * 32 + lane] = TP.w[k];
+  }
+}
+
+// Hand the untried rest of one warp's depth-first search to the task queue:
+// every untried branch at each stored level and at the current level becomes
+// a task.  All or nothing: returns false, publishing nothing, without room.
+template <int WPL, bool SM>
+__device__ bool spill_frontier(const SA &a, const Root &r, const uint32_t *A, int Ws, int W, const uint32_t *stk,
+                               int d, int csize0, Bits<WPL> P, Bits<WPL> B, Bits<WPL> C) {
+  const int lane = threadIdx.x & 31;
+  const int stride = 64 * WPL + 2;
+  int ntask = bcount(B);
+  for (int l = 0; l < d; l++) {
+    Bits<WPL> Bl;
+#pragma unroll
+    for (int k = 0; k < WPL; k++) Bl.w[k] = stk[(int64_t)l * stride + 32 * WPL + k * 32 + lane];
+    ntask += bcount(Bl);
+  }
+  int rec = -1, t0 = -1;
+  long long off = 0;
+  if (lane == 0 && ntask > 0) {
+    rec = reserve_record(a, r, Ws, &off);
+    if (rec >= 0) t0 = reserve_tasks(a, ntask);
+  }
+  t0 = __shfl_sync(FULL, t0, 0);
+  if (t0 < 0) return false;
+  rec = __shfl_sync(FULL, rec, 0);
+  off = __shfl_sync(FULL, off, 0);
+  write_record(a, r, A, Ws, W, rec, off, lane, 32);
+  int t = t0;
+  for (int l = 0; l <= d; l++) {
+    Bits<WPL> Pl, Bl, Cl = C;
+    if (l < d) {
+      const uint32_t *q = stk + (int64_t)l * stride;
+#pragma unroll
+      for (int k = 0; k < WPL; k++) {
+        Pl.w[k] = q[k * 32 + lane];
+        Bl.w[k] = q[32 * WPL + k * 32 + lane];
+      }
+      for (int m = l; m < d; m++) bclear(Cl, (int)stk[(int64_t)m * stride + 64 * WPL + 1]);
+    } else {
+      Pl = P;
+      Bl = B;
+    }
+    for (;;) {
+      const int x = bhighest(Bl);
+      if (x < 0) break;
+      bclear(Bl, x);
+      bclear(Pl, x);
+      emit_task<WPL, SM>(a, r, A, Ws, W, rec, t++, Cl, csize0 + l, Pl, x);
+    }
+  }
+  __threadfence();
+  return true;
+}
 
 // Depth-first Branch from one level (csize0 = |C| including the root u).
 // Stack levels above the start hold (P, B, omega-at-colouring, chosen).
@@ -298,16 +454,25 @@ struct Root {
 template <int WPL, bool SM>
 __device__ void dfs(const SA &a, const Root &r, const uint32_t *A, int Ws, int W, uint32_t *stk, int csize0,
                     Bits<WPL> P, Bits<WPL> B, Bits<WPL> C, int wat, Pool<WPL> *pool, unsigned long long &nodes,
-                    unsigned long long &donations) {
+                    unsigned long long &donations, long long budget = 0) {
   const int lane = threadIdx.x & 31;
   const int stride = 64 * WPL + 2;
   int d = 0, csize = csize0;
+  long long spent = 0;
   for (;;) {
     if (*(volatile int32_t *)a.err) return;
     int om = read_best(a.best, r.g);
     if (om > wat) {
       color_ise<WPL, SM>(A, Ws, W, P, om - csize, B);
       wat = om;
+    }
+    if constexpr (WPL == 1) {
+      if (budget > 0 && spent > budget) {
+        // past its node budget a lone warp hands the rest of the tree to the
+        // task queue, where whole blocks search it
+        if (spill_frontier<WPL, SM>(a, r, A, Ws, W, stk, d, csize0, P, B, C)) return;
+        budget = 0;
+      }
     }
     int v = bhighest(B);
     if (v < 0) {
@@ -330,6 +495,7 @@ __device__ void dfs(const SA &a, const Root &r, const uint32_t *A, int Ws, int W
     Bits<WPL> NP = P;
     band_row<WPL, SM>(NP, A, Ws, W, v);
     nodes++;
+    spent++;
     if (!bany(NP)) {
       if (csize + 1 > om) {
         const Bits<WPL> Cc = C;
@@ -467,29 +633,54 @@ __device__ __forceinline__ void load_P(const SA &a, int u, int om, int *Pidx, in
 }
 
 // Matrix rows of P: for each member x (index i), every later neighbour y of x
-// that is in P (index j) sets bits (i, j) and (j, i).
+// that is in P (index j) sets bits (i, j) and (j, i).  The lanes of a warp
+// form four groups of eight, each walking a different member's row, with two
+// int4 loads per lane in flight, so a warp keeps eight rows' loads in the
+// memory system instead of one.
 __device__ __forceinline__ void build_rows(const SA &a, const int *Pidx, int p, const int *hk, const short *hv,
                                            int hmask, uint32_t *A, int Ws, int wid, int nw) {
   const int lane = threadIdx.x & 31;
-  for (int i = wid; i < p; i += nw) {
-    const int x = Pidx[i];
-    const int64_t e0 = a.orow[x], e1 = a.orow[x + 1];
+  const int grp = lane >> 3, gl = lane & 7;
+  unsigned long long scanned = 0;
+  for (int i0 = wid * 4; i0 < p; i0 += nw * 4) {
+    const int i = i0 + grp;
+    int64_t e0 = 0, e1 = 0;
+    if (i < p) {
+      const int x = Pidx[i];
+      e0 = a.orow[x];
+      e1 = a.orow[x + 1];
+    }
     const int4 *row = reinterpret_cast<const int4 *>(a.ocol + e0);
-    const int64_t nq = (e1 - e0) >> 2;
-    for (int64_t q = lane; q < nq; q += 32) {
-      int4 y = __ldg(row + q);
-      int ys[4] = {y.x, y.y, y.z, y.w};
+    const int nq = (int)((e1 - e0) >> 2);
+    const int nqmax = max(max(__shfl_sync(FULL, nq, 0), __shfl_sync(FULL, nq, 8)),
+                          max(__shfl_sync(FULL, nq, 16), __shfl_sync(FULL, nq, 24)));
+    if (gl == 0) scanned += 4ull * (unsigned long long)nq;
+    for (int q0 = gl; q0 < nqmax; q0 += 16) {
+      int4 ys[2];
 #pragma unroll
-      for (int j = 0; j < 4; j++) {
-        if (ys[j] < 0) continue;
-        int b = hash_find(hk, hv, hmask, ys[j]);
-        if (b >= 0) {
-          atomicOr(A + (int64_t)i * Ws + (b >> 5), 1u << (b & 31));
-          atomicOr(A + (int64_t)b * Ws + (i >> 5), 1u << (i & 31));
+      for (int u = 0; u < 2; u++) {
+        const int q = q0 + 8 * u;
+        ys[u] = (q < nq) ? __ldg(row + q) : make_int4(-1, -1, -1, -1);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        const int yy[4] = {ys[u].x, ys[u].y, ys[u].z, ys[u].w};
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          if (yy[j] < 0) continue;
+          int b = hash_find(hk, hv, hmask, yy[j]);
+          if (b >= 0) {
+            atomicOr(A + (int64_t)i * Ws + (b >> 5), 1u << (b & 31));
+            atomicOr(A + (int64_t)b * Ws + (i >> 5), 1u << (i & 31));
+          }
         }
       }
     }
   }
+  // row entries scanned (Fact 3's work), one atomic per warp
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) scanned += __shfl_xor_sync(FULL, scanned, o);
+  if (lane == 0 && scanned) atomicAdd(a.counters + 4, scanned);
 }
 
 // ------------------------------------------------------------ warp class ---
@@ -582,8 +773,9 @@ __global__ void __launch_bounds__(kSW * 32) search_warp_kernel(SA a) {
     branched++;
     Bits<1> C;
     bzero(C);
-    Root r{u, g, S.Pidx};
-    dfs<1, true>(a, r, S.A, Ws, W, stk, 1, al, B, C, om, (Pool<1> *)nullptr, nodes, don);
+    Root r{u, g, S.Pidx, p};
+    dfs<1, true>(a, r, S.A, Ws, W, stk, 1, al, B, C, om, (Pool<1> *)nullptr, nodes, don,
+                 a.tasks ? kSpillNodes : 0);
   }
   if (lane == 0) {
     atomicAdd(a.counters + 0, colored);
@@ -611,6 +803,84 @@ struct BlockLayout {
   static constexpr size_t off_A = off_ctl + 64;
   static constexpr size_t bytes = off_A + (SM ? (size_t)PCAP * WSMAX * 4 : 0);
 };
+
+// The warps of a block search one root (or one task) together: warps that
+// hold work run the depth-first Branch and hand untried branches to idle
+// warps through the block's pool; the call returns when the pool is empty
+// and every warp is idle.  All warps of the block call it.
+template <int WPL, bool SM>
+__device__ void block_search(const SA &a, const Root &r, const uint32_t *A, int Ws, int W, uint32_t *stk,
+                             Pool<WPL> *pool, bool have, Bits<WPL> P, Bits<WPL> B, Bits<WPL> C, int cs, int wat,
+                             unsigned long long &nodes, unsigned long long &don) {
+  const int lane = threadIdx.x & 31;
+  const int g = r.g;
+  long long waited = 0;
+  int lastbeat = -1;
+  for (;;) {
+    if (have) {
+      dfs<WPL, SM>(a, r, A, Ws, W, stk, cs, P, B, C, wat, pool, nodes, don);
+      have = false;
+      if (lane == 0) {
+        if (pool_lock(pool, a.err, a.spin)) {
+          pool->idle++;
+          pool_unlock(pool);
+        }
+      }
+      __syncwarp();
+    }
+    int got = 0;
+    if (lane == 0) {
+      if (pool_lock(pool, a.err, a.spin)) {
+        if (pool->count > 0) {
+          got = pool->count--;
+          pool->idle--;
+        } else if (pool->idle == kBW) {
+          got = -1;
+        }
+        if (got <= 0) pool_unlock(pool);
+      } else {
+        got = -1;
+      }
+    }
+    got = __shfl_sync(FULL, got, 0);
+    if (got < 0) break;
+    if (got == 0) {
+      int beat = *(volatile int *)&pool->beat;
+      if (beat != lastbeat) {
+        lastbeat = beat;
+        waited = 0;
+      }
+      if (++waited > a.spin || *(volatile int32_t *)a.err) {
+        if (lane == 0) atomicExch(a.err, kDevTimeout);
+        break;
+      }
+      __nanosleep(128);
+      continue;
+    }
+    // copy the task while still holding the lock (lane 0 holds it)
+    const int slot = got - 1;
+#pragma unroll
+    for (int k = 0; k < WPL; k++) {
+      C.w[k] = pool->C[slot][k * 32 + lane];
+      P.w[k] = pool->P[slot][k * 32 + lane];
+    }
+    cs = pool->csize[slot];
+    __syncwarp();
+    if (lane == 0) pool_unlock(pool);
+    __syncwarp();
+    int om2 = read_best(a.best, g);
+    color_ise<WPL, SM>(A, Ws, W, P, om2 - cs, B);
+    wat = om2;
+    have = bany(B);
+    if (!have && lane == 0) {
+      if (pool_lock(pool, a.err, a.spin)) {
+        pool->idle++;
+        pool_unlock(pool);
+      }
+    }
+    __syncwarp();
+  }
+}
 
 template <int WPL, bool SM>
 __global__ void __launch_bounds__(kBT) search_block_kernel(SA a) {
@@ -697,7 +967,7 @@ __global__ void __launch_bounds__(kBT) search_block_kernel(SA a) {
       }
     }
     // colouring test and the search, started by warp 0
-    Root r{u, g, Pidx};
+    Root r{u, g, Pidx, p};
     Bits<WPL> P, B, C;
     bzero(C);
     int cs = 1, wat = om;
@@ -723,72 +993,20 @@ __global__ void __launch_bounds__(kBT) search_block_kernel(SA a) {
     }
     __syncthreads();
     if (!ctl[4]) continue;
-    long long waited = 0;
-    int lastbeat = -1;
-    for (;;) {
-      if (have) {
-        dfs<WPL, SM>(a, r, A, Ws, W, stk, cs, P, B, C, wat, pool, nodes, don);
-        have = false;
-        if (lane == 0) {
-          if (pool_lock(pool, a.err, a.spin)) {
-            pool->idle++;
-            pool_unlock(pool);
-          }
+    if constexpr (SM && WPL == 1) {
+      if (a.tasks) {
+        // Publish the root: its matrix and P list go to the arena and its
+        // first-level branches become tasks that any block may take.
+        // Without room the block searches the root itself.
+        if (wid == 0) {
+          const bool done = spill_frontier<WPL, SM>(a, r, A, Ws, W, stk, 0, 1, P, B, C);
+          if (lane == 0) ctl[4] = done ? 0 : 1;
         }
-        __syncwarp();
+        __syncthreads();
+        if (!ctl[4]) continue;
       }
-      int got = 0;
-      if (lane == 0) {
-        if (pool_lock(pool, a.err, a.spin)) {
-          if (pool->count > 0) {
-            got = pool->count--;
-            pool->idle--;
-          } else if (pool->idle == kBW) {
-            got = -1;
-          }
-          if (got <= 0) pool_unlock(pool);
-        } else {
-          got = -1;
-        }
-      }
-      got = __shfl_sync(FULL, got, 0);
-      if (got < 0) break;
-      if (got == 0) {
-        int beat = *(volatile int *)&pool->beat;
-        if (beat != lastbeat) {
-          lastbeat = beat;
-          waited = 0;
-        }
-        if (++waited > a.spin || *(volatile int32_t *)a.err) {
-          if (lane == 0) atomicExch(a.err, kDevTimeout);
-          break;
-        }
-        __nanosleep(128);
-        continue;
-      }
-      // copy the task while still holding the lock (lane 0 holds it)
-      const int slot = got - 1;
-#pragma unroll
-      for (int k = 0; k < WPL; k++) {
-        C.w[k] = pool->C[slot][k * 32 + lane];
-        P.w[k] = pool->P[slot][k * 32 + lane];
-      }
-      cs = pool->csize[slot];
-      __syncwarp();
-      if (lane == 0) pool_unlock(pool);
-      __syncwarp();
-      int om2 = read_best(a.best, g);
-      color_ise<WPL, SM>(A, Ws, W, P, om2 - cs, B);
-      wat = om2;
-      have = bany(B);
-      if (!have && lane == 0) {
-        if (pool_lock(pool, a.err, a.spin)) {
-          pool->idle++;
-          pool_unlock(pool);
-        }
-      }
-      __syncwarp();
     }
+    block_search<WPL, SM>(a, r, A, Ws, W, stk, pool, have, P, B, C, cs, wat, nodes, don);
     __syncthreads();
   }
   if (lane == 0) {
@@ -799,14 +1017,83 @@ __global__ void __launch_bounds__(kBT) search_block_kernel(SA a) {
   }
 }
 
+
+// Tasks of published roots: each block takes tasks in order, loads the
+// root's matrix and P list into shared memory when it changes, and searches
+// the task with its warps as in search_block_kernel.
+__global__ void __launch_bounds__(kBT) branch_task_kernel(SA a) {
+  using L = BlockLayout<1, true>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  int *Pidx = (int *)(smem + L::off_P);
+  Pool<1> *pool = (Pool<1> *)(smem + L::off_pool);
+  int *ctl = (int *)(smem + L::off_ctl);
+  uint32_t *A = (uint32_t *)(smem + L::off_A);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  uint32_t *stk = a.stack + ((int64_t)blockIdx.x * kBW + wid) * a.stack_stride;
+  unsigned long long nodes = 0, don = 0;
+  const int ntasks = min(*a.ntasks, a.task_cap);
+  int loaded = -1;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) ctl[0] = atomicAdd(a.task_next, 1);
+    __syncthreads();
+    const int t = ctl[0];
+    if (t >= ntasks || *(volatile int32_t *)a.err) break;
+    const uint32_t *tk = a.tasks + (int64_t)t * kTaskWords;
+    if (tk[1] == 0u) continue;  // decided when it was written
+    const int rec = (int)tk[0];
+    const RootRec rr = a.recs[rec];
+    if (rec != loaded) {
+      const uint32_t *sm = a.arena + rr.off;
+      for (int i = tid; i < rr.p * rr.Ws; i += kBT) A[i] = __ldcg(sm + i);
+      const int *sp = (const int *)(sm + (int64_t)rr.p * rr.Ws);
+      for (int i = tid; i < rr.p; i += kBT) Pidx[i] = __ldcg(sp + i);
+      loaded = rec;
+    }
+    __syncthreads();
+    Root r{rr.u, rr.g, Pidx, rr.p};
+    Bits<1> P, B, C;
+    int cs = (int)tk[1], wat = 0;
+    bool have = false;
+    if (wid == 0) {
+      C.w[0] = tk[2 + lane];
+      P.w[0] = tk[34 + lane];
+      wat = read_best(a.best, rr.g);
+      color_ise<1, true>(A, rr.Ws, rr.W, P, wat - cs, B);
+      have = bany(B);
+      if (lane == 0) {
+        ctl[4] = have ? 1 : 0;
+        pool->lock = 0;
+        pool->count = 0;
+        pool->idle = kBW - 1;
+        pool->beat = 0;
+      }
+    } else {
+      bzero(P);
+      bzero(B);
+      bzero(C);
+    }
+    __syncthreads();
+    if (!ctl[4]) continue;
+    block_search<1, true>(a, r, A, rr.Ws, rr.W, stk, pool, have, P, B, C, cs, wat, nodes, don);
+  }
+  if (lane == 0) {
+    atomicAdd(a.counters + 2, nodes);
+    atomicAdd(a.counters + 3, don);
+  }
+}
+
 }  // namespace
 
-int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, long long spin_limit, SearchCounters *cnt) {
+int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_split, long long spin_limit,
+                  SearchCounters *cnt) {
   // Persistent kernels with fixed grids; the root counts are read on the
   // device (pg.d_counts), and sizes are bounded by K(G) >= |N+(u)|, so the
   // launches need no host synchronisation.
   void *p;
   MC_TRY(ws_get(g, "se.ctr", 16 * sizeof(unsigned long long), &p));
+  // [0..4] colored, branched, nodes, donations, entries; [8..9] three root
+  // queue heads; [10] arena words used; [11..12] records, tasks, task head
   unsigned long long *ctr = (unsigned long long *)p;
   int32_t *next = (int32_t *)(ctr + 8);
   MC_CUDA_TRY(cudaMemsetAsync(ctr, 0, 16 * sizeof(unsigned long long), g->stream));
@@ -826,26 +1113,52 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, long long s
   a.counters = ctr;
   const int kbound = std::max(g->max_core, 1);  // |P| <= |N+(u)| <= K(u) <= K(G)
   const int wmax = g->warp_max_used;
+  if (!no_split) {
+    MC_TRY(ws_get(g, "se.arena", (size_t)kArenaWords * 4, &p));
+    a.arena = (uint32_t *)p;
+    a.arena_cap = kArenaWords;
+    a.arena_used = ctr + 10;
+    MC_TRY(ws_get(g, "se.recs", (size_t)kRecCap * sizeof(RootRec), &p));
+    a.recs = (RootRec *)p;
+    a.rec_cap = kRecCap;
+    a.nrec = (int32_t *)(ctr + 11);
+    MC_TRY(ws_get(g, "se.tasks", (size_t)kTaskCap * kTaskWords * 4, &p));
+    a.tasks = (uint32_t *)p;
+    a.task_cap = kTaskCap;
+    a.ntasks = a.nrec + 1;
+    a.task_next = a.nrec + 2;
+  }
+  // Block-worker launches (shared-memory matrices) and the task kernel share
+  // one shape and one stack buffer.
+  using LB = BlockLayout<1, true>;
+  const size_t smem_b = LB::bytes;
+  int per_sm_b = 0;
+  MC_CUDA_TRY(cudaFuncSetAttribute(search_block_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem_b));
+  MC_CUDA_TRY(cudaFuncSetAttribute(branch_task_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
+  MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, search_block_kernel<1, true>, kBT, smem_b));
+  int per_sm_t = 0;
+  MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_t, branch_task_kernel, kBT, smem_b));
+  per_sm_b = std::min(per_sm_b, per_sm_t);
+  if (per_sm_b < 1) return MC_ERR_CUDA;
+  const int blocks_b = g->sm_count * per_sm_b;
+  const int64_t stride_b = (int64_t)(std::min(kbound, 1024) + 2) * (64 + 2);
+  uint32_t *stk_b = nullptr;
+  if (kbound > wmax || !no_split) {
+    MC_TRY(ws_get(g, "se.stk_b", (size_t)blocks_b * kBW * stride_b * 4, &p));
+    stk_b = (uint32_t *)p;
+  }
 
-  // block class first (largest trees), then big, then warp class
+  // block class first (largest trees), then big, then warp class, then the
+  // tasks the first and last of these published
   if (kbound > wmax) {
-    using L = BlockLayout<1, true>;
-    const size_t smem = L::bytes;
-    MC_CUDA_TRY(cudaFuncSetAttribute(search_block_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-    int per_sm = 0;
-    MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_block_kernel<1, true>, kBT, smem));
-    if (per_sm < 1) return MC_ERR_CUDA;
-    const int blocks = g->sm_count * per_sm;
-    const int pmax = std::min(kbound, 1024);
-    a.stack_stride = (int64_t)(pmax + 2) * (64 + 2);
-    MC_TRY(ws_get(g, "se.stk_b", (size_t)blocks * kBW * a.stack_stride * 4, &p));
-    a.stack = (uint32_t *)p;
+    a.stack_stride = stride_b;
+    a.stack = stk_b;
     a.gmat = nullptr;
     a.roots = pg.roots_block;
     a.nroots = pg.d_counts + 4;
     a.next = next + 0;
-    search_block_kernel<1, true><<<blocks, kBT, smem, g->stream>>>(a);
+    search_block_kernel<1, true><<<blocks_b, kBT, smem_b, g->stream>>>(a);
     g_launches++;
     MC_CUDA_TRY(cudaGetLastError());
   }
@@ -887,18 +1200,27 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, long long s
     g_launches++;
     MC_CUDA_TRY(cudaGetLastError());
   }
+  if (!no_split) {
+    a.stack_stride = stride_b;
+    a.stack = stk_b;
+    branch_task_kernel<<<blocks_b, kBT, smem_b, g->stream>>>(a);
+    g_launches++;
+    MC_CUDA_TRY(cudaGetLastError());
+  }
   cnt->d_counters = ctr;
   return MC_OK;
 }
 
 int read_search_counters(mc_graph *g, SearchCounters *cnt) {
   unsigned long long *h = (unsigned long long *)g->h_small;
-  MC_CUDA_TRY(cudaMemcpyAsync(h, cnt->d_counters, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, g->stream));
+  MC_CUDA_TRY(cudaMemcpyAsync(h, cnt->d_counters, 13 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, g->stream));
   MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
   cnt->roots_colored = h[0];
   cnt->roots_branched = h[1];
   cnt->nodes = h[2];
   cnt->donations = h[3];
+  cnt->entries = h[4];
+  cnt->tasks = (unsigned long long)std::min(((const int32_t *)(h + 11))[1], kTaskCap);
   return MC_OK;
 }
 

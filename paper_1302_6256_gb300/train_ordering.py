@@ -66,7 +66,11 @@ def sample_rows(g, feat, core, witness, omega, rng, neg_ratio):
     return feat[idx], pos[idx].astype(np.float32)
 
 
-def build_dataset(graphs: int, seed: int, neg_ratio: int, workers: int, log=print):
+def _log(*a):
+    print(*a, flush=True)
+
+
+def build_dataset(graphs: int, seed: int, neg_ratio: int, workers: int, log=_log, budget_s: float = 0.0):
     rng = np.random.default_rng(seed)
     X, Y, info = [], [], []
     t0 = time.time()
@@ -88,12 +92,18 @@ def build_dataset(graphs: int, seed: int, neg_ratio: int, workers: int, log=prin
             Y.append(y)
             info.append((g.n, g.m, om, st["heuristic_size"]))
             futs[i] = None
-            if (i + 1) % max(1, graphs // 10) == 0:
+            if (i + 1) % max(1, graphs // 20) == 0:
                 log("  %d/%d graphs, %.0f s" % (i + 1, graphs, time.time() - t0))
+            if budget_s > 0 and time.time() - t0 > budget_s:
+                log("  time budget reached after %d graphs" % (i + 1))
+                break
+        for f in futs:
+            if f is not None:
+                f.cancel()
     return np.concatenate(X), np.concatenate(Y), info
 
 
-def train(X, Y, epochs: int, batch: int, lr: float, seed: int, log=print):
+def train(X, Y, epochs: int, batch: int, lr: float, seed: int, log=_log):
     m = mc.MLP(seed=seed)
     npos = float(Y.sum())
     pos_weight = (len(Y) - npos) / max(npos, 1.0)
@@ -126,14 +136,15 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--workers", type=int, default=max(1, (os.cpu_count() or 2) - 2))
     ap.add_argument("--out", default=DEFAULT_OUT)
+    ap.add_argument("--budget-s", type=float, default=0.0, help="stop adding graphs after this many seconds")
     a = ap.parse_args(argv)
     t = time.time()
-    X, Y, info = build_dataset(a.graphs, a.seed, a.neg_ratio, a.workers)
+    X, Y, info = build_dataset(a.graphs, a.seed, a.neg_ratio, a.workers, budget_s=a.budget_s)
     print("dataset: %d rows, %d positive, %.0f s" % (len(Y), int(Y.sum()), time.time() - t), flush=True)
     m, pw, losses = train(X, Y, a.epochs, a.batch, a.lr, a.seed)
     p = m.get_params()
     np.save(a.out, p)
-    meta = {"graphs": a.graphs, "seed": a.seed, "rows": int(len(Y)), "positives": int(Y.sum()), "pos_weight": pw,
+    meta = {"graphs": len(info), "graphs_requested": a.graphs, "seed": a.seed, "rows": int(len(Y)), "positives": int(Y.sum()), "pos_weight": pw,
             "epochs": a.epochs, "lr": a.lr, "batch": a.batch, "losses": losses,
             "omega_gap_mean": float(np.mean([o - hs for (_, _, o, hs) in info])), "seconds": time.time() - t}
     with open(os.path.splitext(a.out)[0] + ".json", "w") as f:

@@ -108,7 +108,8 @@ def test_heuristic_racy_is_valid(mc, g):
 
 
 @pytest.mark.parametrize("opts", [dict(ordering=2), dict(no_neigh_cores=True), dict(heuristic=1),
-                                  dict(heuristic=2), dict(warp_max=16), dict(warp_max=1)],
+                                  dict(heuristic=2), dict(warp_max=16), dict(warp_max=1), dict(no_split=True),
+                                  dict(heuristic=2, warp_max=16)],
                          ids=lambda o: ",".join("%s=%s" % kv for kv in o.items()))
 def test_options_keep_omega(mc, opts):
     for g in medium_graphs()[:6]:
@@ -116,6 +117,22 @@ def test_options_keep_omega(mc, opts):
         om, wit, _ = mc.mc_max_clique(h, **opts)
         assert om == ref_omega(g), g.name
         assert oracle.is_clique(g, wit)
+
+
+def test_split_tasks_keep_omega(mc):
+    """Block-worker neighbourhoods that reach Branch are split into
+    first-level tasks; with the heuristic off (omega starts at 0) many roots
+    branch, and the result must equal the unsplit search and the oracle."""
+    seen = 0
+    for g in medium_graphs()[:4] + [gg.relabel(gg.turan(300, 33), 3)]:
+        h = load(mc, g)
+        om, wit, st = mc.mc_max_clique(h, heuristic=2, warp_max=16)
+        om2, wit2, st2 = mc.mc_max_clique(h, heuristic=2, warp_max=16, no_split=True)
+        assert om == om2 == ref_omega(g), g.name
+        assert oracle.is_clique(g, wit) and oracle.is_clique(g, wit2)
+        assert st2["tasks"] == 0
+        seen += st["tasks"]
+    assert seen > 0
 
 
 def test_host_pointers_and_repeat_calls(mc):
@@ -259,3 +276,12 @@ def test_big_neighbourhoods_turan(mc):
     assert oracle.is_clique(g, wit)
     om2, wit2, _ = mc.mc_max_clique(h, heuristic=2)  # no heuristic: the search finds it alone
     assert om2 == 300 and oracle.is_clique(g, wit2)
+
+
+def test_autotune_returns_a_working_setting(mc):
+    g = gg.rmat(14, 16, planted=30, seed=16)
+    h = load(mc, g)
+    opts, ms = mc.mc_autotune(h, repeats=1)
+    assert opts["warp_max"] in (32, 64, 128) and ms > 0
+    om, wit, _ = mc.mc_max_clique(h, **opts)
+    assert om == ref_omega(g) and oracle.is_clique(g, wit)
