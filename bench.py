@@ -37,6 +37,64 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
 
 
+# Per-launch DRAM traffic of search_block_kernel on the R-MAT scale-22 solve,
+# from the ncu capture summarised in profiles/search_block_kernel_rmat_s22.md
+# (dram__bytes_read.sum + dram__bytes_write.sum); None until a capture of the
+# current kernel exists.
+SEARCH_BLOCK_TRAFFIC_S22 = None
+
+
+def roofline(stats, n, nnz, clk, dev):
+    """Roofline of the kernel that takes the most time in a solve, timed by the
+    library's CUDA events on its own stream over the timed steps.
+
+    - kcore_peel_kernel: HBM-bound; algorithmic bytes = the CSR read once plus
+      the core numbers written, 8(n+1) + 4 nnz + 4n.
+    - search_block_kernel / search_warp_kernel (InitialBranch + Branch):
+      bound by shared-memory probes, one per later-neighbour row entry read
+      while building the neighbourhood matrices (Fact 3's work); peak = SMs x
+      32 lanes x SM clock, one 4-byte shared-memory access per lane per clock.
+    - anything else: HBM-bound against the CSR read once.
+    """
+    import torch
+    peaks = load_peaks()
+    mean = lambda k: sum(s[k] for s in stats) / len(stats)
+    kern = {
+        "kcore_peel_kernel": mean("ms_cores"),
+        "heuristic_kernel": mean("ms_heuristic"),
+        "prune (outdeg, fill, scans)": mean("ms_prune"),
+        "search_block_kernel": mean("ms_search_block"),
+        "search_block_kernel (big neighbourhoods)": mean("ms_search_big"),
+        "search_warp_kernel": mean("ms_search_warp"),
+        "branch_task_kernel": mean("ms_search_tasks"),
+        "verify": mean("ms_verify"),
+    }
+    dom = max(kern, key=kern.get)
+    ms = kern[dom]
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if not peaks.get("fallback") else "fallback 6.8 TB/s"
+    if dom in ("search_block_kernel", "search_warp_kernel"):
+        ent = mean("neighbourhood_entries_block") if dom == "search_block_kernel" else \
+            mean("neighbourhood_entries") - mean("neighbourhood_entries_block")
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = clk.get("sm_max_mhz") or 2070.0
+        peak = sms * 32 * mhz * 1e6 / 1e9
+        achieved = ent / (ms / 1e3) / 1e9
+        return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "G entries/s",
+                "frac": achieved / peak,
+                "traffic": SEARCH_BLOCK_TRAFFIC_S22 if dom == "search_block_kernel" else None,
+                "peak_source": "derived: %d SMs x 32 lanes x %.0f MHz, one shared-memory probe per lane per clock"
+                               % (sms, mhz),
+                "algorithmic_units": ent, "unit_note": "neighbour-list entries read in InitialBranch (Fact 3)",
+                "kernel_ms": ms, "_stages": kern}
+    alg = 8 * (n + 1) + 4 * nnz + (4 * n if dom == "kcore_peel_kernel" else 0)
+    achieved = alg / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "traffic": None, "peak_source": hbm_src, "algorithmic_bytes": alg,
+            "kernel_ms": ms, "_stages": kern}
+
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -339,31 +397,9 @@ def main():
         e2e_ms = float(tt.item())
     assert om_e == om
 
-    # roofline of the dominant stage
-    peaks = load_peaks()
-    mean = lambda k: sum(s[k] for s in stats) / len(stats)
-    stages = {k: mean(k) for k in ("ms_cores", "ms_heuristic", "ms_prune", "ms_search", "ms_verify")}
-    dom = max(stages, key=stages.get)
-    n, nnz = g.n, int(g.row_ptr[-1])
-    core_bytes = 8 * (n + 1) + 4 * nnz + 4 * n  # read the CSR once, write K
-    if dom == "ms_cores":
-        alg = core_bytes
-        kernel = "kcore_peel_kernel (+degree_init, peel_pos)"
-    elif dom == "ms_search":
-        # oriented rows of every P member read once per root (Fact 3 work)
-        alg = 4 * mean("pruned_arcs")
-        kernel = "search_block_kernel (InitialBranch + Branch)"
-    elif dom == "ms_heuristic":
-        alg = 8 * (n + 1) + 4 * nnz
-        kernel = "heuristic_kernel"
-    else:
-        alg = 8 * (n + 1) + 4 * nnz
-        kernel = dom
-    achieved = alg / (stages[dom] / 1e3) / 1e9
-    roof = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-            "frac": achieved / peaks.get("hbm_gbs", 6800.0), "traffic": None,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if not peaks.get("fallback") else "fallback",
-            "algorithmic_bytes": alg, "stage_ms": stages}
+    n = g.n
+    roof = roofline(stats, n, int(g.row_ptr[-1]), clk, dev)
+    stages = roof.pop("_stages")
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -378,6 +414,7 @@ def main():
         "roofline": roof,
         "gpu_launches": int(launches),
         "clocks": clk,
+        "kernel_ms": stages,
         "stats_last": stats[-1],
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

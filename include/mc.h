@@ -91,11 +91,18 @@ typedef struct {
    * adjacency matrix and its first-level branches as tasks that every block
    * takes from one queue, so one hard neighbourhood spreads over the GPU */
   int32_t no_split;
+  /* Branch nodes a warp worker expands on one root before it spills the
+   * rest of its tree to the task queue (a block worker: four times as
+   * many); 0 = default (4096) */
+  int32_t split_nodes;
 } mc_options;
 
 /* Per-call statistics (all times in milliseconds, CUDA events). */
 typedef struct {
   double ms_total, ms_cores, ms_heuristic, ms_prune, ms_search, ms_verify;
+  /* the search stage by kernel: block workers, big-neighbourhood workers,
+   * warp workers, the task queue (0 where a kernel did not run) */
+  double ms_search_block, ms_search_big, ms_search_warp, ms_search_tasks;
   int64_t n, edges;            /* vertices and undirected edges */
   int64_t pruned_n;            /* vertices left after the core pruning (Section 4.2) */
   int64_t pruned_arcs;         /* arcs of the oriented pruned graph */
@@ -106,7 +113,8 @@ typedef struct {
   int64_t donations;           /* subproblems handed to other warps */
   int64_t neighbourhood_entries; /* later-neighbour row entries read to build the
                                     roots' adjacency matrices (Fact 3's work) */
-  int64_t tasks;               /* first-level branches published as tasks */
+  int64_t neighbourhood_entries_block; /* ... of which read by block workers */
+  int64_t tasks;               /* subproblems spilled to the task queue */
   int32_t max_core, heuristic_size, omega, verified;
 } mc_stats;
 
@@ -166,11 +174,12 @@ int mc_max_clique_batch(mc_graph *g, const mc_options *opt, int32_t *omegas_out,
                         int64_t capacity, int64_t *witness_offsets, mc_stats *stats);
 
 /* Autotuner (an extension; the paper tunes nothing on a GPU): solves the
- * graph `repeats` times under each candidate setting of the work split
- * between warp and block workers (warp_max 32, 64, 128) and of CUDA-graph
- * replay (graph 0, 1), starting from `base` (NULL = defaults), and writes the
- * fastest setting to *best_out and its mean time (ms) to *best_ms_out
- * (nullable).  Every trial is a full exact solve. */
+ * graph `repeats` times per candidate setting, one coordinate at a time,
+ * starting from `base` (NULL = defaults): the work split between warp and
+ * block workers (warp_max 32, 64, 128), then the task queue (no_split, or
+ * split_nodes 1024, 4096, 16384), then CUDA-graph replay (graph 0, 1).  It
+ * writes the fastest setting to *best_out and its mean time (ms) to
+ * *best_ms_out (nullable).  Every trial is a full exact solve. */
 int mc_autotune(mc_graph *g, const mc_options *base, int32_t repeats, mc_options *best_out, double *best_ms_out);
 
 /* Check a vertex set on the device: *is_clique_out = 1 iff the k vertices are

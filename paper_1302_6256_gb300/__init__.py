@@ -47,18 +47,21 @@ class Options(ctypes.Structure):
                 ("heuristic", ctypes.c_int32), ("warp_max", ctypes.c_int32),
                 ("spin_limit", ctypes.c_int64), ("scores", ctypes.c_void_p),
                 ("seeds", ctypes.c_int32), ("graph", ctypes.c_int32),
-                ("no_split", ctypes.c_int32)]
+                ("no_split", ctypes.c_int32), ("split_nodes", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("ms_total", ctypes.c_double), ("ms_cores", ctypes.c_double),
                 ("ms_heuristic", ctypes.c_double), ("ms_prune", ctypes.c_double),
                 ("ms_search", ctypes.c_double), ("ms_verify", ctypes.c_double),
+                ("ms_search_block", ctypes.c_double), ("ms_search_big", ctypes.c_double),
+                ("ms_search_warp", ctypes.c_double), ("ms_search_tasks", ctypes.c_double),
                 ("n", ctypes.c_int64), ("edges", ctypes.c_int64), ("pruned_n", ctypes.c_int64),
                 ("pruned_arcs", ctypes.c_int64), ("roots", ctypes.c_int64),
                 ("roots_colored", ctypes.c_int64), ("roots_branched", ctypes.c_int64),
                 ("nodes", ctypes.c_int64), ("donations", ctypes.c_int64),
-                ("neighbourhood_entries", ctypes.c_int64), ("tasks", ctypes.c_int64),
+                ("neighbourhood_entries", ctypes.c_int64), ("neighbourhood_entries_block", ctypes.c_int64),
+                ("tasks", ctypes.c_int64),
                 ("max_core", ctypes.c_int32), ("heuristic_size", ctypes.c_int32),
                 ("omega", ctypes.c_int32), ("verified", ctypes.c_int32)]
 
@@ -230,8 +233,9 @@ def mc_heuristic_clique(g: Graph, mode: int = 0, core=None):
 
 
 def _options(ordering=0, no_neigh_cores=False, heuristic=0, warp_max=0, spin_limit=0, scores=None, seeds=0,
-             graph=False, no_split=False):
+             graph=False, no_split=False, split_nodes=0):
     o = Options()
+    o.split_nodes = split_nodes
     o.graph = 1 if graph else 0
     o.no_split = 1 if no_split else 0
     o.ordering = ordering
@@ -363,10 +367,12 @@ class MLP:
 
 
 def mc_autotune(g: Graph, repeats: int = 2, **opts):
-    """Fastest (warp_max, graph) setting for this graph; returns (options dict, ms)."""
+    """Fastest (warp_max, no_split, split_nodes, graph) setting for this
+    graph; returns (options dict, ms)."""
     L = load_library()
     base, keep = _options(**opts)
     best = Options()
     ms = ctypes.c_double(0)
     _check(L.mc_autotune(g.handle, ctypes.byref(base), repeats, ctypes.byref(best), ctypes.byref(ms)), "mc_autotune")
-    return {"warp_max": best.warp_max, "graph": bool(best.graph)}, ms.value
+    return {"warp_max": best.warp_max, "no_split": bool(best.no_split), "split_nodes": best.split_nodes,
+            "graph": bool(best.graph)}, ms.value

@@ -273,7 +273,7 @@ static float elapsed(cudaEvent_t a, cudaEvent_t b) {
 
 // Record a stage event; inside capture it becomes an external event-record
 // node, so the replayed graph records it and the host can wait on it.
-static int record(mc_graph *g, int i) {
+int record_event(mc_graph *g, int i) {
   if (g->capturing) {
     MC_CUDA_TRY(cudaEventRecordWithFlags(g->ev[i], g->stream, cudaEventRecordExternal));
   } else {
@@ -287,7 +287,8 @@ static int check_options(const mc_options *opt, mc_options *o) {
   *o = mc_options{};
   if (opt) *o = *opt;
   if (o->ordering < 0 || o->ordering > 2 || o->heuristic < 0 || o->heuristic > 2 || o->warp_max < 0 ||
-      o->seeds < 0 || o->graph < 0 || o->graph > 1 || o->no_split < 0 || o->no_split > 1)
+      o->seeds < 0 || o->graph < 0 || o->graph > 1 || o->no_split < 0 || o->no_split > 1 ||
+      o->split_nodes < 0)
     return MC_ERR_ARG;
   if (o->ordering == 1 && !o->scores) return MC_ERR_ARG;
   return MC_OK;
@@ -300,11 +301,11 @@ static int check_options(const mc_options *opt, mc_options *o) {
 static int enqueue_solve(mc_graph *g, const mc_options &o, Pruned *pg, SearchCounters *sc, int32_t **d_ok_out) {
   const long long spin = spin_of(&o);
   g->warp_max_used = o.warp_max > 0 ? std::min(o.warp_max, 128) : 128;
-  MC_TRY(record(g, 0));
+  MC_TRY(record_event(g, 0));
   // every solve recomputes the core numbers (Algorithm 2, line 2)
   g->cores_valid = false;
   MC_TRY(ensure_cores(g, spin));
-  MC_TRY(record(g, 1));
+  MC_TRY(record_event(g, 1));
   MC_CUDA_TRY(cudaMemsetAsync(g->best, 0, g->count * 4, g->stream));
   MC_CUDA_TRY(cudaMemsetAsync(g->lock, 0, g->count * 4, g->stream));
   // learned scores (host or device) -> device copy
@@ -329,20 +330,20 @@ static int enqueue_solve(mc_graph *g, const mc_options &o, Pruned *pg, SearchCou
     }
   }
   if (o.heuristic != 2 && g->n > 0) MC_TRY(launch_heuristic(g, o.heuristic, spin, d_seeds, nseeds));
-  MC_TRY(record(g, 2));
+  MC_TRY(record_event(g, 2));
   int32_t *h_heur = (int32_t *)((char *)g->h_small + 1024);
   MC_CUDA_TRY(cudaMemcpyAsync(h_heur, g->best, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
   if (g->n > 0) MC_TRY(launch_prune(g, o.ordering, d_scores, g->warp_max_used, pg, spin));
-  MC_TRY(record(g, 3));
-  if (g->n > 0) MC_TRY(launch_search(g, *pg, o.no_neigh_cores, o.no_split, spin, sc));
+  MC_TRY(record_event(g, 3));
+  if (g->n > 0) MC_TRY(launch_search(g, *pg, o.no_neigh_cores, o.no_split, o.split_nodes, spin, sc));
   trivial_kernel<<<std::max(1, std::min(g->count / 256 + 1, 1024)), 256, 0, g->stream>>>(
       g->count, g->gid ? g->voff : nullptr, g->n, g->best, g->wit);
   g_launches++;
-  MC_TRY(record(g, 4));
+  MC_TRY(record_event(g, 4));
   MC_TRY(ws_get(g, "cp.ok", (size_t)g->count * 4, &p));
   *d_ok_out = (int32_t *)p;
   MC_TRY(launch_verify(g, *d_ok_out));
-  MC_TRY(record(g, 5));
+  MC_TRY(record_event(g, 5));
   return MC_OK;
 }
 
@@ -359,6 +360,12 @@ static int finish_solve(mc_graph *g, Pruned *pg, SearchCounters *sc, const int32
   st->ms_search = elapsed(g->ev[3], g->ev[4]);
   st->ms_verify = elapsed(g->ev[4], g->ev[5]);
   st->ms_total = elapsed(g->ev[0], g->ev[5]);
+  if (g->n > 0) {
+    st->ms_search_block = elapsed(g->ev[8], g->ev[9]);
+    st->ms_search_big = elapsed(g->ev[9], g->ev[10]);
+    st->ms_search_warp = elapsed(g->ev[10], g->ev[11]);
+    st->ms_search_tasks = elapsed(g->ev[11], g->ev[12]);
+  }
   if (g->n > 0 && pg->d_counts) {
     MC_TRY(read_pruned_counts(g, pg));
     st->pruned_n = pg->n;
@@ -372,6 +379,7 @@ static int finish_solve(mc_graph *g, Pruned *pg, SearchCounters *sc, const int32
     st->nodes = (int64_t)sc->nodes;
     st->donations = (int64_t)sc->donations;
     st->neighbourhood_entries = (int64_t)sc->entries;
+    st->neighbourhood_entries_block = (int64_t)sc->entries_block;
     st->tasks = (int64_t)sc->tasks;
   }
   st->max_core = g->max_core;
@@ -397,6 +405,7 @@ static uint64_t options_key(const mc_options &o) {
   mix((uint64_t)(uintptr_t)o.scores);
   mix((uint64_t)o.seeds);
   mix((uint64_t)o.no_split);
+  mix((uint64_t)o.split_nodes);
   return k;
 }
 
@@ -601,27 +610,61 @@ int mc_autotune(mc_graph *g, const mc_options *base, int32_t repeats, mc_options
   if (!g || !best_out || repeats < 1) return MC_ERR_ARG;
   mc_options b;
   MC_TRY(check_options(base, &b));
-  // candidate settings: warp/block split of the roots x direct or replayed graph
-  const int32_t splits[] = {32, 64, 128};
-  double best = 1e300;
-  mc_options bo = b;
   mc_stats st;
-  for (int gi = 0; gi < 2; gi++) {
-    for (int32_t wm : splits) {
-      mc_options o = b;
-      o.warp_max = wm;
-      o.graph = gi;
-      MC_TRY(run_max_clique(g, &o, &st));  // warm-up (and capture, for graph replay)
-      double tot = 0.0;
-      for (int r = 0; r < repeats; r++) {
-        MC_TRY(run_max_clique(g, &o, &st));
-        tot += st.ms_total;
-      }
-      const double ms = tot / repeats;
-      if (ms < best) {
-        best = ms;
-        bo = o;
-      }
+  // mean solve time of one setting (after one untimed solve, which also
+  // captures the CUDA graph when replay is on)
+  auto trial = [&](const mc_options &o, double *ms) -> int {
+    MC_TRY(run_max_clique(g, &o, &st));
+    double tot = 0.0;
+    for (int r = 0; r < repeats; r++) {
+      MC_TRY(run_max_clique(g, &o, &st));
+      tot += st.ms_total;
+    }
+    *ms = tot / repeats;
+    return MC_OK;
+  };
+  // one coordinate at a time: the warp/block split of the roots, the spill
+  // budget of the task queue, then direct launches vs graph replay
+  mc_options bo = b;
+  bo.graph = 0;
+  double best = 1e300;
+  for (int32_t wm : {32, 64, 128}) {
+    mc_options o = bo;
+    o.warp_max = wm;
+    double ms;
+    MC_TRY(trial(o, &ms));
+    if (ms < best) {
+      best = ms;
+      b.warp_max = wm;
+    }
+  }
+  bo.warp_max = b.warp_max;
+  struct Split {
+    int32_t no_split, nodes;
+  };
+  const Split splits[] = {{1, 0}, {0, 1024}, {0, 4096}, {0, 16384}};
+  Split bs = {bo.no_split, bo.split_nodes};
+  for (const Split &sp : splits) {
+    mc_options o = bo;
+    o.no_split = sp.no_split;
+    o.split_nodes = sp.nodes;
+    double ms;
+    MC_TRY(trial(o, &ms));
+    if (ms < best) {
+      best = ms;
+      bs = sp;
+    }
+  }
+  bo.no_split = bs.no_split;
+  bo.split_nodes = bs.nodes;
+  {
+    mc_options o = bo;
+    o.graph = 1;
+    double ms;
+    MC_TRY(trial(o, &ms));
+    if (ms < best) {
+      best = ms;
+      bo.graph = 1;
     }
   }
   *best_out = bo;

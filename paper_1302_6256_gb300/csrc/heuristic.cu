@@ -187,9 +187,9 @@ __global__ void __launch_bounds__(kHT) heuristic_kernel(HA a) {
   const int64_t total = a.limit;
   for (;;) {
     int64_t i = 0;
-    if (lane == 0) i = a.begin + atomicAdd(a.next, 1);
+    if (lane == 0) i = *(volatile int32_t *)a.err ? total : a.begin + atomicAdd(a.next, 1);
     i = __shfl_sync(FULL, (long long)i, 0);
-    if (i >= total || *(volatile int32_t *)a.err) break;
+    if (i >= total) break;
     int v;
     if (i < a.nseeds) {
       v = a.seeds[i];

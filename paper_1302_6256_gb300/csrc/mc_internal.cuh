@@ -98,12 +98,14 @@ int read_pruned_counts(mc_graph *g, Pruned *out);
 
 // Search (InitialBranch + Branch) over all roots.
 struct SearchCounters {
-  unsigned long long roots_colored, roots_branched, nodes, donations, entries, tasks;
+  unsigned long long roots_colored, roots_branched, nodes, donations, entries, entries_block, tasks;
   unsigned long long *d_counters;  // device copy, read by read_search_counters
 };
 int read_search_counters(mc_graph *g, SearchCounters *cnt);
-int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_split, long long spin_limit,
-                  SearchCounters *counters);
+// Record event i of the graph on its stream (external when capturing).
+int record_event(mc_graph *g, int i);
+int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_split, int split_nodes,
+                  long long spin_limit, SearchCounters *counters);
 
 }  // namespace mc
 
@@ -136,7 +138,7 @@ struct mc_graph {
   std::map<std::string, mc::DevBuf> ws;
   // pinned host staging for small results
   void *h_small = nullptr;
-  cudaEvent_t ev[8] = {};
+  cudaEvent_t ev[13] = {};  // 0-5 stages, 6-7 graph replay order, 8-12 search kernels
   // captured solve (CUDA graph replay) and what it was captured with
   cudaGraphExec_t graph_exec = nullptr;
   cudaStream_t cap_stream = nullptr;

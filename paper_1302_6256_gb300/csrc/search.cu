@@ -68,9 +68,15 @@ struct SA {
   int32_t rec_cap;
   int32_t *nrec;
   uint32_t *tasks;               // kTaskWords words per task
-  int32_t task_cap;
-  int32_t *ntasks;
-  int32_t *task_next;
+  int32_t *ready;                // per ring slot: 2*lap free for lap's writer, 2*lap+1 written
+  int32_t task_cap;              // ring slots (a power of two)
+  int32_t *ntasks;               // positions taken (the queue's tail, monotonic)
+  int32_t *task_next;            // positions handed out (the queue's head)
+  int32_t *active;               // blocks of the task kernel holding a task
+  int32_t *progress;             // heartbeat: bumped every 256 Branch nodes
+  int32_t queue_gate;            // spill only while fewer tasks wait (0 = always)
+  long long budget_warp;         // Branch nodes before a warp worker spills
+  long long budget_block;        // ... and a block, on one root or task
 };
 
 struct RootRec {
@@ -80,8 +86,8 @@ struct RootRec {
 constexpr int kTaskWords = 2 + 64;  // root record, clique size, C bits, P bits (32 words each)
 constexpr long long kArenaWords = 64ll << 20;  // 256 MB of published matrices
 constexpr int kRecCap = 1 << 16;
-constexpr int kTaskCap = 1 << 17;          // 34.6 MB of tasks
-constexpr long long kSpillNodes = 4096;    // Branch nodes a lone warp expands before it spills
+constexpr int kTaskCap = 1 << 20;          // ring slots, 277 MB
+constexpr long long kSpillNodes = 4096;    // default Branch-node budget of a warp worker
 
 template <int WPL>
 struct Bits {
@@ -280,10 +286,22 @@ __device__ void write_clique(int32_t *base, const Bits<WPL> &C, int v, const int
   if (lane == 0) base[0] = oold[u];
 }
 
+// A word of a stack level that lane 0 wrote (omega at colouring, the chosen
+// vertex), read back by lane 0 and broadcast: the other lanes did not write
+// it and must not act on a copy of their own.
+__device__ __forceinline__ int level_word(const uint32_t *p) {
+  int x = 0;
+  if ((threadIdx.x & 31) == 0) x = (int)*p;
+  return __shfl_sync(FULL, x, 0);
+}
+
 // Shared-memory task pool of a block worker.
 template <int WPL>
 struct Pool {
   int lock, count, idle, beat;
+  int spent;  // Branch nodes the block has expanded on this root or task
+  int spill;  // 0 searching here, 2 record being written, 1 spilling, 3 no room
+  int rec;    // record of the root's matrix in the arena, -1 none yet
   int csize[kPoolCap];
   uint32_t C[kPoolCap][32 * WPL];
   uint32_t P[kPoolCap][32 * WPL];
@@ -314,16 +332,26 @@ struct Root {
   int p;  // |P|: rows of the root's matrix
 };
 
-// Take k consecutive task slots, all or none; returns the first or -1.
+// Take k consecutive queue positions, all or none; returns the first or -1.
+// The queue is a ring of task_cap slots: positions are taken only while
+// fewer than task_cap are taken and not yet handed out.
 __device__ int reserve_tasks(const SA &a, int k) {
   int cur = *(volatile int32_t *)a.ntasks;
   for (long long it = 0; it < a.spin; it++) {
-    if (cur + k > a.task_cap) return -1;
+    const int head = *(volatile int32_t *)a.task_next;
+    if (cur - head + k > a.task_cap || cur > INT_MAX - k) return -1;
     const int prev = atomicCAS(a.ntasks, cur, cur + k);
     if (prev == cur) return cur;
     cur = prev;
   }
   return -1;
+}
+
+// True while the queue is short enough that splitting work pays.
+__device__ __forceinline__ bool queue_short(const SA &a) {
+  if (a.queue_gate <= 0) return true;
+  const int tail = *(volatile int32_t *)a.ntasks, head = *(volatile int32_t *)a.task_next;
+  return tail - head < a.queue_gate;
 }
 
 // Reserve arena room and a record for a root's matrix and P list.  Returns
@@ -339,14 +367,14 @@ __device__ int reserve_record(const SA &a, const Root &r, int Ws, long long *off
 }
 
 // Copy a root's matrix and P list to its arena room and write its record,
-// over nthr threads starting at thread t.
-__device__ void write_record(const SA &a, const Root &r, const uint32_t *A, int Ws, int W, int rec, long long off,
-                             int t, int nthr) {
+// over the 32 lanes of a warp.
+__device__ void write_record(const SA &a, const Root &r, const uint32_t *A, int Ws, int W, int rec, long long off) {
+  const int lane = threadIdx.x & 31;
   uint32_t *dm = a.arena + off;
-  for (int i = t; i < r.p * Ws; i += nthr) dm[i] = A[i];
+  for (int i = lane; i < r.p * Ws; i += 32) dm[i] = A[i];
   int *dp = (int *)(dm + (int64_t)r.p * Ws);
-  for (int i = t; i < r.p; i += nthr) dp[i] = r.Pidx[i];
-  if (t == 0) {
+  for (int i = lane; i < r.p; i += 32) dp[i] = r.Pidx[i];
+  if (lane == 0) {
     RootRec rr;
     rr.u = r.u;
     rr.g = r.g;
@@ -357,81 +385,95 @@ __device__ void write_record(const SA &a, const Root &r, const uint32_t *A, int 
     rr.off = off;
     a.recs[rec] = rr;
   }
+  __syncwarp();
+  __threadfence();
 }
 
-// One task: the branch x of a node with clique Cl (csl vertices with u) and
-// candidates Pl (x and its earlier siblings already removed).  Writes the
-// task to slot t, or an empty task when x's subproblem is decided at once
-// (raising the incumbent if {u} + Cl + x is a larger maximal clique).
-template <int WPL, bool SM>
-__device__ void emit_task(const SA &a, const Root &r, const uint32_t *A, int Ws, int W, int rec, int t,
-                          const Bits<WPL> &Cl, int csl, const Bits<WPL> &Pl, int x) {
+// Write the task at queue position t (clique size cs counting u, 0 =
+// empty; clique bits C; candidates P) and mark its slot written.  Position
+// t uses slot t mod task_cap in lap t / task_cap: the slot's word counts
+// 2*lap when the previous lap's task has been read (its reader already
+// holds it, since t was reserved after that position was handed out) and
+// 2*lap+1 once this task is written.  Warp-collective.
+__device__ void write_task(const SA &a, int t, int rec, int cs, const Bits<1> &C, const Bits<1> &P) {
   const int lane = threadIdx.x & 31;
-  Bits<WPL> TP = Pl;
-  band_row<WPL, SM>(TP, A, Ws, W, x);
-  const int om = read_best(a.best, r.g);
-  int live = 1;
-  if (!bany(TP)) {
-    live = 0;
-    if (csl + 1 > om) {
-      const Bits<WPL> Cc = Cl;
-      dev::raise_incumbent(a.best, a.lock, a.wit, a.voff, r.g, csl + 1, a.err, a.spin,
-                           [&](int, int32_t *base) { write_clique<WPL>(base, Cc, x, r.Pidx, a.oold, r.u); });
+  const int slot = t & (a.task_cap - 1);
+  const int lap2 = 2 * (t / a.task_cap);
+  if (lane == 0) {
+    long long w = 0;
+    while (*(volatile int32_t *)(a.ready + slot) != lap2) {
+      if (++w > a.spin) {
+        atomicExch(a.err, kDevTimeout);
+        break;
+      }
+      __nanosleep(32);
     }
-  } else if (csl + 1 + bcount(TP) <= om) {
-    live = 0;
   }
-  uint32_t *tk = a.tasks + (int64_t)t * kTaskWords;
+  __syncwarp();
+  __threadfence();
+  uint32_t *tk = a.tasks + (int64_t)slot * kTaskWords;
   if (lane == 0) {
     tk[0] = (uint32_t)rec;
-    tk[1] = live ? (uint32_t)(csl + 1) : 0u;  // 0 = empty task
+    tk[1] = (uint32_t)cs;
   }
-  Bits<WPL> Cx = Cl;
+  tk[2 + lane] = C.w[0];
+  tk[34 + lane] = P.w[0];
+  __syncwarp();
+  __threadfence();
+  if (lane == 0) atomicExch(a.ready + slot, lap2 + 1);
+}
+
+// The branch x of a node with clique Cl (csl vertices with u) and candidates
+// Pl (x and its earlier siblings already removed) as task slot t; the task
+// is empty when x's subproblem is decided at once (raising the incumbent if
+// {u} + Cl + x is a larger maximal clique).
+__device__ void emit_task(const SA &a, const Root &r, const uint32_t *A, int Ws, int W, int rec, int t,
+                          const Bits<1> &Cl, int csl, const Bits<1> &Pl, int x) {
+  Bits<1> TP = Pl;
+  band_row<1, true>(TP, A, Ws, W, x);
+  const int om = read_best(a.best, r.g);
+  int cs = csl + 1;
+  if (!bany(TP)) {
+    if (csl + 1 > om) {
+      const Bits<1> Cc = Cl;
+      dev::raise_incumbent(a.best, a.lock, a.wit, a.voff, r.g, csl + 1, a.err, a.spin,
+                           [&](int, int32_t *base) { write_clique<1>(base, Cc, x, r.Pidx, a.oold, r.u); });
+    }
+    cs = 0;
+  } else if (csl + 1 + bcount(TP) <= om) {
+    cs = 0;
+  }
+  Bits<1> Cx = Cl;
   bset(Cx, x);
-#pragma unroll
-  for (int k = 0; k < WPL; k++) {
-    tk[2 + k * 32 + lane] = Cx.w[k];
-    tk[34 + k * 32 + lane] = TP.w[k];
-  }
+  write_task(a, t, rec, cs, Cx, TP);
 }
 
 // Hand the untried rest of one warp's depth-first search to the task queue:
 // every untried branch at each stored level and at the current level becomes
-// a task.  All or nothing: returns false, publishing nothing, without room.
-template <int WPL, bool SM>
-__device__ bool spill_frontier(const SA &a, const Root &r, const uint32_t *A, int Ws, int W, const uint32_t *stk,
-                               int d, int csize0, Bits<WPL> P, Bits<WPL> B, Bits<WPL> C) {
+// a task of record rec.  All or nothing: returns false, publishing nothing,
+// without room in the queue.
+__device__ bool spill_levels(const SA &a, const Root &r, const uint32_t *A, int Ws, int W, const uint32_t *stk, int d,
+                             int csize0, const Bits<1> &P, const Bits<1> &B, const Bits<1> &C, int rec) {
   const int lane = threadIdx.x & 31;
-  const int stride = 64 * WPL + 2;
+  const int stride = 64 + 2;
   int ntask = bcount(B);
   for (int l = 0; l < d; l++) {
-    Bits<WPL> Bl;
-#pragma unroll
-    for (int k = 0; k < WPL; k++) Bl.w[k] = stk[(int64_t)l * stride + 32 * WPL + k * 32 + lane];
+    Bits<1> Bl;
+    Bl.w[0] = stk[(int64_t)l * stride + 32 + lane];
     ntask += bcount(Bl);
   }
-  int rec = -1, t0 = -1;
-  long long off = 0;
-  if (lane == 0 && ntask > 0) {
-    rec = reserve_record(a, r, Ws, &off);
-    if (rec >= 0) t0 = reserve_tasks(a, ntask);
-  }
-  t0 = __shfl_sync(FULL, t0, 0);
-  if (t0 < 0) return false;
-  rec = __shfl_sync(FULL, rec, 0);
-  off = __shfl_sync(FULL, off, 0);
-  write_record(a, r, A, Ws, W, rec, off, lane, 32);
-  int t = t0;
+  if (ntask == 0) return true;
+  int t = -1;
+  if (lane == 0) t = reserve_tasks(a, ntask);
+  t = __shfl_sync(FULL, t, 0);
+  if (t < 0) return false;
   for (int l = 0; l <= d; l++) {
-    Bits<WPL> Pl, Bl, Cl = C;
+    Bits<1> Pl, Bl, Cl = C;
     if (l < d) {
       const uint32_t *q = stk + (int64_t)l * stride;
-#pragma unroll
-      for (int k = 0; k < WPL; k++) {
-        Pl.w[k] = q[k * 32 + lane];
-        Bl.w[k] = q[32 * WPL + k * 32 + lane];
-      }
-      for (int m = l; m < d; m++) bclear(Cl, (int)stk[(int64_t)m * stride + 64 * WPL + 1]);
+      Pl.w[0] = q[lane];
+      Bl.w[0] = q[32 + lane];
+      for (int m = l; m < d; m++) bclear(Cl, level_word(stk + (int64_t)m * stride + 65));
     } else {
       Pl = P;
       Bl = B;
@@ -441,11 +483,45 @@ __device__ bool spill_frontier(const SA &a, const Root &r, const uint32_t *A, in
       if (x < 0) break;
       bclear(Bl, x);
       bclear(Pl, x);
-      emit_task<WPL, SM>(a, r, A, Ws, W, rec, t++, Cl, csize0 + l, Pl, x);
+      emit_task(a, r, A, Ws, W, rec, t++, Cl, csize0 + l, Pl, x);
     }
   }
-  __threadfence();
   return true;
+}
+
+// Spill state of a block worker past its node budget (warp-collective):
+// the first warp to see the budget spent writes the root's record (unless
+// the task already has one) and opens the spill; returns 1 when this warp
+// should spill now, 3 when there is no room, 0 or 2 to keep searching.
+__device__ int block_spill_state(const SA &a, const Root &r, const uint32_t *A, int Ws, int W, Pool<1> *pool,
+                                 long long budget) {
+  const int lane = threadIdx.x & 31;
+  int s = 0;
+  if (lane == 0) {
+    s = *(volatile int *)&pool->spill;
+    if (s == 0 && *(volatile int *)&pool->spent > budget && queue_short(a)) {
+      if (atomicCAS(&pool->spill, 0, 2) == 0) s = 4;
+      else s = *(volatile int *)&pool->spill;
+    }
+  }
+  s = __shfl_sync(FULL, s, 0);
+  if (s != 4) return s;
+  int rec = __shfl_sync(FULL, lane == 0 ? *(volatile int *)&pool->rec : 0, 0);
+  if (rec < 0) {
+    long long off = 0;
+    if (lane == 0) rec = reserve_record(a, r, Ws, &off);
+    rec = __shfl_sync(FULL, rec, 0);
+    off = __shfl_sync(FULL, off, 0);
+    if (rec >= 0) write_record(a, r, A, Ws, W, rec, off);
+  }
+  s = rec >= 0 ? 1 : 3;
+  if (lane == 0) {
+    *(volatile int *)&pool->rec = rec;
+    __threadfence_block();
+    atomicExch(&pool->spill, s);
+  }
+  __syncwarp();
+  return s;
 }
 
 // Depth-first Branch from one level (csize0 = |C| including the root u).
@@ -460,18 +536,36 @@ __device__ void dfs(const SA &a, const Root &r, const uint32_t *A, int Ws, int W
   int d = 0, csize = csize0;
   long long spent = 0;
   for (;;) {
-    if (*(volatile int32_t *)a.err) return;
+    if (__shfl_sync(FULL, lane == 0 ? *(volatile int32_t *)a.err : 0, 0)) return;
     int om = read_best(a.best, r.g);
     if (om > wat) {
       color_ise<WPL, SM>(A, Ws, W, P, om - csize, B);
       wat = om;
     }
-    if constexpr (WPL == 1) {
-      if (budget > 0 && spent > budget) {
-        // past its node budget a lone warp hands the rest of the tree to the
-        // task queue, where whole blocks search it
-        if (spill_frontier<WPL, SM>(a, r, A, Ws, W, stk, d, csize0, P, B, C)) return;
+    if constexpr (WPL == 1 && SM) {
+      // Past its node budget a worker hands the untried rest of its tree to
+      // the task queue, where whole blocks search it.
+      if (budget > 0 && !pool && spent > budget) {
+        int rec = -1;
+        long long off = 0;
+        if (lane == 0) rec = reserve_record(a, r, Ws, &off);
+        rec = __shfl_sync(FULL, rec, 0);
+        off = __shfl_sync(FULL, off, 0);
+        if (rec >= 0) {
+          write_record(a, r, A, Ws, W, rec, off);
+          if (spill_levels(a, r, A, Ws, W, stk, d, csize0, P, B, C, rec)) return;
+        }
         budget = 0;
+      } else if (budget > 0 && pool) {
+        const int st = block_spill_state(a, r, A, Ws, W, pool, budget);
+        if (st == 1) {
+          int rec = lane == 0 ? *(volatile int *)&pool->rec : 0;
+          rec = __shfl_sync(FULL, rec, 0);
+          if (spill_levels(a, r, A, Ws, W, stk, d, csize0, P, B, C, rec)) return;
+          budget = 0;
+        } else if (st == 3) {
+          budget = 0;
+        }
       }
     }
     int v = bhighest(B);
@@ -484,8 +578,8 @@ __device__ void dfs(const SA &a, const Root &r, const uint32_t *A, int Ws, int W
         P.w[k] = lv[k * 32 + lane];
         B.w[k] = lv[32 * WPL + k * 32 + lane];
       }
-      wat = (int)lv[64 * WPL];
-      int ch = (int)lv[64 * WPL + 1];
+      wat = level_word(lv + 64 * WPL);
+      const int ch = level_word(lv + 64 * WPL + 1);
       bclear(C, ch);
       csize--;
       continue;
@@ -496,6 +590,10 @@ __device__ void dfs(const SA &a, const Root &r, const uint32_t *A, int Ws, int W
     band_row<WPL, SM>(NP, A, Ws, W, v);
     nodes++;
     spent++;
+    if (lane == 0) {
+      if (pool && budget > 0) atomicAdd(&pool->spent, 1);
+      if (a.progress && (spent & 255) == 0) atomicAdd(a.progress, 1);
+    }
     if (!bany(NP)) {
       if (csize + 1 > om) {
         const Bits<WPL> Cc = C;
@@ -563,7 +661,7 @@ __device__ void dfs(const SA &a, const Root &r, const uint32_t *A, int Ws, int W
           }
           // clique at level lev: C minus the vertices chosen at levels >= lev
           Bits<WPL> Cl = C;
-          for (int l = lev; l < d; l++) bclear(Cl, (int)stk[(int64_t)l * stride + 64 * WPL + 1]);
+          for (int l = lev; l < d; l++) bclear(Cl, level_word(stk + (int64_t)l * stride + 64 * WPL + 1));
           bset(Cl, x);
           Bits<WPL> TP = Pl;
           band_row<WPL, SM>(TP, A, Ws, W, x);
@@ -585,6 +683,9 @@ __device__ void dfs(const SA &a, const Root &r, const uint32_t *A, int Ws, int W
                 pool->C[slot][k * 32 + lane] = Cl.w[k];
                 pool->P[slot][k * 32 + lane] = TP.w[k];
               }
+              // a *_sync exchange does not reconverge the warp: every lane's
+              // words must be written before lane 0 releases the pool
+              __syncwarp();
               if (lane == 0) {
                 pool->csize[slot] = tcs;
                 pool_unlock(pool);
@@ -638,7 +739,8 @@ __device__ __forceinline__ void load_P(const SA &a, int u, int om, int *Pidx, in
 // int4 loads per lane in flight, so a warp keeps eight rows' loads in the
 // memory system instead of one.
 __device__ __forceinline__ void build_rows(const SA &a, const int *Pidx, int p, const int *hk, const short *hv,
-                                           int hmask, uint32_t *A, int Ws, int wid, int nw) {
+                                           int hmask, uint32_t *A, int Ws, int wid, int nw,
+                                           unsigned long long *count) {
   const int lane = threadIdx.x & 31;
   const int grp = lane >> 3, gl = lane & 7;
   unsigned long long scanned = 0;
@@ -680,7 +782,7 @@ __device__ __forceinline__ void build_rows(const SA &a, const int *Pidx, int p, 
   // row entries scanned (Fact 3's work), one atomic per warp
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) scanned += __shfl_xor_sync(FULL, scanned, o);
-  if (lane == 0 && scanned) atomicAdd(a.counters + 4, scanned);
+  if (lane == 0 && scanned) atomicAdd(count, scanned);
 }
 
 // ------------------------------------------------------------ warp class ---
@@ -706,9 +808,9 @@ __global__ void __launch_bounds__(kSW * 32) search_warp_kernel(SA a) {
   for (;;) {
     __syncwarp();
     int idx = 0;
-    if (lane == 0) idx = atomicAdd(a.next, 1);
+    if (lane == 0) idx = *(volatile int32_t *)a.err ? INT_MAX : atomicAdd(a.next, 1);
     idx = __shfl_sync(FULL, idx, 0);
-    if (idx >= nroots || *(volatile int32_t *)a.err) break;
+    if (idx >= nroots) break;
     const int u = a.roots[idx];
     const int g = a.ogid ? a.ogid[u] : 0;
     int om = read_best(a.best, g);
@@ -732,7 +834,7 @@ __global__ void __launch_bounds__(kSW * 32) search_warp_kernel(SA a) {
     const int W = (p + 31) >> 5, Ws = W | 1;
     for (int i = lane; i < p * Ws; i += 32) S.A[i] = 0;
     __syncwarp();
-    build_rows(a, S.Pidx, p, S.hk, S.hv, hmask, S.A, Ws, 0, 1);
+    build_rows(a, S.Pidx, p, S.hk, S.hv, hmask, S.A, Ws, 0, 1, a.counters + 4);
     __syncwarp();
     // alive set = all p vertices; (omega-1)-core of G[P]
     if (lane < 4) S.al[lane] = (lane < W) ? ((lane == W - 1 && (p & 31)) ? ((1u << (p & 31)) - 1u) : FULL) : 0u;
@@ -775,7 +877,7 @@ __global__ void __launch_bounds__(kSW * 32) search_warp_kernel(SA a) {
     bzero(C);
     Root r{u, g, S.Pidx, p};
     dfs<1, true>(a, r, S.A, Ws, W, stk, 1, al, B, C, om, (Pool<1> *)nullptr, nodes, don,
-                 a.tasks ? kSpillNodes : 0);
+                 a.tasks ? a.budget_warp : 0);
   }
   if (lane == 0) {
     atomicAdd(a.counters + 0, colored);
@@ -811,14 +913,14 @@ struct BlockLayout {
 template <int WPL, bool SM>
 __device__ void block_search(const SA &a, const Root &r, const uint32_t *A, int Ws, int W, uint32_t *stk,
                              Pool<WPL> *pool, bool have, Bits<WPL> P, Bits<WPL> B, Bits<WPL> C, int cs, int wat,
-                             unsigned long long &nodes, unsigned long long &don) {
+                             unsigned long long &nodes, unsigned long long &don, long long budget) {
   const int lane = threadIdx.x & 31;
   const int g = r.g;
   long long waited = 0;
   int lastbeat = -1;
   for (;;) {
     if (have) {
-      dfs<WPL, SM>(a, r, A, Ws, W, stk, cs, P, B, C, wat, pool, nodes, don);
+      dfs<WPL, SM>(a, r, A, Ws, W, stk, cs, P, B, C, wat, pool, nodes, don, budget);
       have = false;
       if (lane == 0) {
         if (pool_lock(pool, a.err, a.spin)) {
@@ -850,7 +952,7 @@ __device__ void block_search(const SA &a, const Root &r, const uint32_t *A, int 
         lastbeat = beat;
         waited = 0;
       }
-      if (++waited > a.spin || *(volatile int32_t *)a.err) {
+      if (__shfl_sync(FULL, (++waited > a.spin || (lane == 0 && *(volatile int32_t *)a.err)) ? 1 : 0, 0)) {
         if (lane == 0) atomicExch(a.err, kDevTimeout);
         break;
       }
@@ -868,6 +970,29 @@ __device__ void block_search(const SA &a, const Root &r, const uint32_t *A, int 
     __syncwarp();
     if (lane == 0) pool_unlock(pool);
     __syncwarp();
+    if constexpr (WPL == 1 && SM) {
+      // while the block spills, pooled subproblems go to the queue as tasks
+      int sp = 0, rec = -1, t = -1;
+      if (lane == 0 && budget > 0 && *(volatile int *)&pool->spill == 1) {
+        sp = 1;
+        rec = *(volatile int *)&pool->rec;
+        t = reserve_tasks(a, 1);
+      }
+      sp = __shfl_sync(FULL, sp, 0);
+      if (sp) {
+        t = __shfl_sync(FULL, t, 0);
+        rec = __shfl_sync(FULL, rec, 0);
+        if (t >= 0) {
+          write_task(a, t, rec, cs, C, P);
+          if (lane == 0 && pool_lock(pool, a.err, a.spin)) {
+            pool->idle++;
+            pool_unlock(pool);
+          }
+          __syncwarp();
+          continue;
+        }
+      }
+    }
     int om2 = read_best(a.best, g);
     color_ise<WPL, SM>(A, Ws, W, P, om2 - cs, B);
     wat = om2;
@@ -892,7 +1017,7 @@ __global__ void __launch_bounds__(kBT) search_block_kernel(SA a) {
   uint32_t *al = (uint32_t *)(smem + L::off_al);
   uint32_t *rm = (uint32_t *)(smem + L::off_rm);
   Pool<WPL> *pool = (Pool<WPL> *)(smem + L::off_pool);
-  int *ctl = (int *)(smem + L::off_ctl);  // [0] root idx, [1] omega, [2] count, [3] flag, [4] go
+  int *ctl = (int *)(smem + L::off_ctl);  // [0] root idx, [1] omega, [2] count, [3] flag, [4] go, [5] error
   uint32_t *A = SM ? (uint32_t *)(smem + L::off_A) : (a.gmat + (int64_t)blockIdx.x * a.gmat_stride);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   uint32_t *stk = a.stack + ((int64_t)blockIdx.x * kBW + wid) * a.stack_stride;
@@ -905,10 +1030,11 @@ __global__ void __launch_bounds__(kBT) search_block_kernel(SA a) {
     if (tid == 0) {
       ctl[0] = atomicAdd(a.next, 1);
       ctl[2] = 0;
+      ctl[5] = *(volatile int32_t *)a.err;
     }
     __syncthreads();
     const int idx = ctl[0];
-    if (idx >= nroots || *(volatile int32_t *)a.err) break;
+    if (idx >= nroots || ctl[5]) break;
     const int u = a.roots[idx];
     const int g = a.ogid ? a.ogid[u] : 0;
     if (tid == 0) ctl[1] = *(volatile int32_t *)(a.best + g);
@@ -934,7 +1060,7 @@ __global__ void __launch_bounds__(kBT) search_block_kernel(SA a) {
     for (int64_t i = tid; i < (int64_t)p * Ws; i += kBT) A[i] = 0;
     if (!SM) __threadfence();
     __syncthreads();
-    build_rows(a, Pidx, p, hk, hv, hmask, A, Ws, wid, kBW);
+    build_rows(a, Pidx, p, hk, hv, hmask, A, Ws, wid, kBW, a.counters + 5);
     if (!SM) __threadfence();
     __syncthreads();
     for (int w = tid; w < L::WMAX; w += kBT)
@@ -989,24 +1115,15 @@ __global__ void __launch_bounds__(kBT) search_block_kernel(SA a) {
         pool->count = 0;
         pool->idle = kBW - 1;
         pool->beat = 0;
+        pool->spent = 0;
+        pool->spill = 0;
+        pool->rec = -1;
       }
     }
     __syncthreads();
     if (!ctl[4]) continue;
-    if constexpr (SM && WPL == 1) {
-      if (a.tasks) {
-        // Publish the root: its matrix and P list go to the arena and its
-        // first-level branches become tasks that any block may take.
-        // Without room the block searches the root itself.
-        if (wid == 0) {
-          const bool done = spill_frontier<WPL, SM>(a, r, A, Ws, W, stk, 0, 1, P, B, C);
-          if (lane == 0) ctl[4] = done ? 0 : 1;
-        }
-        __syncthreads();
-        if (!ctl[4]) continue;
-      }
-    }
-    block_search<WPL, SM>(a, r, A, Ws, W, stk, pool, have, P, B, C, cs, wat, nodes, don);
+    block_search<WPL, SM>(a, r, A, Ws, W, stk, pool, have, P, B, C, cs, wat, nodes, don,
+                          (SM && WPL == 1 && a.tasks) ? a.budget_block : 0);
     __syncthreads();
   }
   if (lane == 0) {
@@ -1018,9 +1135,13 @@ __global__ void __launch_bounds__(kBT) search_block_kernel(SA a) {
 }
 
 
-// Tasks of published roots: each block takes tasks in order, loads the
-// root's matrix and P list into shared memory when it changes, and searches
-// the task with its warps as in search_block_kernel.
+// The task queue: tasks of spilled roots, searched by whole blocks.  A block
+// takes the next task, loads its root's matrix and P list into shared
+// memory when the root changes, and searches it like a block worker; past
+// its node budget, while the queue is short, it spills again.  The kernel
+// ends when the queue is empty and no block holds a task (a block counts
+// itself in `active` before it looks for a task and leaves it only after
+// its spilled tasks are visible).
 __global__ void __launch_bounds__(kBT) branch_task_kernel(SA a) {
   using L = BlockLayout<1, true>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1031,18 +1152,120 @@ __global__ void __launch_bounds__(kBT) branch_task_kernel(SA a) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   uint32_t *stk = a.stack + ((int64_t)blockIdx.x * kBW + wid) * a.stack_stride;
   unsigned long long nodes = 0, don = 0;
-  const int ntasks = min(*a.ntasks, a.task_cap);
   int loaded = -1;
   for (;;) {
     __syncthreads();
-    if (tid == 0) ctl[0] = atomicAdd(a.task_next, 1);
+    Bits<1> C, P;
+    bzero(C);
+    bzero(P);
+    if (wid == 0) {
+      int got = -1;
+      if (lane == 0) {
+        long long waited = 0;
+        int last = -1;
+        atomicAdd(a.active, 1);
+        __threadfence();
+        for (;;) {
+          if (*(volatile int32_t *)a.err) break;
+          const int tail = *(volatile int32_t *)a.ntasks, head = *(volatile int32_t *)a.task_next;
+          if (head < tail) {
+            if (atomicCAS(a.task_next, head, head + 1) == head) {
+              got = head;
+              break;
+            }
+            continue;
+          }
+          // nothing queued: stand down and wait for work or for the end (no
+          // block holds a task and the queue is empty)
+          atomicSub(a.active, 1);
+          __threadfence();
+          bool done = false, work = false;
+          while (!done && !work) {
+            if (*(volatile int32_t *)a.err) {
+              done = true;
+              break;
+            }
+            const int act = *(volatile int32_t *)a.active;
+            __threadfence();
+            const int tail2 = *(volatile int32_t *)a.ntasks, head2 = *(volatile int32_t *)a.task_next;
+            if (head2 < tail2) {
+              work = true;
+            } else if (act == 0) {
+              done = true;
+            } else {
+              const int prog = *(volatile int32_t *)a.progress + tail2;
+              if (prog != last) {
+                last = prog;
+                waited = 0;
+              }
+              if (++waited > a.spin) {
+                atomicExch(a.err, kDevTimeout);
+                done = true;
+              }
+              __nanosleep(512);
+            }
+          }
+          if (done) break;
+          atomicAdd(a.active, 1);
+          __threadfence();
+        }
+        if (got >= 0) {
+          // the slot's words are written before its word reads 2*lap+1
+          const int slot = got & (a.task_cap - 1);
+          const int lap2 = 2 * (got / a.task_cap);
+          long long w = 0;
+          while (*(volatile int32_t *)(a.ready + slot) != lap2 + 1) {
+            if (++w > a.spin) {
+              atomicExch(a.err, kDevTimeout);
+              break;
+            }
+            __nanosleep(64);
+          }
+          __threadfence();
+        }
+      }
+      got = __shfl_sync(FULL, got, 0);
+      if (got >= 0) {
+        const uint32_t *tk = a.tasks + (int64_t)(got & (a.task_cap - 1)) * kTaskWords;
+        C.w[0] = __ldcg(tk + 2 + lane);
+        P.w[0] = __ldcg(tk + 34 + lane);
+        const int cs1 = (int)__ldcg(tk + 1), rec1 = (int)__ldcg(tk + 0);
+        __syncwarp();
+        if (lane == 0) {
+          __threadfence();
+          // free the slot for the next lap's writer
+          atomicExch(a.ready + (got & (a.task_cap - 1)), 2 * (got / a.task_cap) + 2);
+          ctl[1] = cs1;
+          ctl[2] = rec1;
+        }
+      }
+      if (lane == 0) {
+        ctl[0] = got;
+        ctl[3] = *(volatile int32_t *)a.err;
+      }
+    }
     __syncthreads();
     const int t = ctl[0];
-    if (t >= ntasks || *(volatile int32_t *)a.err) break;
-    const uint32_t *tk = a.tasks + (int64_t)t * kTaskWords;
-    if (tk[1] == 0u) continue;  // decided when it was written
-    const int rec = (int)tk[0];
-    const RootRec rr = a.recs[rec];
+    if (t < 0) break;
+    const int cs0 = ctl[1], rec = ctl[2];
+    if (cs0 == 0 || ctl[3]) {  // empty task (or giving up)
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        atomicSub(a.active, 1);
+      }
+      continue;
+    }
+    RootRec rr;
+    {
+      const int *rp = (const int *)(a.recs + rec);
+      rr.u = __ldcg(rp + 0);
+      rr.g = __ldcg(rp + 1);
+      rr.p = __ldcg(rp + 2);
+      rr.W = __ldcg(rp + 3);
+      rr.Ws = __ldcg(rp + 4);
+      rr.off = __ldcg((const long long *)(rp + 6));
+    }
     if (rec != loaded) {
       const uint32_t *sm = a.arena + rr.off;
       for (int i = tid; i < rr.p * rr.Ws; i += kBT) A[i] = __ldcg(sm + i);
@@ -1052,12 +1275,11 @@ __global__ void __launch_bounds__(kBT) branch_task_kernel(SA a) {
     }
     __syncthreads();
     Root r{rr.u, rr.g, Pidx, rr.p};
-    Bits<1> P, B, C;
-    int cs = (int)tk[1], wat = 0;
+    Bits<1> B;
+    bzero(B);
+    int cs = cs0, wat = 0;
     bool have = false;
     if (wid == 0) {
-      C.w[0] = tk[2 + lane];
-      P.w[0] = tk[34 + lane];
       wat = read_best(a.best, rr.g);
       color_ise<1, true>(A, rr.Ws, rr.W, P, wat - cs, B);
       have = bany(B);
@@ -1067,15 +1289,19 @@ __global__ void __launch_bounds__(kBT) branch_task_kernel(SA a) {
         pool->count = 0;
         pool->idle = kBW - 1;
         pool->beat = 0;
+        pool->spent = 0;
+        pool->spill = 0;
+        pool->rec = rec;
       }
-    } else {
-      bzero(P);
-      bzero(B);
-      bzero(C);
     }
     __syncthreads();
-    if (!ctl[4]) continue;
-    block_search<1, true>(a, r, A, rr.Ws, rr.W, stk, pool, have, P, B, C, cs, wat, nodes, don);
+    if (ctl[4]) block_search<1, true>(a, r, A, rr.Ws, rr.W, stk, pool, have, P, B, C, cs, wat, nodes, don,
+                                      a.budget_block);
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      atomicSub(a.active, 1);
+    }
   }
   if (lane == 0) {
     atomicAdd(a.counters + 2, nodes);
@@ -1085,15 +1311,17 @@ __global__ void __launch_bounds__(kBT) branch_task_kernel(SA a) {
 
 }  // namespace
 
-int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_split, long long spin_limit,
-                  SearchCounters *cnt) {
+int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_split, int split_nodes,
+                  long long spin_limit, SearchCounters *cnt) {
   // Persistent kernels with fixed grids; the root counts are read on the
   // device (pg.d_counts), and sizes are bounded by K(G) >= |N+(u)|, so the
   // launches need no host synchronisation.
   void *p;
   MC_TRY(ws_get(g, "se.ctr", 16 * sizeof(unsigned long long), &p));
-  // [0..4] colored, branched, nodes, donations, entries; [8..9] three root
-  // queue heads; [10] arena words used; [11..12] records, tasks, task head
+  // [0..5] colored, branched, nodes, donations, row entries read by warp
+  // workers, by block workers; [8..9] three root
+  // queue heads; [10] arena words used; [11..12] records, task tail, task
+  // head, blocks holding a task
   unsigned long long *ctr = (unsigned long long *)p;
   int32_t *next = (int32_t *)(ctr + 8);
   MC_CUDA_TRY(cudaMemsetAsync(ctr, 0, 16 * sizeof(unsigned long long), g->stream));
@@ -1124,9 +1352,17 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_spli
     a.nrec = (int32_t *)(ctr + 11);
     MC_TRY(ws_get(g, "se.tasks", (size_t)kTaskCap * kTaskWords * 4, &p));
     a.tasks = (uint32_t *)p;
+    MC_TRY(ws_get(g, "se.ready", (size_t)kTaskCap * 4, &p));
+    a.ready = (int32_t *)p;
+    MC_CUDA_TRY(cudaMemsetAsync(a.ready, 0, (size_t)kTaskCap * 4, g->stream));
     a.task_cap = kTaskCap;
     a.ntasks = a.nrec + 1;
     a.task_next = a.nrec + 2;
+    a.active = a.nrec + 3;
+    a.progress = a.nrec + 4;
+    a.queue_gate = 0;
+    a.budget_warp = split_nodes > 0 ? split_nodes : kSpillNodes;
+    a.budget_block = 4 * a.budget_warp;
   }
   // Block-worker launches (shared-memory matrices) and the task kernel share
   // one shape and one stack buffer.
@@ -1150,7 +1386,8 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_spli
   }
 
   // block class first (largest trees), then big, then warp class, then the
-  // tasks the first and last of these published
+  // tasks the first and last of these published; events 8-12 time each
+  MC_TRY(record_event(g, 8));
   if (kbound > wmax) {
     a.stack_stride = stride_b;
     a.stack = stk_b;
@@ -1162,6 +1399,7 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_spli
     g_launches++;
     MC_CUDA_TRY(cudaGetLastError());
   }
+  MC_TRY(record_event(g, 9));
   if (kbound > 1024) {
     if (kbound > 4096) return MC_ERR_UNSUPPORTED;
     using L = BlockLayout<4, false>;
@@ -1184,6 +1422,7 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_spli
     g_launches++;
     MC_CUDA_TRY(cudaGetLastError());
   }
+  MC_TRY(record_event(g, 10));
   {
     int per_sm = 0;
     MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_warp_kernel, kSW * 32, 0));
@@ -1200,13 +1439,16 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_spli
     g_launches++;
     MC_CUDA_TRY(cudaGetLastError());
   }
+  MC_TRY(record_event(g, 11));
   if (!no_split) {
     a.stack_stride = stride_b;
     a.stack = stk_b;
+    a.queue_gate = 2 * blocks_b;
     branch_task_kernel<<<blocks_b, kBT, smem_b, g->stream>>>(a);
     g_launches++;
     MC_CUDA_TRY(cudaGetLastError());
   }
+  MC_TRY(record_event(g, 12));
   cnt->d_counters = ctr;
   return MC_OK;
 }
@@ -1219,7 +1461,8 @@ int read_search_counters(mc_graph *g, SearchCounters *cnt) {
   cnt->roots_branched = h[1];
   cnt->nodes = h[2];
   cnt->donations = h[3];
-  cnt->entries = h[4];
+  cnt->entries = h[4] + h[5];
+  cnt->entries_block = h[5];
   cnt->tasks = (unsigned long long)std::min(((const int32_t *)(h + 11))[1], kTaskCap);
   return MC_OK;
 }

@@ -120,18 +120,23 @@ def test_options_keep_omega(mc, opts):
 
 
 def test_split_tasks_keep_omega(mc):
-    """Block-worker neighbourhoods that reach Branch are split into
-    first-level tasks; with the heuristic off (omega starts at 0) many roots
-    branch, and the result must equal the unsplit search and the oracle."""
+    """Workers past their Branch-node budget spill the rest of their trees
+    to the task queue.  Small budgets force spills on every tree, from warp
+    and block workers and from tasks themselves; the result must equal the
+    unsplit search and the oracle."""
     seen = 0
-    for g in medium_graphs()[:4] + [gg.relabel(gg.turan(300, 33), 3)]:
+    graphs = medium_graphs()[:4] + [gg.relabel(gg.turan(300, 33), 3), gg.rmat(14, 16, planted=30, seed=16)]
+    for g in graphs:
         h = load(mc, g)
-        om, wit, st = mc.mc_max_clique(h, heuristic=2, warp_max=16)
         om2, wit2, st2 = mc.mc_max_clique(h, heuristic=2, warp_max=16, no_split=True)
-        assert om == om2 == ref_omega(g), g.name
-        assert oracle.is_clique(g, wit) and oracle.is_clique(g, wit2)
+        assert om2 == ref_omega(g), g.name
         assert st2["tasks"] == 0
-        seen += st["tasks"]
+        for budget in (1, 7, 64):
+            for wm in (16, 0):
+                om, wit, st = mc.mc_max_clique(h, heuristic=2, warp_max=wm, split_nodes=budget)
+                assert om == om2, (g.name, budget, wm)
+                assert oracle.is_clique(g, wit)
+                seen += st["tasks"]
     assert seen > 0
 
 
