@@ -39,9 +39,9 @@ def load_peaks():
 
 # Per-launch DRAM traffic of search_block_kernel on the R-MAT scale-22 solve,
 # from the ncu capture summarised in profiles/search_block_kernel_rmat_s22.md
-# (dram__bytes_read.sum + dram__bytes_write.sum); None until a capture of the
-# current kernel exists.
-SEARCH_BLOCK_TRAFFIC_S22 = None
+# (dram__bytes_read.sum + dram__bytes_write.sum); set to None whenever the
+# kernel changes until it is captured again.
+SEARCH_BLOCK_TRAFFIC_S22 = 121.6e6
 
 
 def roofline(stats, n, nnz, clk, dev):
