@@ -41,7 +41,7 @@ def load_peaks():
 # from the ncu capture summarised in profiles/search_block_kernel_rmat_s22.md
 # (dram__bytes_read.sum + dram__bytes_write.sum); set to None whenever the
 # kernel changes until it is captured again.
-SEARCH_BLOCK_TRAFFIC_S22 = 121.6e6
+SEARCH_BLOCK_TRAFFIC_S22 = None
 
 
 def roofline(stats, n, nnz, clk, dev):

@@ -75,6 +75,8 @@ struct SA {
   int32_t *active;               // blocks of the task kernel holding a task
   int32_t *progress;             // heartbeat: bumped every 256 Branch nodes
   int32_t queue_gate;            // spill only while fewer tasks wait (0 = always)
+  int32_t *overflow;             // roots too large for this launch's layout (or null)
+  int64_t *noverflow;
   long long budget_warp;         // Branch nodes before a warp worker spills
   long long budget_block;        // ... and a block, on one root or task
 };
@@ -888,9 +890,9 @@ __global__ void __launch_bounds__(kSW * 32) search_warp_kernel(SA a) {
 
 // ----------------------------------------------------------- block class ---
 
-template <int WPL, bool SM>
+template <int WPL, bool SM, int PC = 1024 * WPL>
 struct BlockLayout {
-  static constexpr int PCAP = 1024 * WPL;
+  static constexpr int PCAP = PC;
   static constexpr int HCAP = 2 * PCAP;
   static constexpr int WMAX = 32 * WPL;
   static constexpr int WSMAX = WMAX + 1;
@@ -1007,9 +1009,12 @@ __device__ void block_search(const SA &a, const Root &r, const uint32_t *A, int 
   }
 }
 
-template <int WPL, bool SM>
-__global__ void __launch_bounds__(kBT) search_block_kernel(SA a) {
-  using L = BlockLayout<WPL, SM>;
+// PC: candidate capacity of the shared-memory layout.  The 512-candidate
+// layout fits two blocks per SM; its roots with more candidates go to the
+// overflow list, which the 1,024-candidate launch then searches.
+template <int WPL, bool SM, int PC>
+__global__ void __launch_bounds__(kBT, (SM && PC <= 512) ? 2 : 1) search_block_kernel(SA a) {
+  using L = BlockLayout<WPL, SM, PC>;
   extern __shared__ __align__(16) unsigned char smem[];
   int *Pidx = (int *)(smem + L::off_P);
   int *hk = (int *)(smem + L::off_hk);
@@ -1048,6 +1053,10 @@ __global__ void __launch_bounds__(kBT) search_block_kernel(SA a) {
     __syncthreads();
     const int p = ctl[2];
     if (p > L::PCAP) {
+      if (a.overflow) {
+        if (tid == 0) a.overflow[atomicAdd((unsigned long long *)a.noverflow, 1ull)] = u;
+        continue;
+      }
       if (tid == 0) atomicExch(a.err, kDevUnsupported);
       break;
     }
@@ -1319,9 +1328,9 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_spli
   void *p;
   MC_TRY(ws_get(g, "se.ctr", 16 * sizeof(unsigned long long), &p));
   // [0..5] colored, branched, nodes, donations, row entries read by warp
-  // workers, by block workers; [8..9] three root
-  // queue heads; [10] arena words used; [11..12] records, task tail, task
-  // head, blocks holding a task
+  // workers, by block workers; [8..9] four root queue heads; [10] arena
+  // words used; [11..13] records, task tail, task head, blocks holding a
+  // task, heartbeat; [14] roots left to the 1,024-candidate launch
   unsigned long long *ctr = (unsigned long long *)p;
   int32_t *next = (int32_t *)(ctr + 8);
   MC_CUDA_TRY(cudaMemsetAsync(ctr, 0, 16 * sizeof(unsigned long long), g->stream));
@@ -1364,21 +1373,26 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_spli
     a.budget_warp = split_nodes > 0 ? split_nodes : kSpillNodes;
     a.budget_block = 4 * a.budget_warp;
   }
-  // Block-worker launches (shared-memory matrices) and the task kernel share
-  // one shape and one stack buffer.
+  // Block workers (shared-memory matrices): a 512-candidate launch first,
+  // then a 1,024-candidate launch over the roots it could not hold; the task
+  // kernel shares the large layout and its stack buffer.
   using LB = BlockLayout<1, true>;
-  const size_t smem_b = LB::bytes;
-  int per_sm_b = 0;
-  MC_CUDA_TRY(cudaFuncSetAttribute(search_block_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  using LM = BlockLayout<1, true, 512>;
+  const size_t smem_b = LB::bytes, smem_m = LM::bytes;
+  MC_CUDA_TRY(cudaFuncSetAttribute(search_block_kernel<1, true, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem_b));
+  MC_CUDA_TRY(cudaFuncSetAttribute(search_block_kernel<1, true, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem_m));
   MC_CUDA_TRY(cudaFuncSetAttribute(branch_task_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
-  MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, search_block_kernel<1, true>, kBT, smem_b));
-  int per_sm_t = 0;
+  int per_sm_b = 0, per_sm_t = 0, per_sm_m = 0;
+  MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, search_block_kernel<1, true, 1024>, kBT, smem_b));
   MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_t, branch_task_kernel, kBT, smem_b));
+  MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_m, search_block_kernel<1, true, 512>, kBT, smem_m));
   per_sm_b = std::min(per_sm_b, per_sm_t);
-  if (per_sm_b < 1) return MC_ERR_CUDA;
-  const int blocks_b = g->sm_count * per_sm_b;
+  if (per_sm_b < 1 || per_sm_m < 1) return MC_ERR_CUDA;
+  const int blocks_b = g->sm_count * per_sm_b, blocks_m = g->sm_count * per_sm_m;
   const int64_t stride_b = (int64_t)(std::min(kbound, 1024) + 2) * (64 + 2);
+  const int64_t stride_m = (int64_t)(std::min(kbound, 512) + 2) * (64 + 2);
   uint32_t *stk_b = nullptr;
   if (kbound > wmax || !no_split) {
     MC_TRY(ws_get(g, "se.stk_b", (size_t)blocks_b * kBW * stride_b * 4, &p));
@@ -1389,22 +1403,40 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_spli
   // tasks the first and last of these published; events 8-12 time each
   MC_TRY(record_event(g, 8));
   if (kbound > wmax) {
-    a.stack_stride = stride_b;
-    a.stack = stk_b;
     a.gmat = nullptr;
     a.roots = pg.roots_block;
     a.nroots = pg.d_counts + 4;
     a.next = next + 0;
-    search_block_kernel<1, true><<<blocks_b, kBT, smem_b, g->stream>>>(a);
+    if (kbound > 512) {
+      MC_TRY(ws_get(g, "se.ovf", (size_t)std::max<int64_t>(g->n, 1) * 4, &p));
+      a.overflow = (int32_t *)p;
+      a.noverflow = (int64_t *)(ctr + 14);
+    }
+    MC_TRY(ws_get(g, "se.stk_m", (size_t)blocks_m * kBW * stride_m * 4, &p));
+    a.stack = (uint32_t *)p;
+    a.stack_stride = stride_m;
+    search_block_kernel<1, true, 512><<<blocks_m, kBT, smem_m, g->stream>>>(a);
     g_launches++;
     MC_CUDA_TRY(cudaGetLastError());
+    if (kbound > 512) {
+      a.roots = a.overflow;
+      a.nroots = a.noverflow;
+      a.next = next + 3;
+      a.overflow = nullptr;
+      a.noverflow = nullptr;
+      a.stack = stk_b;
+      a.stack_stride = stride_b;
+      search_block_kernel<1, true, 1024><<<blocks_b, kBT, smem_b, g->stream>>>(a);
+      g_launches++;
+      MC_CUDA_TRY(cudaGetLastError());
+    }
   }
   MC_TRY(record_event(g, 9));
   if (kbound > 1024) {
     if (kbound > 4096) return MC_ERR_UNSUPPORTED;
     using L = BlockLayout<4, false>;
     const size_t smem = L::bytes;
-    MC_CUDA_TRY(cudaFuncSetAttribute(search_block_kernel<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    MC_CUDA_TRY(cudaFuncSetAttribute(search_block_kernel<4, false, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
     const int blocks = g->sm_count;
     const int pmax = kbound;
@@ -1418,7 +1450,7 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_spli
     a.roots = pg.roots_big;
     a.nroots = pg.d_counts + 5;
     a.next = next + 1;
-    search_block_kernel<4, false><<<blocks, kBT, smem, g->stream>>>(a);
+    search_block_kernel<4, false, 4096><<<blocks, kBT, smem, g->stream>>>(a);
     g_launches++;
     MC_CUDA_TRY(cudaGetLastError());
   }
