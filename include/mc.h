@@ -79,8 +79,10 @@ typedef struct {
   /* ordering == 1: one float score per vertex (host or device), higher first;
    * for a batch, one score per vertex of the union */
   const float *scores;
-  /* heuristic seeds from the scores: the top `seeds` vertices of each graph
-   * are also grown by Algorithm 1's greedy step first; 0 = none */
+  /* heuristic seeds from the scores: the `seeds` vertices of highest score
+   * (over all graphs of a batch) are grown first, each by Algorithm 1's
+   * greedy step with one change: the next member is the remaining candidate
+   * of highest score (ties: larger core number, smaller id); 0 = none */
   int32_t seeds;
   /* 1 = run the whole solve as one CUDA graph: the first call with these
    * options solves directly (sizing every buffer), then captures the solve;
@@ -192,7 +194,7 @@ int mc_verify_clique(mc_graph *g, const int32_t *vertices, int32_t k, int32_t *i
  * captured in a mode that forbids allocation, inside an allocator hook, or
  * under a host that owns every byte of device memory it gives the library.
  * Nothing is allocated: the peel's working memory is one fixed device array
- * of about 30 MB inside the library, which every GPU that loads the library
+ * of about 33 MB inside the library, which every GPU that loads the library
  * holds until the process exits.
  *   n: vertices, at most 1,048,576; row_ptr (n+1 int64) and col_idx
  *   (row_ptr[n] int32, at most 67,108,864 entries): a simple symmetric CSR

@@ -329,7 +329,7 @@ static int enqueue_solve(mc_graph *g, const mc_options &o, Pruned *pg, SearchCou
       d_seeds = seeds;
     }
   }
-  if (o.heuristic != 2 && g->n > 0) MC_TRY(launch_heuristic(g, o.heuristic, spin, d_seeds, nseeds));
+  if (o.heuristic != 2 && g->n > 0) MC_TRY(launch_heuristic(g, o.heuristic, spin, d_seeds, nseeds, d_scores));
   MC_TRY(record_event(g, 2));
   int32_t *h_heur = (int32_t *)((char *)g->h_small + 1024);
   MC_CUDA_TRY(cudaMemcpyAsync(h_heur, g->best, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
@@ -548,7 +548,7 @@ int mc_heuristic_clique(mc_graph *g, const int32_t *core, int32_t mode, int32_t 
   MC_TRY(ensure_cores(g, kDefaultSpinLimit));
   MC_CUDA_TRY(cudaMemsetAsync(g->best, 0, g->count * 4, g->stream));
   MC_CUDA_TRY(cudaMemsetAsync(g->lock, 0, g->count * 4, g->stream));
-  if (g->n > 0) MC_TRY(launch_heuristic(g, mode, kDefaultSpinLimit, nullptr, 0));
+  if (g->n > 0) MC_TRY(launch_heuristic(g, mode, kDefaultSpinLimit, nullptr, 0, nullptr));
   MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
   MC_TRY(check_device_error(g));
   int32_t size = 0;

@@ -17,6 +17,9 @@
 // mode 1 (deterministic): every start vertex is grown with threshold 0 and
 //   the largest clique wins, ties to the smallest start vertex (a 64-bit
 //   atomicMax key); a second kernel regrows the winner and writes it.
+// Seeds (learned scores): the top-scored vertices are also grown first, by
+//   the same greedy step with the next member chosen by highest score; in
+//   mode 1 they only add candidates, so the bound can only rise.
 // Start vertices that cannot reach the current best (K(v) + 1 below it) are
 // skipped, and a greedy run stops once C plus all remaining candidates cannot
 // beat the best; neither changes the result of either mode.
@@ -31,6 +34,8 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kHT = 256;  // threads per block
+constexpr int64_t kSmallCap = 4096;  // least candidate entries per warp in the first launch
+constexpr int64_t kWarm = 256;       // start vertices of the warm-up launch
 
 struct HA {
   int64_t n;
@@ -48,7 +53,15 @@ struct HA {
   unsigned long long *detkey;  // per graph (mode 1)
   const int32_t *seeds;
   int64_t nseeds;
+  const float *score;    // learned vertex scores (seeded start vertices grow by them)
   int64_t begin, limit;  // start vertices [begin, limit) of the visiting order in this launch
+  int64_t cap;           // candidate buffer entries per warp
+  // start vertices whose candidate set exceeds cap are appended to defer and
+  // grown by a second launch with larger buffers, which visits list[0..*nlist)
+  int32_t *defer;
+  unsigned long long *ndefer;
+  const int32_t *list;
+  const unsigned long long *nlist;
   // batches peeled graph by graph: visit the j-th highest vertex of every
   // graph before the (j+1)-th of any, so each graph's maximum is set early
   int32_t count;
@@ -75,6 +88,16 @@ __device__ __forceinline__ Key warp_best(Key x) {
 __device__ __forceinline__ Key key_of(const HA &a, int u) {
   return Key{a.core[u], (int)(a.rp[u + 1] - a.rp[u]), u};
 }
+// Order of a float score as an int (larger score, larger int).
+__device__ __forceinline__ int score_order(float f) {
+  const int i = __float_as_int(f);
+  return i >= 0 ? i : i ^ 0x7fffffff;
+}
+// Candidate key of a seeded growth: higher score first, then Algorithm 1's
+// order (larger core number, then smaller id).
+__device__ __forceinline__ Key key_of_scored(const HA &a, int u) {
+  return Key{score_order(a.score[u]), a.core[u], u};
+}
 __device__ __forceinline__ bool in_row(const HA &a, int x, int y) {
   int64_t lo = a.rp[x], hi = a.rp[x + 1];
   while (lo < hi) {
@@ -86,9 +109,13 @@ __device__ __forceinline__ bool in_row(const HA &a, int x, int y) {
 }
 
 // Greedy clique from v (all lanes).  thr: candidate core threshold; stop_at:
-// stop once |C| + |cand| < stop_at (cannot reach it).  Writes the clique to
-// cl[0..size) and returns its size.
-__device__ int grow(const HA &a, int v, int thr, int stop_at, int32_t *cand, int32_t *cl) {
+// stop once |C| + |cand| < stop_at (cannot reach it).  by_score: the next
+// member is the candidate of highest learned score instead of Algorithm 1's
+// largest core number.  Writes the clique to cl[0..size) and returns its
+// size, or -1 if the candidates do not fit in cap entries (nothing is grown
+// then).
+__device__ int grow(const HA &a, int v, int thr, int stop_at, int32_t *cand, int32_t *cl, int64_t cap,
+                    bool by_score = false, int g = 0) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const Key none{INT_MIN, INT_MIN, INT_MAX};
@@ -105,16 +132,32 @@ __device__ int grow(const HA &a, int v, int thr, int stop_at, int32_t *cand, int
     }
     unsigned m = __ballot_sync(FULL, ok);
     if (ok) {
-      cand[cnt + __popc(m & lt)] = u;
-      Key k = key_of(a, u);
+      const int at = cnt + __popc(m & lt);
+      if (at < cap) cand[at] = u;
+      Key k = by_score ? key_of_scored(a, u) : key_of(a, u);
       if (better(k, bk)) bk = k;
     }
     cnt += __popc(m);
   }
+  if (cnt > cap) return -1;
   bk = warp_best(bk);
   int size = 1;
   if (lane == 0) cl[0] = v;
   for (;;) {
+    // the shared best rises while this clique grows: re-read it every step
+    // (mode 0: prune candidates below it and stop when C plus candidates
+    // cannot beat it; mode 1: stop when they cannot reach its size)
+    int cur = 0;
+    if (lane == 0)
+      cur = a.mode == 0 ? *(volatile int32_t *)(a.best + g)
+                        : (int)(*(volatile unsigned long long *)(a.detkey + g) >> 32);
+    cur = __shfl_sync(FULL, cur, 0);
+    if (a.mode == 0) {
+      thr = max(thr, cur);
+      stop_at = max(stop_at, cur + 1);
+    } else {
+      stop_at = max(stop_at, cur);
+    }
     if (cnt == 0 || size + cnt < stop_at) break;
     const int w = bk.id;
     if (lane == 0) cl[size] = w;
@@ -162,11 +205,12 @@ __device__ int grow(const HA &a, int v, int thr, int stop_at, int32_t *cand, int
         pos = wp;
         keep = keep && i < cnt && x != w;
       }
+      if (keep && thr > 0) keep = a.core[x] >= thr;
       unsigned m = __ballot_sync(FULL, keep);
       __syncwarp();
       if (keep) {
         cand[out + __popc(m & lt)] = x;
-        Key k = key_of(a, x);
+        Key k = by_score ? key_of_scored(a, x) : key_of(a, x);
         if (better(k, nb)) nb = k;
       }
       out += __popc(m);
@@ -184,14 +228,16 @@ __global__ void __launch_bounds__(kHT) heuristic_kernel(HA a) {
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int32_t *cand = a.cand + gw * a.cand_stride;
   int32_t *cl = a.cl + gw * a.cl_stride;
-  const int64_t total = a.limit;
+  const int64_t total = a.list ? (int64_t)*a.nlist : a.limit;
   for (;;) {
     int64_t i = 0;
     if (lane == 0) i = *(volatile int32_t *)a.err ? total : a.begin + atomicAdd(a.next, 1);
     i = __shfl_sync(FULL, (long long)i, 0);
     if (i >= total) break;
     int v;
-    if (i < a.nseeds) {
+    if (a.list) {
+      v = a.list[i];
+    } else if (i < a.nseeds) {
       v = a.seeds[i];
     } else if (a.interleave) {
       const int64_t r = i - a.nseeds, gi = r % a.count, j = r / a.count;
@@ -208,7 +254,12 @@ __global__ void __launch_bounds__(kHT) heuristic_kernel(HA a) {
       if (lane == 0) mx = *(volatile int32_t *)(a.best + g);
       mx = __shfl_sync(FULL, mx, 0);
       if (kv < mx) continue;
-      int size = grow(a, v, mx, mx + 1, cand, cl);
+      const bool seeded = !a.list && i < a.nseeds && a.score;
+      int size = grow(a, v, mx, mx + 1, cand, cl, a.cap, seeded, g);
+      if (size < 0) {
+        if (lane == 0) a.defer[atomicAdd(a.ndefer, 1ull)] = v;
+        continue;
+      }
       if (size > mx) {
         dev::raise_incumbent(a.best, a.lock, a.wit, a.voff, g, size, a.err, a.spin, [&](int ln, int32_t *base) {
           for (int t = ln; t < size; t += 32) base[t] = cl[t];
@@ -220,8 +271,15 @@ __global__ void __launch_bounds__(kHT) heuristic_kernel(HA a) {
       cur = __shfl_sync(FULL, cur, 0);
       int bsz = (int)(cur >> 32);
       if (kv + 1 < bsz) continue;
-      int size = grow(a, v, 0, bsz, cand, cl);
-      unsigned long long key = ((unsigned long long)size << 32) | (unsigned)(0x7fffffff - v);
+      const bool seeded = !a.list && i < a.nseeds && a.score;
+      int size = grow(a, v, 0, bsz, cand, cl, a.cap, seeded, g);
+      if (size < 0) {
+        if (lane == 0) a.defer[atomicAdd(a.ndefer, 1ull)] = v;
+        continue;
+      }
+      // key: size, then seeded growth, then the smaller start vertex
+      unsigned long long key = ((unsigned long long)size << 32) | ((seeded ? 1ull : 0ull) << 31) |
+                               (unsigned)(0x7fffffff - v);
       if (lane == 0 && key > cur) atomicMax(a.detkey + g, key);
     }
   }
@@ -238,8 +296,9 @@ __global__ void heuristic_finalize_kernel(HA a, int32_t ngraphs) {
     unsigned long long key = a.detkey[g];
     int size = (int)(key >> 32);
     if (size == 0) continue;
-    int v = 0x7fffffff - (int)(key & 0xffffffffu);
-    int s2 = grow(a, v, 0, 0, cand, cl);
+    const bool seeded = ((key >> 31) & 1ull) != 0;
+    int v = 0x7fffffff - (int)(key & 0x7fffffffu);
+    int s2 = grow(a, v, 0, 0, cand, cl, a.cap, seeded && a.score, (int)g);
     if (s2 != size) {
       if (lane == 0) atomicExch(a.err, kDevCheck);
       continue;
@@ -255,25 +314,38 @@ __global__ void heuristic_finalize_kernel(HA a, int32_t ngraphs) {
 
 }  // namespace
 
-int launch_heuristic(mc_graph *g, int mode, long long spin_limit, const int32_t *seeds, int64_t nseeds) {
+int launch_heuristic(mc_graph *g, int mode, long long spin_limit, const int32_t *seeds, int64_t nseeds,
+                     const float *scores) {
   if (g->n == 0) return MC_OK;
   void *p;
-  const int64_t cstride = (int64_t)g->max_degree + 1;
+  // First launch: 32 warps per SM with candidate buffers that share 2 GiB;
+  // start vertices with more candidates are deferred to a second launch with
+  // buffers for the largest degree (as many warps as 2 GiB allows).
+  const int64_t full = (int64_t)g->max_degree + 1;
+  const int64_t budget = (int64_t)1 << 29;  // int32 entries (2 GiB)
+  const int64_t cap_s = std::min<int64_t>(full, std::max<int64_t>(kSmallCap, budget / ((int64_t)g->sm_count * 32)));
+  const bool two = full > cap_s;
   const int64_t lstride = (int64_t)g->max_core + 2;
-  // warps limited so that the candidate buffers stay within ~1 GiB
-  int64_t warps = (int64_t)g->sm_count * 16;
-  const int64_t budget = (int64_t)1 << 28;  // int32 entries
-  warps = std::max<int64_t>(32, std::min<int64_t>(warps, budget / cstride));
-  warps = std::min<int64_t>(warps, ((g->n + nseeds) + 0) + 32);
-  warps = (warps + 7) / 8 * 8;
-  MC_TRY(ws_get(g, "he.cand", (size_t)warps * cstride * 4, &p));
+  int64_t warps_s = std::min<int64_t>((int64_t)g->sm_count * 32, budget / cap_s);
+  warps_s = std::max<int64_t>(32, std::min<int64_t>(warps_s, g->n + nseeds + 32));
+  warps_s = (warps_s + 7) / 8 * 8;
+  int64_t warps_b = std::max<int64_t>(32, std::min<int64_t>((int64_t)g->sm_count * 16, budget / full));
+  warps_b = (warps_b + 7) / 8 * 8;
+  const int64_t cand_entries = std::max(warps_s * cap_s, two || mode == 1 ? warps_b * full : 0);
+  MC_TRY(ws_get(g, "he.cand", (size_t)cand_entries * 4, &p));
   int32_t *cand = (int32_t *)p;
-  MC_TRY(ws_get(g, "he.cl", (size_t)warps * lstride * 4, &p));
+  MC_TRY(ws_get(g, "he.cl", (size_t)std::max(warps_s, warps_b) * lstride * 4, &p));
   int32_t *cl = (int32_t *)p;
   MC_TRY(ws_get(g, "he.ctl", 64 + (size_t)g->count * 8, &p));
-  int32_t *next = (int32_t *)p;
+  int32_t *next = (int32_t *)p;  // [0] warm-up, [2] main launch, [1] deferred launch; [4..5] deferred count
+  unsigned long long *ndefer = (unsigned long long *)((char *)p + 16);
   unsigned long long *detkey = (unsigned long long *)((char *)p + 64);
   MC_CUDA_TRY(cudaMemsetAsync(p, 0, 64 + (size_t)g->count * 8, g->stream));
+  int32_t *defer = nullptr;
+  if (two) {
+    MC_TRY(ws_get(g, "he.defer", (size_t)(g->n + nseeds) * 4, &p));
+    defer = (int32_t *)p;
+  }
   HA a{};
   a.n = g->n;
   a.rp = g->row_ptr;
@@ -289,25 +361,53 @@ int launch_heuristic(mc_graph *g, int mode, long long spin_limit, const int32_t 
   a.spin = spin_limit;
   a.mode = mode;
   a.cand = cand;
-  a.cand_stride = cstride;
+  a.cand_stride = cap_s;
+  a.cap = two ? cap_s : full;
+  a.defer = defer;
+  a.ndefer = ndefer;
   a.cl = cl;
   a.cl_stride = lstride;
   a.next = next;
   a.detkey = detkey;
   a.seeds = seeds;
   a.nseeds = seeds ? nseeds : 0;
+  a.score = seeds ? scores : nullptr;
   a.count = g->count;
   a.max_graph_n = g->max_graph_n;
   a.interleave = (g->count > 1 && g->max_graph_n <= kBatchPeelCap) ? 1 : 0;
-  const int blocks = (int)((warps * 32 + kHT - 1) / kHT);
   const int64_t total = a.interleave ? (int64_t)g->count * g->max_graph_n + a.nseeds : g->n + a.nseeds;
+  // A warm-up launch grows the first kWarm start vertices (the seeds and the
+  // largest core numbers) with kWarm warps, so the shared maximum is already
+  // high when the other warps start and prunes their candidate sets.
+  const int64_t warm = std::min<int64_t>(total, kWarm);
   a.begin = 0;
-  a.limit = total;
-  heuristic_kernel<<<blocks, kHT, 0, g->stream>>>(a);
+  a.limit = warm;
+  heuristic_kernel<<<(int)((std::min<int64_t>(warps_s, kWarm) * 32 + kHT - 1) / kHT), kHT, 0, g->stream>>>(a);
   g_launches++;
   MC_CUDA_TRY(cudaGetLastError());
+  if (warm < total) {
+    a.begin = warm;
+    a.limit = total;
+    a.next = next + 2;
+    heuristic_kernel<<<(int)((warps_s * 32 + kHT - 1) / kHT), kHT, 0, g->stream>>>(a);
+    g_launches++;
+    MC_CUDA_TRY(cudaGetLastError());
+  }
+  // second launch (deferred start vertices) and the mode-1 regrow use the
+  // large buffers
+  a.cand_stride = full;
+  a.cap = full;
+  const int blocks_b = (int)((warps_b * 32 + kHT - 1) / kHT);
+  if (two) {
+    a.list = defer;
+    a.nlist = ndefer;
+    a.next = next + 1;
+    heuristic_kernel<<<blocks_b, kHT, 0, g->stream>>>(a);
+    g_launches++;
+    MC_CUDA_TRY(cudaGetLastError());
+  }
   if (mode == 1) {
-    heuristic_finalize_kernel<<<blocks, kHT, 0, g->stream>>>(a, g->count);
+    heuristic_finalize_kernel<<<blocks_b, kHT, 0, g->stream>>>(a, g->count);
     g_launches++;
     MC_CUDA_TRY(cudaGetLastError());
   }

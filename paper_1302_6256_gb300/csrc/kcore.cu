@@ -7,7 +7,7 @@
 //           frontier (warp-aggregated appends); vertices of larger degree are
 //           compacted into the next live list, so later scans only touch what
 //           is left; if nothing joins, k jumps to the smallest remaining degree;
-//   process each frontier vertex becomes one work item per 512-edge chunk of
+//   process each frontier vertex becomes one work item per 128-edge chunk of
 //           its row; the items appended before a grid barrier are split
 //           statically over all warps (rows under 32 edges one lane per
 //           item, longer chunks one warp per item, coalesced), and every neighbour whose
@@ -28,7 +28,7 @@ namespace {
 
 constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
-constexpr int kChunk = 512;  // edges per work item
+constexpr int kChunk = 128;  // edges per work item
 
 struct KcoreCtl {
   unsigned bar_count, bar_gen;

@@ -72,7 +72,8 @@ int launch_core_numbers(mc_graph *g, long long spin_limit);
 
 // Heuristic (Algorithm 1).  mode 0 racy, 1 deterministic.  Raises the
 // incumbent of every graph.  seeds (nullable, device): vertices grown first.
-int launch_heuristic(mc_graph *g, int mode, long long spin_limit, const int32_t *seeds, int64_t nseeds);
+int launch_heuristic(mc_graph *g, int mode, long long spin_limit, const int32_t *seeds, int64_t nseeds,
+                     const float *scores);
 
 // Pruned, oriented graph and the root lists (see prune.cu).
 struct Pruned {

@@ -773,10 +773,7 @@ __device__ __forceinline__ void build_rows(const SA &a, const int *Pidx, int p, 
         for (int j = 0; j < 4; j++) {
           if (yy[j] < 0) continue;
           int b = hash_find(hk, hv, hmask, yy[j]);
-          if (b >= 0) {
-            atomicOr(A + (int64_t)i * Ws + (b >> 5), 1u << (b & 31));
-            atomicOr(A + (int64_t)b * Ws + (i >> 5), 1u << (i & 31));
-          }
+          if (b >= 0) atomicOr(A + (int64_t)i * Ws + (b >> 5), 1u << (b & 31));
         }
       }
     }
@@ -785,6 +782,38 @@ __device__ __forceinline__ void build_rows(const SA &a, const int *Pidx, int p, 
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) scanned += __shfl_xor_sync(FULL, scanned, o);
   if (lane == 0 && scanned) atomicAdd(count, scanned);
+}
+
+// Complete the adjacency matrix from its lower triangle.  build_rows sets
+// bit (i, b) for every edge of G[P] with b < i (a later neighbour has a
+// higher rank, hence a smaller index in P); the 32 x 32 tiles on and below
+// the diagonal are transposed with warp ballots and OR-ed into their mirror
+// tiles.  A tile's reads (lower words) and writes (upper words, or the same
+// diagonal tile after all its rows were read) never overlap another tile's.
+template <bool SM>
+__device__ void symmetrize(uint32_t *A, int Ws, int W, int p, int wid, int nw) {
+  const int lane = threadIdx.x & 31;
+  const int tiles = W * (W + 1) / 2;
+  for (int t = wid; t < tiles; t += nw) {
+    // tile t = (I, J) with J <= I, row-major over the lower triangle
+    int I = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+    while (I * (I + 1) / 2 > t) I--;
+    while ((I + 1) * (I + 2) / 2 <= t) I++;
+    const int J = t - I * (I + 1) / 2;
+    const int r = 32 * I + lane;
+    const uint32_t x = (r < p) ? rw<SM>(A, (int64_t)r * Ws + J) : 0u;
+    uint32_t col = 0;
+#pragma unroll
+    for (int c = 0; c < 32; c++) {
+      const uint32_t m = __ballot_sync(FULL, (x >> c) & 1u);
+      if (lane == c) col = m;
+    }
+    const int rt = 32 * J + lane;
+    if (rt < p) {
+      const int64_t at = (int64_t)rt * Ws + I;
+      A[at] = (I == J) ? (x | col) : (rw<SM>(A, at) | col);
+    }
+  }
 }
 
 // ------------------------------------------------------------ warp class ---
@@ -837,6 +866,8 @@ __global__ void __launch_bounds__(kSW * 32) search_warp_kernel(SA a) {
     for (int i = lane; i < p * Ws; i += 32) S.A[i] = 0;
     __syncwarp();
     build_rows(a, S.Pidx, p, S.hk, S.hv, hmask, S.A, Ws, 0, 1, a.counters + 4);
+    __syncwarp();
+    symmetrize<true>(S.A, Ws, W, p, 0, 1);
     __syncwarp();
     // alive set = all p vertices; (omega-1)-core of G[P]
     if (lane < 4) S.al[lane] = (lane < W) ? ((lane == W - 1 && (p & 31)) ? ((1u << (p & 31)) - 1u) : FULL) : 0u;
@@ -893,7 +924,7 @@ __global__ void __launch_bounds__(kSW * 32) search_warp_kernel(SA a) {
 template <int WPL, bool SM, int PC = 1024 * WPL>
 struct BlockLayout {
   static constexpr int PCAP = PC;
-  static constexpr int HCAP = 2 * PCAP;
+  static constexpr int HCAP = 4 * PCAP;  // load factor 1/4: short probes
   static constexpr int WMAX = 32 * WPL;
   static constexpr int WSMAX = WMAX + 1;
   // bytes: Pidx, hk, hv, alive/rm words, pool, control, matrix
@@ -1070,6 +1101,9 @@ __global__ void __launch_bounds__(kBT, (SM && PC <= 512) ? 2 : 1) search_block_k
     if (!SM) __threadfence();
     __syncthreads();
     build_rows(a, Pidx, p, hk, hv, hmask, A, Ws, wid, kBW, a.counters + 5);
+    if (!SM) __threadfence();
+    __syncthreads();
+    symmetrize<SM>(A, Ws, W, p, wid, kBW);
     if (!SM) __threadfence();
     __syncthreads();
     for (int w = tid; w < L::WMAX; w += kBT)

@@ -76,3 +76,42 @@ def test_learned_ordering_keeps_omega_exact(mc, kind):
         om, wit, st = mc.mc_max_clique(h, ordering=1, scores=s, seeds=16)
         assert om == oracle.max_clique(g)[0]
         assert oracle.is_clique(g, wit)
+
+
+def test_trained_network_raises_the_lower_bound(mc):
+    """What the committed network (trained on 2,000 generated Chung-Lu and
+    R-MAT graphs, seed 7) gains over the method without it, on 60 held-out
+    graphs of the same families (seed 11).  In the deterministic heuristic
+    the seeds only add candidate cliques (each seed grown by highest score),
+    so the lower bound can only rise; the trained network must close part of
+    the gap between it and omega, more than random scores do, and omega never
+    changes."""
+    import os
+    from paper_1302_6256_gb300 import train_ordering as T
+    w = np.load(os.path.join(os.path.dirname(mc.__file__), "ordering_mlp.npy"))
+    net = mc.MLP(seed=0)
+    net.set_params(w)
+    rng = np.random.default_rng(5)
+    gap = {"plain": 0, "learned": 0, "random": 0}
+    for i in range(60):
+        g = T.make_graph(i, 11)
+        h = mc.mc_load_csr(g.row_ptr, g.col_idx)
+        feat = torch.zeros((g.n, 6), dtype=torch.float32, device="cuda")
+        score = torch.zeros(g.n, dtype=torch.float32, device="cuda")
+        mc.mc_features(h, feat)
+        net.forward(feat, score)
+        rand = torch.from_numpy(rng.random(g.n).astype(np.float32)).cuda()
+        om, _, st = mc.mc_max_clique(h, heuristic=1)
+        om_l, wit_l, st_l = mc.mc_max_clique(h, heuristic=1, ordering=1, scores=score, seeds=64)
+        om_r, _, st_r = mc.mc_max_clique(h, heuristic=1, ordering=1, scores=rand, seeds=64)
+        assert om == om_l == om_r
+        assert oracle.is_clique(g, wit_l) and len(wit_l) == om
+        assert st_l["heuristic_size"] >= st["heuristic_size"]
+        assert st_r["heuristic_size"] >= st["heuristic_size"]
+        gap["plain"] += om - st["heuristic_size"]
+        gap["learned"] += om - st_l["heuristic_size"]
+        gap["random"] += om - st_r["heuristic_size"]
+        h.close()
+    print("lower-bound gap over 60 held-out graphs:", gap)
+    assert gap["learned"] < gap["plain"]
+    assert gap["learned"] < gap["random"]
