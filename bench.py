@@ -95,6 +95,25 @@ def roofline(stats, n, nnz, clk, dev):
 
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest x over all ranks of the initialised process group (x
+    itself on one rank); device: where the reduction tensor lives (cuda for
+    NCCL, cpu for gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, ranks: int, ms_max: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time (weak scaling: every rank solves its own replica)."""
+    return units_per_rank * ranks / (ms_max / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -174,6 +193,7 @@ def run_reference(args):
         return
     import oracle
     import graphgen as gg
+    from graphgen import workloads as W
     g = gg.rmat(SAMPLE_SCALE, 16, 0.57, 0.19, 0.19, planted=40, seed=2)
     for _ in range(args.warmup):
         oracle.max_clique(g)
@@ -188,8 +208,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": "rmat scale=%d ef=16 abc=(0.57,0.19,0.19) planted=40 seed=2 (CPU sample of the "
-                               "rmat scale=22 workload)" % SAMPLE_SCALE},
+        "config": {"workload": W.RMAT_S22,
+                   "sample": "each step: the oracle on R-MAT scale %d from the same generator (n=%d, m=%d); "
+                             "the scale-22 solve takes the oracle 6,161 s" % (SAMPLE_SCALE, g.n, g.m)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -261,7 +282,8 @@ def run_single(args):
 
     mc.load_library()
     gen = {"rmat-s22": (W.RMAT_S22, W.rmat_s22), "rmat-s24": (W.RMAT_S24, W.rmat_s24),
-           "chung-lu-20k": (W.CHUNG_LU_20K, W.chung_lu_20k)}[args.workload]
+           "chung-lu-20k": (W.CHUNG_LU_20K, W.chung_lu_20k),
+           "chung-lu-100m": (W.CHUNG_LU_100M, W.chung_lu_100m)}[args.workload]
     g = gen[1]()
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
@@ -312,7 +334,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="rmat-s22", choices=["rmat-s22", "er-batch", "rmat-s24", "chung-lu-20k"])
+    ap.add_argument("--workload", default="rmat-s22", choices=["rmat-s22", "er-batch", "rmat-s24", "chung-lu-20k", "chung-lu-100m"])
     ap.add_argument("--form", default="chosen", choices=["chosen", "plain", "per-graph", "learned"],
                     help="chosen: the default solve (graph replay for batches); plain: direct launches, "
                          "degeneracy order; learned: root order and heuristic seeds from the trained network; "
@@ -374,11 +396,8 @@ def main():
     launches = mc.mc_launch_count() - launches0
     ms = t0.elapsed_time(t1) / args.steps
     clk = clocks.stop()
-    if ws > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = g.m * ws / (ms / 1e3)
+    ms = max_over_ranks(ms, dev)
+    value = job_value(g.m, ws, ms)
 
     # end to end through the public API from host buffers: H2D of the CSR,
     # solve, D2H of omega and witness, every step
@@ -391,10 +410,7 @@ def main():
         he.close()
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - te) * 1e3 / e2e_steps
-    if ws > 1:
-        tt = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(e2e_ms, dev)
     assert om_e == om
 
     n = g.n
@@ -408,7 +424,7 @@ def main():
         "config": {"workload": W.RMAT_S22, "n": n, "m": g.m, "omega": om, "max_core": stats[-1]["max_core"],
                    "form": "chosen (block/warp workers, degeneracy-order colouring)", "l2": "inputs > L2 (537 MB CSR)",
                    "parallelism": "replicas" if ws > 1 else "1 GPU"},
-        "e2e": {"value": g.m * ws / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+        "e2e": {"value": job_value(g.m, ws, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(rp_h.numel() * 8 + ci_h.numel() * 4),
                 "d2h_bytes_per_step": int(4 + 4 * om)},
         "roofline": roof,

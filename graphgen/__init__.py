@@ -171,15 +171,13 @@ def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c:
 
 def chung_lu(n: int, gamma: float, mean: float, cap: float, planted: int = 0, seed: int = 1) -> Graph:
     """Chung-Lu graph: i.i.d. Pareto(gamma) expected degrees with the given mean
-    (after capping at cap), round(sum(w)/2) endpoint pairs drawn proportional to
-    w, then symmetrised and deduplicated, plus an optional planted clique."""
+    (after capping at cap, the weights' mean), round(n * mean / 2) endpoint
+    pairs drawn proportional to w, then symmetrised and deduplicated, plus an
+    optional planted clique."""
     w = np.empty(n, np.float64)
     rc = _L().gg_chung_lu_weights(n, gamma, mean, cap, seed, _ptr(w))
     if rc != 0:
         raise ValueError("graphgen: chung-lu weights failed (%d)" % rc)
-    tot = 0.0
-    for x in np.split(w, max(1, n // (1 << 20))):
-        tot += float(np.sum(x))
     ne = int(round(n * mean / 2.0))
     members, ps, pd = _planted_edges(n, planted, seed)
     src = np.empty(ne + ps.shape[0], np.int32)

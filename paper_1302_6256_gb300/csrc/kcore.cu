@@ -29,6 +29,7 @@ namespace {
 constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
 constexpr int kChunk = 128;  // edges per work item
+constexpr int kPer = 4;      // edges per lane in flight in a long chunk
 
 struct KcoreCtl {
   unsigned bar_count, bar_gen;
@@ -225,21 +226,29 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
           append_frontier(nf, u, k, rp, core, order, wq, ctl);
         }
       }
-      // pass B: longer chunks, one warp each (coalesced row reads)
+      // pass B: longer chunks, one warp each (coalesced row reads); each
+      // lane keeps kPer edges in flight before the frontier appends
       for (long long t = s0 + gwarp; t < e0; t += nwarps) {
         const long long item = __ldcg(wq + t);
         const int v = (int)(item >> 32), c = (int)(item & 0xffffffff);
         const int64_t b0 = rp[v] + (int64_t)c * kChunk;
         const int len = (int)(min(rp[v + 1], b0 + kChunk) - b0);
         if (len < 32) continue;
-        for (int eb = 0; eb < len; eb += 32) {
-          bool nf = false;
-          int u = -1;
-          if (eb + lane < len) {
-            u = ci[b0 + eb + lane];
-            if (__ldcg(deg + u) > k) nf = (atomicSub(deg + u, 1) == k + 1);
+        for (int eb = 0; eb < len; eb += 32 * kPer) {
+          int u[kPer];
+          bool nf[kPer];
+#pragma unroll
+          for (int q = 0; q < kPer; q++) {
+            const int e = eb + q * 32 + lane;
+            u[q] = e < len ? ci[b0 + e] : -1;
           }
-          append_frontier(nf, u, k, rp, core, order, wq, ctl);
+#pragma unroll
+          for (int q = 0; q < kPer; q++) {
+            nf[q] = false;
+            if (u[q] >= 0 && __ldcg(deg + u[q]) > k) nf[q] = (atomicSub(deg + u[q], 1) == k + 1);
+          }
+#pragma unroll
+          for (int q = 0; q < kPer; q++) append_frontier(nf[q], u[q], k, rp, core, order, wq, ctl);
         }
       }
       long long e1 = 0;

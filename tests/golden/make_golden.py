@@ -6,7 +6,9 @@ counts, the SHA-256 of the int32 core-number array (little endian), the
 maximum core number, the maximum clique size omega with one witness, and
 the oracle's run statistics.  Usage:
 
-    python tests/golden/make_golden.py chung-lu-20k rmat-s22 ...
+    python tests/golden/make_golden.py [--out DIR] chung-lu-20k rmat-s22 ...
+
+(--out: write the files to DIR instead of this folder.)
 """
 import hashlib
 import json
@@ -26,11 +28,15 @@ SLUGS = {
     "chung-lu-20k": (W.CHUNG_LU_20K, W.chung_lu_20k),
     "rmat-s22": (W.RMAT_S22, W.rmat_s22),
     "rmat-s24": (W.RMAT_S24, W.rmat_s24),
+    "chung-lu-100m": (W.CHUNG_LU_100M, W.chung_lu_100m),
 }
 
 
 def core_hash(core: np.ndarray) -> str:
     return hashlib.sha256(np.ascontiguousarray(core, dtype="<i4").tobytes()).hexdigest()
+
+
+OUT = HERE
 
 
 def batch_golden(count):
@@ -44,7 +50,7 @@ def batch_golden(count):
         omegas.append(int(om))
     out = {"workload": b.name, "graphs": b.count, "n": b.n, "m": b.m, "omegas": omegas,
            "oracle_s": round(time.time() - t0, 1)}
-    with open(os.path.join(HERE, "er-batch-%d.json" % count), "w") as f:
+    with open(os.path.join(OUT, "er-batch-%d.json" % count), "w") as f:
         json.dump(out, f)
     print("er-batch", count, "max omega", max(omegas), round(time.time() - t0, 1), flush=True)
 
@@ -65,10 +71,14 @@ def main(slugs):
         out = {"workload": name, "n": g.n, "m": g.m, "core_sha256": core_hash(core),
                "max_core": int(core.max()), "omega": int(om), "witness": [int(x) for x in wit],
                "oracle_stats": st, "oracle_core_s": round(t1 - t0, 3), "oracle_max_clique_s": round(t2 - t1, 3)}
-        with open(os.path.join(HERE, slug + ".json"), "w") as f:
+        with open(os.path.join(OUT, slug + ".json"), "w") as f:
             json.dump(out, f, indent=1)
         print(slug, om, st, round(t2 - t1, 1), flush=True)
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or ["chung-lu-20k"])
+    args = sys.argv[1:]
+    if len(args) >= 2 and args[0] == "--out":
+        OUT = args[1]
+        args = args[2:]
+    main(args or ["chung-lu-20k"])

@@ -248,6 +248,32 @@ def test_rmat_s22_golden(mc):
     assert oracle.is_clique(g, wit)
 
 
+@pytest.mark.slow
+def test_chung_lu_100m_golden(mc):
+    """The social-network-scale workload (Chung-Lu, 10^8 vertices, about 1.8
+    billion edges) at full size: core-number hash and omega against the stored
+    oracle run, the witness checked by the oracle's clique test.  Generating
+    the graph takes minutes on the host, so it runs only with
+    MC_FULL_SIZE=1."""
+    if os.environ.get("MC_FULL_SIZE") != "1":
+        pytest.skip("set MC_FULL_SIZE=1 to run the 10^8-vertex workload")
+    path = os.path.join(HERE, "golden", "chung-lu-100m.json")
+    if not os.path.exists(path):
+        pytest.skip("oracle golden file for chung-lu-100m not generated")
+    from graphgen import workloads as W
+    import hashlib
+    gold = json.load(open(path))
+    g = W.chung_lu_100m()
+    assert g.n == gold["n"] and g.m == gold["m"]
+    h = load(mc, g, flags=0)
+    core, kmax = mc.mc_core_numbers(h)
+    assert kmax == gold["max_core"]
+    assert hashlib.sha256(core.astype("<i4").tobytes()).hexdigest() == gold["core_sha256"]
+    om, wit, st = mc.mc_max_clique(h)
+    assert om == gold["omega"]
+    assert oracle.is_clique(g, wit)
+
+
 def test_graph_replay_single_and_batch(mc):
     """opt graph=1: the first call solves and captures, later calls replay the
     captured CUDA graph; every replay must give the oracle's omega."""
