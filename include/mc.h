@@ -117,6 +117,9 @@ typedef struct {
                                     roots' adjacency matrices (Fact 3's work) */
   int64_t neighbourhood_entries_block; /* ... of which read by block workers */
   int64_t tasks;               /* subproblems spilled to the task queue */
+  int64_t heuristic_grows;     /* start vertices grown by Algorithm 1 */
+  int64_t heuristic_tests;     /* adjacency tests of its greedy steps */
+  int64_t heuristic_row_entries; /* CSR row entries it read (gathers, merges) */
   int32_t max_core, heuristic_size, omega, verified;
 } mc_stats;
 

@@ -61,7 +61,8 @@ class Stats(ctypes.Structure):
                 ("roots_colored", ctypes.c_int64), ("roots_branched", ctypes.c_int64),
                 ("nodes", ctypes.c_int64), ("donations", ctypes.c_int64),
                 ("neighbourhood_entries", ctypes.c_int64), ("neighbourhood_entries_block", ctypes.c_int64),
-                ("tasks", ctypes.c_int64),
+                ("tasks", ctypes.c_int64), ("heuristic_grows", ctypes.c_int64),
+                ("heuristic_tests", ctypes.c_int64), ("heuristic_row_entries", ctypes.c_int64),
                 ("max_core", ctypes.c_int32), ("heuristic_size", ctypes.c_int32),
                 ("omega", ctypes.c_int32), ("verified", ctypes.c_int32)]
 

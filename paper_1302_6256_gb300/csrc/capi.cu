@@ -329,7 +329,8 @@ static int enqueue_solve(mc_graph *g, const mc_options &o, Pruned *pg, SearchCou
       d_seeds = seeds;
     }
   }
-  if (o.heuristic != 2 && g->n > 0) MC_TRY(launch_heuristic(g, o.heuristic, spin, d_seeds, nseeds, d_scores));
+  g->heur_ran = o.heuristic != 2 && g->n > 0;
+  if (g->heur_ran) MC_TRY(launch_heuristic(g, o.heuristic, spin, d_seeds, nseeds, d_scores));
   MC_TRY(record_event(g, 2));
   int32_t *h_heur = (int32_t *)((char *)g->h_small + 1024);
   MC_CUDA_TRY(cudaMemcpyAsync(h_heur, g->best, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
@@ -385,6 +386,13 @@ static int finish_solve(mc_graph *g, Pruned *pg, SearchCounters *sc, const int32
   st->max_core = g->max_core;
   g->heur0 = *(int32_t *)((char *)g->h_small + 1024);  // copied by the solve; the stream is synchronised
   st->heuristic_size = g->heur0;
+  if (g->d_heur_ctr && g->heur_ran) {
+    unsigned long long hc[3];
+    MC_CUDA_TRY(cudaMemcpy(hc, g->d_heur_ctr, sizeof(hc), cudaMemcpyDeviceToHost));
+    st->heuristic_grows = (int64_t)hc[0];
+    st->heuristic_tests = (int64_t)hc[1];
+    st->heuristic_row_entries = (int64_t)hc[2];
+  }
   std::vector<int32_t> ok(g->count);
   MC_CUDA_TRY(cudaMemcpy(ok.data(), d_ok, g->count * 4, cudaMemcpyDeviceToHost));
   st->verified = 1;

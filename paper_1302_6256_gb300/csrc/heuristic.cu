@@ -41,6 +41,7 @@ struct HA {
   int64_t n;
   const int64_t *rp;
   const int32_t *ci, *core, *order, *gid;
+  unsigned long long *ctr;  // [0] start vertices grown, [1] adjacency tests, [2] row entries read
   const int64_t *voff;
   int32_t *best, *lock, *wit, *err;
   long long spin;
@@ -140,6 +141,10 @@ __device__ int grow(const HA &a, int v, int thr, int stop_at, int32_t *cand, int
     cnt += __popc(m);
   }
   if (cnt > cap) return -1;
+  if (lane == 0) {
+    atomicAdd(a.ctr + 0, 1ull);
+    atomicAdd(a.ctr + 2, (unsigned long long)(e1 - e0));
+  }
   bk = warp_best(bk);
   int size = 1;
   if (lane == 0) cl[0] = v;
@@ -170,6 +175,10 @@ __device__ int grow(const HA &a, int v, int thr, int stop_at, int32_t *cand, int
     Key nb = none;
     const int64_t r0 = a.rp[w], r1 = a.rp[w + 1];
     const bool merge = (int64_t)cnt * 16 >= (r1 - r0);
+    if (lane == 0) {
+      atomicAdd(a.ctr + 1, (unsigned long long)cnt);
+      if (merge) atomicAdd(a.ctr + 2, (unsigned long long)(r1 - r0));
+    }
     int64_t pos = r0;
     for (int base = 0; base < cnt; base += 32) {
       const int i = base + lane;
@@ -339,6 +348,7 @@ int launch_heuristic(mc_graph *g, int mode, long long spin_limit, const int32_t 
   MC_TRY(ws_get(g, "he.ctl", 64 + (size_t)g->count * 8, &p));
   int32_t *next = (int32_t *)p;  // [0] warm-up, [2] main launch, [1] deferred launch; [4..5] deferred count
   unsigned long long *ndefer = (unsigned long long *)((char *)p + 16);
+  unsigned long long *hctr = (unsigned long long *)((char *)p + 24);  // three counters, bytes 24..47
   unsigned long long *detkey = (unsigned long long *)((char *)p + 64);
   MC_CUDA_TRY(cudaMemsetAsync(p, 0, 64 + (size_t)g->count * 8, g->stream));
   int32_t *defer = nullptr;
@@ -348,6 +358,8 @@ int launch_heuristic(mc_graph *g, int mode, long long spin_limit, const int32_t 
   }
   HA a{};
   a.n = g->n;
+  a.ctr = hctr;
+  g->d_heur_ctr = hctr;
   a.rp = g->row_ptr;
   a.ci = g->col_idx;
   a.core = g->core;

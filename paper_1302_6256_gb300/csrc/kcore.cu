@@ -29,7 +29,7 @@ namespace {
 constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
 constexpr int kChunk = 128;  // edges per work item
-constexpr int kPer = 4;      // edges per lane in flight in a long chunk
+constexpr int kPer = 4;      // edges per lane in flight
 
 struct KcoreCtl {
   unsigned bar_count, bar_gen;
@@ -216,14 +216,18 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
         }
         const bool small = valid && len < 32;
         const int maxlen = dev::warp_max(small ? len : 0);
-        for (int j = 0; j < maxlen; j++) {
-          bool nf = false;
-          int u = -1;
-          if (small && j < len) {
-            u = ci[b0 + j];
-            if (__ldcg(deg + u) > k) nf = (atomicSub(deg + u, 1) == k + 1);
+        for (int j0 = 0; j0 < maxlen; j0 += kPer) {
+          int u[kPer];
+          bool nf[kPer];
+#pragma unroll
+          for (int q = 0; q < kPer; q++) u[q] = (small && j0 + q < len) ? ci[b0 + j0 + q] : -1;
+#pragma unroll
+          for (int q = 0; q < kPer; q++) {
+            nf[q] = false;
+            if (u[q] >= 0 && __ldcg(deg + u[q]) > k) nf[q] = (atomicSub(deg + u[q], 1) == k + 1);
           }
-          append_frontier(nf, u, k, rp, core, order, wq, ctl);
+#pragma unroll
+          for (int q = 0; q < kPer; q++) append_frontier(nf[q], u[q], k, rp, core, order, wq, ctl);
         }
       }
       // pass B: longer chunks, one warp each (coalesced row reads); each

@@ -128,6 +128,8 @@ struct mc_graph {
   bool cores_valid = false;
   int32_t max_core = 0;
   int32_t heur0 = 0;  // heuristic clique size of graph 0 in the last solve
+  unsigned long long *d_heur_ctr = nullptr;  // heuristic work counters of the last solve (device)
+  bool heur_ran = false;                     // the last solve ran the heuristic
   int32_t warp_max_used = 128;  // warp/block split of the current solve
   bool capturing = false;       // inside CUDA graph capture: no host synchronisation
   int32_t *core = nullptr, *order = nullptr, *pos = nullptr;  // n each (device)

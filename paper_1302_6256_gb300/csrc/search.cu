@@ -90,6 +90,7 @@ constexpr long long kArenaWords = 64ll << 20;  // 256 MB of published matrices
 constexpr int kRecCap = 1 << 16;
 constexpr int kTaskCap = 1 << 20;          // ring slots, 277 MB
 constexpr long long kSpillNodes = 4096;    // default Branch-node budget of a warp worker
+constexpr int kMidCap = 512;               // candidates of the two-blocks-per-SM block layout
 
 template <int WPL>
 struct Bits {
@@ -925,8 +926,8 @@ template <int WPL, bool SM, int PC = 1024 * WPL>
 struct BlockLayout {
   static constexpr int PCAP = PC;
   static constexpr int HCAP = 4 * PCAP;  // load factor 1/4: short probes
-  static constexpr int WMAX = 32 * WPL;
-  static constexpr int WSMAX = WMAX + 1;
+  static constexpr int WMAX = 32 * WPL;                 // alive / removal words (one per lane)
+  static constexpr int WSMAX = ((PCAP + 31) / 32) | 1;  // largest matrix row stride, W | 1
   // bytes: Pidx, hk, hv, alive/rm words, pool, control, matrix
   static constexpr size_t off_P = 0;
   static constexpr size_t off_hk = off_P + PCAP * 4;
@@ -1040,11 +1041,11 @@ __device__ void block_search(const SA &a, const Root &r, const uint32_t *A, int 
   }
 }
 
-// PC: candidate capacity of the shared-memory layout.  The 512-candidate
-// layout fits two blocks per SM; its roots with more candidates go to the
-// overflow list, which the 1,024-candidate launch then searches.
+// PC: candidate capacity of the shared-memory layout.  The kMidCap layout
+// fits two blocks per SM; its roots with more candidates go to the overflow
+// list, which the 1,024-candidate launch then searches.
 template <int WPL, bool SM, int PC>
-__global__ void __launch_bounds__(kBT, (SM && PC <= 512) ? 2 : 1) search_block_kernel(SA a) {
+__global__ void __launch_bounds__(kBT, (SM && PC <= kMidCap) ? 2 : 1) search_block_kernel(SA a) {
   using L = BlockLayout<WPL, SM, PC>;
   extern __shared__ __align__(16) unsigned char smem[];
   int *Pidx = (int *)(smem + L::off_P);
@@ -1411,22 +1412,23 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_spli
   // then a 1,024-candidate launch over the roots it could not hold; the task
   // kernel shares the large layout and its stack buffer.
   using LB = BlockLayout<1, true>;
-  using LM = BlockLayout<1, true, 512>;
+  using LM = BlockLayout<1, true, kMidCap>;
   const size_t smem_b = LB::bytes, smem_m = LM::bytes;
   MC_CUDA_TRY(cudaFuncSetAttribute(search_block_kernel<1, true, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem_b));
-  MC_CUDA_TRY(cudaFuncSetAttribute(search_block_kernel<1, true, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  MC_CUDA_TRY(cudaFuncSetAttribute(search_block_kernel<1, true, kMidCap>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem_m));
   MC_CUDA_TRY(cudaFuncSetAttribute(branch_task_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
   int per_sm_b = 0, per_sm_t = 0, per_sm_m = 0;
   MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, search_block_kernel<1, true, 1024>, kBT, smem_b));
   MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_t, branch_task_kernel, kBT, smem_b));
-  MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_m, search_block_kernel<1, true, 512>, kBT, smem_m));
+  MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_m, search_block_kernel<1, true, kMidCap>, kBT,
+                                                            smem_m));
   per_sm_b = std::min(per_sm_b, per_sm_t);
   if (per_sm_b < 1 || per_sm_m < 1) return MC_ERR_CUDA;
   const int blocks_b = g->sm_count * per_sm_b, blocks_m = g->sm_count * per_sm_m;
   const int64_t stride_b = (int64_t)(std::min(kbound, 1024) + 2) * (64 + 2);
-  const int64_t stride_m = (int64_t)(std::min(kbound, 512) + 2) * (64 + 2);
+  const int64_t stride_m = (int64_t)(std::min(kbound, kMidCap) + 2) * (64 + 2);
   uint32_t *stk_b = nullptr;
   if (kbound > wmax || !no_split) {
     MC_TRY(ws_get(g, "se.stk_b", (size_t)blocks_b * kBW * stride_b * 4, &p));
@@ -1441,7 +1443,7 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_spli
     a.roots = pg.roots_block;
     a.nroots = pg.d_counts + 4;
     a.next = next + 0;
-    if (kbound > 512) {
+    if (kbound > kMidCap) {
       MC_TRY(ws_get(g, "se.ovf", (size_t)std::max<int64_t>(g->n, 1) * 4, &p));
       a.overflow = (int32_t *)p;
       a.noverflow = (int64_t *)(ctr + 14);
@@ -1449,10 +1451,10 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_spli
     MC_TRY(ws_get(g, "se.stk_m", (size_t)blocks_m * kBW * stride_m * 4, &p));
     a.stack = (uint32_t *)p;
     a.stack_stride = stride_m;
-    search_block_kernel<1, true, 512><<<blocks_m, kBT, smem_m, g->stream>>>(a);
+    search_block_kernel<1, true, kMidCap><<<blocks_m, kBT, smem_m, g->stream>>>(a);
     g_launches++;
     MC_CUDA_TRY(cudaGetLastError());
-    if (kbound > 512) {
+    if (kbound > kMidCap) {
       a.roots = a.overflow;
       a.nroots = a.noverflow;
       a.next = next + 3;
