@@ -1386,20 +1386,26 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_spli
   const int kbound = std::max(g->max_core, 1);  // |P| <= |N+(u)| <= K(u) <= K(G)
   const int wmax = g->warp_max_used;
   if (!no_split) {
-    MC_TRY(ws_get(g, "se.arena", (size_t)kArenaWords * 4, &p));
+    // queue sizes grow with the graph (a small graph gets a small queue; a
+    // full queue only stops further spills)
+    const long long arena_words = std::min<long long>(kArenaWords, std::max<long long>(1ll << 18, 4 * g->nnz));
+    const int rec_cap = (int)std::min<int64_t>(kRecCap, std::max<int64_t>(1024, g->n));
+    int task_cap = 1 << 12;
+    while (task_cap < kTaskCap && (int64_t)task_cap < 4 * g->n) task_cap <<= 1;
+    MC_TRY(ws_get(g, "se.arena", (size_t)arena_words * 4, &p));
     a.arena = (uint32_t *)p;
-    a.arena_cap = kArenaWords;
+    a.arena_cap = arena_words;
     a.arena_used = ctr + 10;
-    MC_TRY(ws_get(g, "se.recs", (size_t)kRecCap * sizeof(RootRec), &p));
+    MC_TRY(ws_get(g, "se.recs", (size_t)rec_cap * sizeof(RootRec), &p));
     a.recs = (RootRec *)p;
-    a.rec_cap = kRecCap;
+    a.rec_cap = rec_cap;
     a.nrec = (int32_t *)(ctr + 11);
-    MC_TRY(ws_get(g, "se.tasks", (size_t)kTaskCap * kTaskWords * 4, &p));
+    MC_TRY(ws_get(g, "se.tasks", (size_t)task_cap * kTaskWords * 4, &p));
     a.tasks = (uint32_t *)p;
-    MC_TRY(ws_get(g, "se.ready", (size_t)kTaskCap * 4, &p));
+    MC_TRY(ws_get(g, "se.ready", (size_t)task_cap * 4, &p));
     a.ready = (int32_t *)p;
-    MC_CUDA_TRY(cudaMemsetAsync(a.ready, 0, (size_t)kTaskCap * 4, g->stream));
-    a.task_cap = kTaskCap;
+    MC_CUDA_TRY(cudaMemsetAsync(a.ready, 0, (size_t)task_cap * 4, g->stream));
+    a.task_cap = task_cap;
     a.ntasks = a.nrec + 1;
     a.task_next = a.nrec + 2;
     a.active = a.nrec + 3;
@@ -1426,7 +1432,11 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_spli
                                                             smem_m));
   per_sm_b = std::min(per_sm_b, per_sm_t);
   if (per_sm_b < 1 || per_sm_m < 1) return MC_ERR_CUDA;
-  const int blocks_b = g->sm_count * per_sm_b, blocks_m = g->sm_count * per_sm_m;
+  // grids (and the stacks sized by them) shrink for small graphs: a block
+  // per 64 vertices at most, a warp per four vertices in the warp class
+  const int64_t small_cap = std::max<int64_t>(1, (g->n + 63) / 64);
+  const int blocks_b = (int)std::min<int64_t>((int64_t)g->sm_count * per_sm_b, small_cap);
+  const int blocks_m = (int)std::min<int64_t>((int64_t)g->sm_count * per_sm_m, small_cap);
   const int64_t stride_b = (int64_t)(std::min(kbound, 1024) + 2) * (64 + 2);
   const int64_t stride_m = (int64_t)(std::min(kbound, kMidCap) + 2) * (64 + 2);
   uint32_t *stk_b = nullptr;
@@ -1495,7 +1505,8 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_spli
     int per_sm = 0;
     MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_warp_kernel, kSW * 32, 0));
     if (per_sm < 1) return MC_ERR_CUDA;
-    const int blocks = g->sm_count * per_sm;
+    const int blocks = (int)std::min<int64_t>((int64_t)g->sm_count * per_sm,
+                                              std::max<int64_t>(1, (g->n + 4 * kSW - 1) / (4 * kSW)));
     const int pmax = std::min(kbound, kWarpCap);
     a.stack_stride = (int64_t)(pmax + 2) * (64 + 2);
     MC_TRY(ws_get(g, "se.stk_w", (size_t)blocks * kSW * a.stack_stride * 4, &p));
@@ -1531,7 +1542,7 @@ int read_search_counters(mc_graph *g, SearchCounters *cnt) {
   cnt->donations = h[3];
   cnt->entries = h[4] + h[5];
   cnt->entries_block = h[5];
-  cnt->tasks = (unsigned long long)std::min(((const int32_t *)(h + 11))[1], kTaskCap);
+  cnt->tasks = (unsigned long long)((const int32_t *)(h + 11))[1];
   return MC_OK;
 }
 
