@@ -41,7 +41,10 @@ def load_peaks():
 # from the ncu capture summarised in profiles/search_block_kernel_rmat_s22.md
 # (dram__bytes_read.sum + dram__bytes_write.sum); set to None whenever the
 # kernel changes until it is captured again.
-SEARCH_BLOCK_TRAFFIC_S22 = None
+SEARCH_BLOCK_TRAFFIC_S22 = 150.4e6
+# ... and of heuristic_kernel (its warm-up and main launches of one solve),
+# from profiles/heuristic_kernel_rmat_s22.md; None until captured.
+HEURISTIC_TRAFFIC_S22 = None
 
 
 def roofline(stats, n, nnz, clk, dev):
@@ -99,7 +102,8 @@ def roofline(stats, n, nnz, clk, dev):
         note = "the CSR read once" + (" and the core numbers written" if dom == "kcore_peel_kernel" else "")
     achieved = alg / (ms / 1e3) / 1e9
     return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": achieved / hbm_peak, "traffic": None, "peak_source": hbm_src, "algorithmic_bytes": alg,
+            "frac": achieved / hbm_peak, "traffic": HEURISTIC_TRAFFIC_S22 if dom == "heuristic_kernel" else None,
+            "peak_source": hbm_src, "algorithmic_bytes": alg,
             "unit_note": note, "kernel_ms": ms, "_stages": kern}
 
 
