@@ -232,6 +232,230 @@ __device__ int grow(const HA &a, int v, int thr, int stop_at, int32_t *cand, int
   return size;
 }
 
+
+// Start vertex of visiting position i (false: position past its graph).
+__device__ __forceinline__ bool pick_vertex(const HA &a, int64_t i, int *v) {
+  if (a.list) {
+    *v = a.list[i];
+  } else if (i < a.nseeds) {
+    *v = a.seeds[i];
+  } else if (a.interleave) {
+    const int64_t r = i - a.nseeds, gi = r % a.count, j = r / a.count;
+    const int64_t v0 = a.voff[gi], v1 = a.voff[gi + 1];
+    if (j >= v1 - v0) return false;
+    *v = a.order[v1 - 1 - j];
+  } else {
+    *v = a.order[a.n - 1 - (i - a.nseeds)];
+  }
+  return true;
+}
+
+constexpr int kWT = 1024;      // threads of a warm-up block
+constexpr int kWW = kWT / 32;  // its warps
+
+// The greedy clique of grow() (same arguments, same result), grown by a whole
+// block: the candidate list is split into one contiguous slice per warp, each
+// warp filters its slice (binary search, or a merge that starts at the
+// slice's first candidate) into its part of the second buffer, and the kept
+// candidates are packed back in order.  For the warm-up, where the first
+// start vertices have every neighbour as a candidate.
+__device__ int grow_block(const HA &a, int v, int thr, int stop_at, int32_t *cur, int32_t *nxt, int32_t *cl,
+                          bool by_score, int g) {
+  __shared__ int s_cnt[kWW];
+  __shared__ Key s_key[kWW];
+  __shared__ int s_best;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const Key none{INT_MIN, INT_MIN, INT_MAX};
+  // candidates: neighbours of v with core >= thr, in row order
+  const int64_t e0 = a.rp[v], e1 = a.rp[v + 1];
+  const int64_t per = (((e1 - e0) + kWW - 1) / kWW + 31) & ~(int64_t)31;
+  const int64_t sb = min(e1, e0 + wid * per), se = min(e1, sb + per);
+  int c = 0;
+  Key bk = none;
+  for (int64_t eb = sb; eb < se; eb += 32) {
+    const int64_t e = eb + lane;
+    int u = -1;
+    bool ok = false;
+    if (e < se) {
+      u = a.ci[e];
+      ok = a.core[u] >= thr;
+    }
+    const unsigned m = __ballot_sync(FULL, ok);
+    if (ok) {
+      nxt[(sb - e0) + c + __popc(m & lt)] = u;
+      const Key k = by_score ? key_of_scored(a, u) : key_of(a, u);
+      if (better(k, bk)) bk = k;
+    }
+    c += __popc(m);
+  }
+  bk = warp_best(bk);
+  if (lane == 0) {
+    s_cnt[wid] = c;
+    s_key[wid] = bk;
+    atomicAdd(a.ctr + 2, (unsigned long long)(se - sb));
+  }
+  __syncthreads();
+  int off = 0, cnt = 0;
+  Key best = none;
+  for (int w = 0; w < kWW; w++) {
+    if (w < wid) off += s_cnt[w];
+    cnt += s_cnt[w];
+    if (better(s_key[w], best)) best = s_key[w];
+  }
+  for (int j = lane; j < c; j += 32) cur[off + j] = nxt[(sb - e0) + j];
+  if (tid == 0) {
+    atomicAdd(a.ctr + 0, 1ull);
+    cl[0] = v;
+  }
+  __syncthreads();
+  int size = 1;
+  for (;;) {
+    if (tid == 0)
+      s_best = a.mode == 0 ? *(volatile int32_t *)(a.best + g)
+                           : (int)(*(volatile unsigned long long *)(a.detkey + g) >> 32);
+    __syncthreads();
+    const int cb = s_best;
+    if (a.mode == 0) {
+      thr = max(thr, cb);
+      stop_at = max(stop_at, cb + 1);
+    } else {
+      stop_at = max(stop_at, cb);
+    }
+    if (cnt == 0 || size + cnt < stop_at) break;
+    const int w = best.id;
+    if (tid == 0) {
+      cl[size] = w;
+      atomicAdd(a.ctr + 1, (unsigned long long)cnt);
+    }
+    size++;
+    const int64_t r0 = a.rp[w], r1 = a.rp[w + 1];
+    const int per2 = ((cnt + kWW - 1) / kWW + 31) & ~31;
+    const int b0 = min(cnt, wid * per2), b1 = min(cnt, b0 + per2);
+    const bool merge = (int64_t)(b1 - b0) * 16 >= (r1 - r0);
+    int64_t pos = r0;
+    if (merge && b0 < b1) {
+      // first row entry not below the slice's first candidate
+      const int x0 = cur[b0];
+      int64_t lo = r0, hi = r1;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (a.ci[mid] < x0) lo = mid + 1; else hi = mid;
+      }
+      pos = lo;
+      if (lane == 0) atomicAdd(a.ctr + 2, (unsigned long long)(r1 - pos));
+    }
+    int kept = 0;
+    Key nb = none;
+    for (int base = b0; base < b1; base += 32) {
+      const int i = base + lane;
+      const int x = (i < b1) ? cur[i] : INT_MAX;
+      bool keep = false;
+      if (!merge) {
+        keep = i < b1 && x != w && in_row(a, w, x);
+      } else {
+        const int last = min(31, b1 - 1 - base);
+        const int xmin = __shfl_sync(FULL, x, 0), xmax = __shfl_sync(FULL, x, last);
+        while (pos < r1) {
+          const int64_t e = min(pos + 31, r1 - 1);
+          if (a.ci[e] >= xmin) break;
+          pos = e + 1;
+        }
+        int64_t wp = pos;
+        while (wp < r1) {
+          const int y = (wp + lane < r1) ? a.ci[wp + lane] : INT_MAX;
+          int l = -1;
+#pragma unroll
+          for (int st = 32; st >= 1; st >>= 1) {
+            const int t = l + st;
+            const int yt = __shfl_sync(FULL, y, t & 31);
+            if (t < 32 && yt <= x) l = t;
+          }
+          const int yl = __shfl_sync(FULL, y, l & 31);
+          if (l >= 0 && yl == x) keep = true;
+          const int ymax = __shfl_sync(FULL, y, 31);
+          if (ymax >= xmax) break;
+          wp += 32;
+        }
+        pos = wp;
+        keep = keep && i < b1 && x != w;
+      }
+      if (keep && thr > 0) keep = a.core[x] >= thr;
+      const unsigned m = __ballot_sync(FULL, keep);
+      if (keep) {
+        nxt[b0 + kept + __popc(m & lt)] = x;
+        const Key k = by_score ? key_of_scored(a, x) : key_of(a, x);
+        if (better(k, nb)) nb = k;
+      }
+      kept += __popc(m);
+    }
+    nb = warp_best(nb);
+    __syncthreads();  // every warp has read its slice of cur
+    if (lane == 0) {
+      s_cnt[wid] = kept;
+      s_key[wid] = nb;
+    }
+    __syncthreads();
+    int off2 = 0, tot = 0;
+    Key nbest = none;
+    for (int ww = 0; ww < kWW; ww++) {
+      if (ww < wid) off2 += s_cnt[ww];
+      tot += s_cnt[ww];
+      if (better(s_key[ww], nbest)) nbest = s_key[ww];
+    }
+    for (int j = lane; j < kept; j += 32) cur[off2 + j] = nxt[b0 + j];
+    __syncthreads();
+    cnt = tot;
+    best = nbest;
+  }
+  __syncthreads();
+  return size;
+}
+
+// Warm-up launch: one block per start vertex (the first positions of the
+// visiting order), so the maximum is high before the warp-per-vertex launch.
+__global__ void __launch_bounds__(kWT) heuristic_warm_kernel(HA a) {
+  __shared__ int64_t s_i;
+  __shared__ int s_x;
+  int32_t *cur = a.cand + (int64_t)blockIdx.x * 2 * a.cand_stride;
+  int32_t *nxt = cur + a.cand_stride;
+  int32_t *cl = a.cl + (int64_t)blockIdx.x * a.cl_stride;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_i = *(volatile int32_t *)a.err ? a.limit : a.begin + atomicAdd(a.next, 1);
+    __syncthreads();
+    const int64_t i = s_i;
+    if (i >= a.limit) break;
+    int v = 0;
+    if (!pick_vertex(a, i, &v)) continue;
+    const int g = a.gid ? a.gid[v] : 0;
+    const int kv = a.core[v];
+    const bool seeded = i < a.nseeds && a.score;
+    __syncthreads();
+    if (a.mode == 0) {
+      if (threadIdx.x == 0) s_x = *(volatile int32_t *)(a.best + g);
+      __syncthreads();
+      const int mx = s_x;
+      if (kv < mx) continue;
+      const int size = grow_block(a, v, mx, mx + 1, cur, nxt, cl, seeded, g);
+      if (size > mx && threadIdx.x < 32) {
+        dev::raise_incumbent(a.best, a.lock, a.wit, a.voff, g, size, a.err, a.spin, [&](int ln, int32_t *base) {
+          for (int t = ln; t < size; t += 32) base[t] = cl[t];
+        });
+      }
+    } else {
+      if (threadIdx.x == 0) s_x = (int)(*(volatile unsigned long long *)(a.detkey + g) >> 32);
+      __syncthreads();
+      const int bsz = s_x;
+      if (kv + 1 < bsz) continue;
+      const int size = grow_block(a, v, 0, bsz, cur, nxt, cl, seeded, g);
+      const unsigned long long key = ((unsigned long long)size << 32) | ((seeded ? 1ull : 0ull) << 31) |
+                                     (unsigned)(0x7fffffff - v);
+      if (threadIdx.x == 0) atomicMax(a.detkey + g, key);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kHT) heuristic_kernel(HA a) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -243,19 +467,8 @@ __global__ void __launch_bounds__(kHT) heuristic_kernel(HA a) {
     if (lane == 0) i = *(volatile int32_t *)a.err ? total : a.begin + atomicAdd(a.next, 1);
     i = __shfl_sync(FULL, (long long)i, 0);
     if (i >= total) break;
-    int v;
-    if (a.list) {
-      v = a.list[i];
-    } else if (i < a.nseeds) {
-      v = a.seeds[i];
-    } else if (a.interleave) {
-      const int64_t r = i - a.nseeds, gi = r % a.count, j = r / a.count;
-      const int64_t v0 = a.voff[gi], v1 = a.voff[gi + 1];
-      if (j >= v1 - v0) continue;
-      v = a.order[v1 - 1 - j];
-    } else {
-      v = a.order[a.n - 1 - (i - a.nseeds)];
-    }
+    int v = 0;
+    if (!pick_vertex(a, i, &v)) continue;
     const int g = a.gid ? a.gid[v] : 0;
     const int kv = a.core[v];
     if (a.mode == 0) {
@@ -340,10 +553,14 @@ int launch_heuristic(mc_graph *g, int mode, long long spin_limit, const int32_t 
   warps_s = (warps_s + 7) / 8 * 8;
   int64_t warps_b = std::max<int64_t>(32, std::min<int64_t>((int64_t)g->sm_count * 16, budget / full));
   warps_b = (warps_b + 7) / 8 * 8;
-  const int64_t cand_entries = std::max(warps_s * cap_s, two || mode == 1 ? warps_b * full : 0);
+  // warm-up blocks hold two full-degree candidate buffers each
+  const int64_t warm_blocks =
+      std::max<int64_t>(1, std::min<int64_t>({(int64_t)g->sm_count, kWarm, budget / (2 * full)}));
+  const int64_t cand_entries =
+      std::max({warps_s * cap_s, warm_blocks * 2 * full, two || mode == 1 ? warps_b * full : (int64_t)0});
   MC_TRY(ws_get(g, "he.cand", (size_t)cand_entries * 4, &p));
   int32_t *cand = (int32_t *)p;
-  MC_TRY(ws_get(g, "he.cl", (size_t)std::max(warps_s, warps_b) * lstride * 4, &p));
+  MC_TRY(ws_get(g, "he.cl", (size_t)std::max({warps_s, warps_b, warm_blocks}) * lstride * 4, &p));
   int32_t *cl = (int32_t *)p;
   MC_TRY(ws_get(g, "he.ctl", 64 + (size_t)g->count * 8, &p));
   int32_t *next = (int32_t *)p;  // [0] warm-up, [2] main launch, [1] deferred launch; [4..5] deferred count
@@ -389,14 +606,16 @@ int launch_heuristic(mc_graph *g, int mode, long long spin_limit, const int32_t 
   a.interleave = (g->count > 1 && g->max_graph_n <= kBatchPeelCap) ? 1 : 0;
   const int64_t total = a.interleave ? (int64_t)g->count * g->max_graph_n + a.nseeds : g->n + a.nseeds;
   // A warm-up launch grows the first kWarm start vertices (the seeds and the
-  // largest core numbers) with kWarm warps, so the shared maximum is already
-  // high when the other warps start and prunes their candidate sets.
+  // largest core numbers), each with a whole block, so the shared maximum is
+  // already high when the warps start and prunes their candidate sets.
   const int64_t warm = std::min<int64_t>(total, kWarm);
   a.begin = 0;
   a.limit = warm;
-  heuristic_kernel<<<(int)((std::min<int64_t>(warps_s, kWarm) * 32 + kHT - 1) / kHT), kHT, 0, g->stream>>>(a);
+  a.cand_stride = full;
+  heuristic_warm_kernel<<<(int)warm_blocks, kWT, 0, g->stream>>>(a);
   g_launches++;
   MC_CUDA_TRY(cudaGetLastError());
+  a.cand_stride = cap_s;
   if (warm < total) {
     a.begin = warm;
     a.limit = total;
