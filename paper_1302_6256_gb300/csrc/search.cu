@@ -1186,8 +1186,9 @@ __global__ void __launch_bounds__(kBT, (SM && PC <= kMidCap) ? 2 : 1) search_blo
 // ends when the queue is empty and no block holds a task (a block counts
 // itself in `active` before it looks for a task and leaves it only after
 // its spilled tasks are visible).
-__global__ void __launch_bounds__(kBT) branch_task_kernel(SA a) {
-  using L = BlockLayout<1, true>;
+template <int PC>
+__global__ void __launch_bounds__(kBT, (PC <= kMidCap) ? 2 : 1) branch_task_kernel(SA a) {
+  using L = BlockLayout<1, true, PC>;  // PC >= every record's p
   extern __shared__ __align__(16) unsigned char smem[];
   int *Pidx = (int *)(smem + L::off_P);
   Pool<1> *pool = (Pool<1> *)(smem + L::off_pool);
@@ -1424,24 +1425,32 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_spli
                                    (int)smem_b));
   MC_CUDA_TRY(cudaFuncSetAttribute(search_block_kernel<1, true, kMidCap>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem_m));
-  MC_CUDA_TRY(cudaFuncSetAttribute(branch_task_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
-  int per_sm_b = 0, per_sm_t = 0, per_sm_m = 0;
+  MC_CUDA_TRY(cudaFuncSetAttribute(branch_task_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
+  MC_CUDA_TRY(cudaFuncSetAttribute(branch_task_kernel<kMidCap>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem_m));
+  int per_sm_b = 0, per_sm_t = 0, per_sm_m = 0, per_sm_tm = 0;
   MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, search_block_kernel<1, true, 1024>, kBT, smem_b));
-  MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_t, branch_task_kernel, kBT, smem_b));
+  MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_t, branch_task_kernel<1024>, kBT, smem_b));
+  MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_tm, branch_task_kernel<kMidCap>, kBT, smem_m));
   MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_m, search_block_kernel<1, true, kMidCap>, kBT,
                                                             smem_m));
   per_sm_b = std::min(per_sm_b, per_sm_t);
-  if (per_sm_b < 1 || per_sm_m < 1) return MC_ERR_CUDA;
+  if (per_sm_b < 1 || per_sm_m < 1 || per_sm_tm < 1) return MC_ERR_CUDA;
   // grids (and the stacks sized by them) shrink for small graphs: a block
   // per 64 vertices at most, a warp per four vertices in the warp class
   const int64_t small_cap = std::max<int64_t>(1, (g->n + 63) / 64);
   const int blocks_b = (int)std::min<int64_t>((int64_t)g->sm_count * per_sm_b, small_cap);
   const int blocks_m = (int)std::min<int64_t>((int64_t)g->sm_count * per_sm_m, small_cap);
+  // the task kernel takes the mid layout (two blocks per SM) when no record
+  // can hold more than kMidCap candidates (p <= K(G))
+  const bool task_mid = kbound <= kMidCap;
+  const int blocks_t =
+      task_mid ? (int)std::min<int64_t>((int64_t)g->sm_count * per_sm_tm, small_cap) : blocks_b;
   const int64_t stride_b = (int64_t)(std::min(kbound, 1024) + 2) * (64 + 2);
   const int64_t stride_m = (int64_t)(std::min(kbound, kMidCap) + 2) * (64 + 2);
   uint32_t *stk_b = nullptr;
   if (kbound > wmax || !no_split) {
-    MC_TRY(ws_get(g, "se.stk_b", (size_t)blocks_b * kBW * stride_b * 4, &p));
+    MC_TRY(ws_get(g, "se.stk_b", (size_t)std::max(blocks_b, blocks_t) * kBW * stride_b * 4, &p));
     stk_b = (uint32_t *)p;
   }
 
@@ -1522,8 +1531,11 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_spli
   if (!no_split) {
     a.stack_stride = stride_b;
     a.stack = stk_b;
-    a.queue_gate = 2 * blocks_b;
-    branch_task_kernel<<<blocks_b, kBT, smem_b, g->stream>>>(a);
+    a.queue_gate = 2 * blocks_t;
+    if (task_mid)
+      branch_task_kernel<kMidCap><<<blocks_t, kBT, smem_m, g->stream>>>(a);
+    else
+      branch_task_kernel<1024><<<blocks_t, kBT, smem_b, g->stream>>>(a);
     g_launches++;
     MC_CUDA_TRY(cudaGetLastError());
   }
