@@ -1,4 +1,4 @@
-// Heuristic clique (Algorithm 1, Section 4.1), one warp per start vertex.
+// Heuristic clique (Algorithm 1, Section 4.1), one warp (or block) per start vertex.
 //
 // Vertices are visited in decreasing core number (the peel order reversed).
 // For a start vertex v the warp gathers S = neighbours with K >= threshold
@@ -22,7 +22,15 @@
 //   mode 1 they only add candidates, so the bound can only rise.
 // Start vertices that cannot reach the current best (K(v) + 1 below it) are
 // skipped, and a greedy run stops once C plus all remaining candidates cannot
-// beat the best; neither changes the result of either mode.
+// beat the best (re-read at every step); neither changes the result of either
+// mode.
+//
+// Launches: a warm-up launch grows the first 256 start vertices (the seeds
+// and the largest core numbers, whose candidate sets are whole neighbourhoods
+// before any clique is known) with one block each; the main launch runs 32
+// warps per SM with candidate buffers sharing 2 GiB; start vertices with more
+// candidates than a buffer holds go to a last launch with full-degree
+// buffers.  Every growth, by a block or a warp, yields the same clique.
 #include <algorithm>
 #include <climits>
 

@@ -7,7 +7,10 @@
 // and the search looks for a clique larger than omega containing u:
 //   1. |P| < omega                    -> return (degree bound, Fact 2 (3))
 //   2. bitset adjacency of G[P]       (the small-graph adjacency matrix of
-//      Section 4.4, built from the later-neighbour rows of P's members)
+//      Section 4.4): each member's later-neighbour row is probed against a
+//      hash table of P, which sets the lower triangle (a later neighbour has
+//      a smaller index in P); warp-ballot transposes of 32 x 32 tiles fill
+//      the upper triangle
 //   3. (omega-1)-core of G[P]: exactly the vertices with neighbourhood core
 //      number K_N >= |H| when u is counted (lines 15-18 of InitialBranch;
 //      the tight form of the test); fewer than omega left -> return
@@ -22,11 +25,18 @@
 //
 // Workers, split by the out-degree of the root (an upper bound on |P|):
 //   warp class   |N+(u)| <= 128: one warp per root, matrix in shared memory;
-//   block class  |N+(u)| <= 1024: one block per root, matrix (<= 128 KB) in
-//                shared memory, the block's 16 warps share the root's search
-//                tree through a shared-memory task pool (a busy warp hands the
-//                shallowest untried branch to an idle one);
+//   block class  |N+(u)| <= 1024: one block per root, matrix in shared
+//                memory; a 512-candidate layout at two blocks per SM first,
+//                then a 1,024-candidate launch for the roots it deferred; the
+//                block's 16 warps share the root's search tree through a
+//                shared-memory pool (a busy warp hands the shallowest untried
+//                branch to an idle one);
 //   big class    larger: as the block class with the matrix in global memory.
+// Task queue: a warp (block) that expands more than its budget of Branch
+// nodes on one root copies the root's matrix to an arena and turns every
+// untried branch of its stack into a task in a GPU-wide ring; the task
+// kernel searches tasks with whole blocks and spills again while the queue
+// is short, so one hard neighbourhood spreads over the whole GPU.
 // Every spin-wait is bounded; on timeout the device error word is set.
 #include <algorithm>
 #include <climits>
