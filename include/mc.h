@@ -86,12 +86,16 @@ typedef struct {
   int32_t seeds;
   /* 1 = run the whole solve as one CUDA graph: the first call with these
    * options solves directly (sizing every buffer), then captures the solve;
-   * later calls replay it with one graph launch.  0 = direct launches. */
+   * later calls replay it with one graph launch.  Host-resident scores are
+   * copied to the device before every replay, so a replay sees their
+   * current values.  0 = direct launches. */
   int32_t graph;
-  /* 1 = search each block-worker neighbourhood inside the block that built
-   * it; 0 = (default) a neighbourhood that reaches Branch publishes its
-   * adjacency matrix and its first-level branches as tasks that every block
-   * takes from one queue, so one hard neighbourhood spreads over the GPU */
+  /* 1 = every worker searches its root's whole tree itself (the warps of a
+   * block worker still share it through the block's pool); 0 = (default) a
+   * worker that expands more than its budget of Branch nodes on one root
+   * copies the root's adjacency matrix to a device arena and turns the
+   * untried branches of its stack into tasks of one GPU-wide queue, which
+   * every block serves, so one hard neighbourhood spreads over the GPU */
   int32_t no_split;
   /* Branch nodes a warp worker expands on one root before it spills the
    * rest of its tree to the task queue (a block worker: four times as
@@ -193,9 +197,8 @@ int mc_verify_clique(mc_graph *g, const int32_t *vertices, int32_t k, int32_t *i
 
 /* Core numbers, like mc_core_numbers, for callers that cannot allocate
  * device memory.  The paper has no counterpart: this exists for code that
- * must not call cudaMalloc -- for example while a CUDA graph is being
- * captured in a mode that forbids allocation, inside an allocator hook, or
- * under a host that owns every byte of device memory it gives the library.
+ * must not call cudaMalloc -- for example inside an allocator hook, or under
+ * a host that owns every byte of device memory it gives the library.
  * Nothing is allocated: the peel's working memory is one fixed device array
  * of about 33 MB inside the library, which every GPU that loads the library
  * holds until the process exits.
@@ -206,11 +209,11 @@ int mc_verify_clique(mc_graph *g, const int32_t *vertices, int32_t k, int32_t *i
  *   int32 or NULL, receives K(G).  cuda_stream: the stream to run on.
  * Larger inputs are rejected with MC_ERR_TOO_LARGE before anything runs.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  The call synchronises its stream before it
- * returns.  All calls share the one array, so calls that overlap on the GPU
- * (other host threads, other streams) race and must be serialised by the
- * caller. */
+ * (cudaGetSymbolAddress) with that device current.  The call synchronises
+ * its stream before it returns (it reads K(G) and the device error word), so
+ * it cannot be recorded into a CUDA graph.  All calls share the one array,
+ * so calls that overlap on the GPU (other host threads, other streams) race
+ * and must be serialised by the caller. */
 int mc_core_numbers_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, int32_t *core_out,
                             int32_t *max_core_out, void *cuda_stream);
 

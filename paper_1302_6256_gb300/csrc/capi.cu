@@ -317,8 +317,11 @@ static int enqueue_solve(mc_graph *g, const mc_options &o, Pruned *pg, SearchCou
     if (is_device_ptr(o.scores)) {
       d_scores = o.scores;
     } else {
+      // host scores: copied here, or, inside capture (a graph cannot copy
+      // from pageable memory), before every replay by stage_host_scores
       MC_TRY(ws_get(g, "cp.scores", g->n * sizeof(float), &p));
-      MC_CUDA_TRY(cudaMemcpyAsync(p, o.scores, g->n * sizeof(float), cudaMemcpyHostToDevice, g->stream));
+      if (!g->capturing)
+        MC_CUDA_TRY(cudaMemcpyAsync(p, o.scores, g->n * sizeof(float), cudaMemcpyHostToDevice, g->stream));
       d_scores = (const float *)p;
     }
     if (o.seeds > 0) {
@@ -402,6 +405,15 @@ static int finish_solve(mc_graph *g, Pruned *pg, SearchCounters *sc, const int32
   return MC_OK;
 }
 
+// Host-resident scores into the device buffer that a captured solve reads.
+static int stage_host_scores(mc_graph *g, const mc_options &o) {
+  if (!o.scores || g->n == 0 || is_device_ptr(o.scores)) return MC_OK;
+  void *p;
+  MC_TRY(ws_get(g, "cp.scores", g->n * sizeof(float), &p));
+  MC_CUDA_TRY(cudaMemcpyAsync(p, o.scores, g->n * sizeof(float), cudaMemcpyHostToDevice, g->stream));
+  return MC_OK;
+}
+
 static uint64_t options_key(const mc_options &o) {
   uint64_t k = 1469598103934665603ULL;
   auto mix = [&](uint64_t x) { k = (k ^ x) * 1099511628211ULL; };
@@ -466,6 +478,7 @@ static int run_max_clique(mc_graph *g, const mc_options *opt, mc_stats *st) {
     g->graph_ok = d_ok;
   }
   // one launch of the captured solve, ordered after the caller's stream
+  MC_TRY(stage_host_scores(g, o));
   MC_CUDA_TRY(cudaEventRecord(g->ev[6], g->stream));
   MC_CUDA_TRY(cudaStreamWaitEvent(g->cap_stream, g->ev[6], 0));
   MC_CUDA_TRY(cudaGraphLaunch(g->graph_exec, g->cap_stream));

@@ -489,10 +489,9 @@ int launch_core_numbers(mc_graph *g, long long spin_limit) {
 // ------------------------------------------------------------------------
 // Core numbers without any device allocation.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA graph is
-// being captured with a capture mode that forbids allocation, allocator
-// hooks that must not re-enter the allocator, or hosts that hand the library
-// a fixed memory budget and own every byte of it.  For them this entry point
+// Some callers cannot call cudaMalloc: allocator hooks that must not
+// re-enter the allocator, or hosts that hand the library a fixed memory
+// budget and own every byte of it.  For them this entry point
 // runs the same peel with its working memory in a file-scope device array of
 // fixed size, reserved when the library is loaded and held by every GPU that
 // loads it until the process exits.
