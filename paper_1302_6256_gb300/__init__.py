@@ -233,8 +233,24 @@ def mc_heuristic_clique(g: Graph, mode: int = 0, core=None):
     return out[:size.value].copy()
 
 
-def _options(ordering=0, no_neigh_cores=False, heuristic=0, warp_max=0, spin_limit=0, scores=None, seeds=0,
+def _scores_arg(scores, n):
+    """Learned scores as one float32 per vertex: numpy input is converted,
+    a torch tensor must already be float32; the length must be n."""
+    if scores is None:
+        return None
+    if hasattr(scores, "data_ptr"):
+        if str(scores.dtype) != "torch.float32":
+            raise TypeError("scores must be a float32 tensor, got %s" % scores.dtype)
+    else:
+        scores = np.ascontiguousarray(scores, dtype=np.float32)
+    if scores.ndim != 1 or int(scores.shape[0]) != n:
+        raise ValueError("scores must hold one value per vertex (%d), got shape %s" % (n, tuple(scores.shape)))
+    return scores
+
+
+def _options(n, ordering=0, no_neigh_cores=False, heuristic=0, warp_max=0, spin_limit=0, scores=None, seeds=0,
              graph=False, no_split=False, split_nodes=0):
+    scores = _scores_arg(scores, n)
     o = Options()
     o.split_nodes = split_nodes
     o.graph = 1 if graph else 0
@@ -254,7 +270,7 @@ def mc_max_clique(g: Graph, witness_out=None, **opts):
     """Returns (omega, witness, stats dict).  witness_out: optional int32
     buffer (host or device) of at least omega entries."""
     L = load_library()
-    o, keep = _options(**opts)
+    o, keep = _options(g.n, **opts)
     st = Stats()
     om = ctypes.c_int32(0)
     if witness_out is None:
@@ -268,7 +284,7 @@ def mc_max_clique(g: Graph, witness_out=None, **opts):
 def mc_max_clique_batch(g: Graph, **opts):
     """Returns (omegas[count], list of witnesses, stats dict)."""
     L = load_library()
-    o, keep = _options(**opts)
+    o, keep = _options(g.n, **opts)
     st = Stats()
     om = np.zeros(g.count, np.int32)
     offs = np.zeros(g.count + 1, np.int64)
@@ -371,7 +387,7 @@ def mc_autotune(g: Graph, repeats: int = 2, **opts):
     """Fastest (warp_max, no_split, split_nodes, graph) setting for this
     graph; returns (options dict, ms)."""
     L = load_library()
-    base, keep = _options(**opts)
+    base, keep = _options(g.n, **opts)
     best = Options()
     ms = ctypes.c_double(0)
     _check(L.mc_autotune(g.handle, ctypes.byref(base), repeats, ctypes.byref(best), ctypes.byref(ms)), "mc_autotune")

@@ -189,13 +189,21 @@ struct NativeG {
   }
 };
 
-// score keys of the pruned vertices; slots past the pruned count sort last
+// Sort keys of the pruned vertices: each score's bits mapped to an unsigned
+// integer of the same order (positives: sign bit set; negatives: all bits
+// flipped), then raised to at least 1, so that every score -- -inf and NaN
+// included -- sorts before the slots past the pruned count, which get 0.
 __global__ void gather_scores_kernel(int64_t n, const int64_t *__restrict__ d_np, const int32_t *__restrict__ oold,
-                                     const float *__restrict__ score, float *__restrict__ key,
+                                     const float *__restrict__ score, uint32_t *__restrict__ key,
                                      int32_t *__restrict__ idx) {
   const int64_t np = *d_np;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-    key[j] = j < np ? score[oold[j]] : -3.0e38f;
+    uint32_t k = 0u;
+    if (j < np) {
+      const uint32_t b = __float_as_uint(score[oold[j]]);
+      k = max((b & 0x80000000u) ? ~b : (b | 0x80000000u), 1u);
+    }
+    key[j] = k;
     idx[j] = (int32_t)j;
   }
 }
@@ -269,8 +277,8 @@ int launch_prune(mc_graph *g, int ordering, const float *scores, int32_t warp_ma
     MC_TRY(device_scan(g, n, NativeF{nid}, NativeG{nid, tab}, nullptr, "pr.scan"));
   } else if (ordering == 1) {
     if (!scores) return MC_ERR_ARG;
-    MC_TRY(ws_get(g, "pr.skey", (2 * n + 2) * sizeof(float), &p));
-    float *skey = (float *)p;
+    MC_TRY(ws_get(g, "pr.skey", (2 * n + 2) * sizeof(uint32_t), &p));
+    uint32_t *skey = (uint32_t *)p;
     MC_TRY(ws_get(g, "pr.sidx", (n + 1) * sizeof(int32_t), &p));
     int32_t *sidx = (int32_t *)p;
     gather_scores_kernel<<<blocks, 256, 0, g->stream>>>(n, dsm + 0, oold, scores, skey, sidx);

@@ -50,3 +50,24 @@ def test_no_cpu_fallback_in_product_package():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "orc_" not in src, f
+
+
+def test_options_marshal_learned_scores():
+    """Learned scores reach the library as one float32 per vertex: numpy
+    input of another dtype is converted, a wrong length is refused before
+    any call (the C side cannot see the array's length)."""
+    import numpy as np
+    import paper_1302_6256_gb300 as mc
+    o, keep = mc._options(4, ordering=1, scores=np.arange(4, dtype=np.float64), seeds=2, graph=True)
+    assert keep.dtype == np.float32 and o.scores == keep.ctypes.data
+    assert o.ordering == 1 and o.seeds == 2 and o.graph == 1
+    f32 = np.zeros(4, np.float32)
+    o, keep = mc._options(4, ordering=1, scores=f32)
+    assert o.scores == f32.ctypes.data  # no copy: graph replay sees later writes
+    with pytest.raises(ValueError):
+        mc._options(5, ordering=1, scores=f32)
+    torch = pytest.importorskip("torch")
+    with pytest.raises(TypeError):
+        mc._options(4, ordering=1, scores=torch.zeros(4, dtype=torch.float64))
+    o, keep = mc._options(4, ordering=1, scores=torch.zeros(4, dtype=torch.float32))
+    assert o.scores == keep.data_ptr()

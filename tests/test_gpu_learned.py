@@ -78,6 +78,60 @@ def test_learned_ordering_keeps_omega_exact(mc, kind):
         assert oracle.is_clique(g, wit)
 
 
+def _bits(u):
+    return np.array([u], dtype=np.uint32).view(np.float32)[0]
+
+
+def _dense_core_and_path(tail=3000):
+    """Erdos-Renyi G(300, 1/2) (omega 12, Algorithm 1's clique 11: the
+    search must find the maximum clique) beside a path of `tail` vertices
+    (core number 1: pruned, so most vertices are gone before the roots are
+    ordered)."""
+    d = gg.erdos_renyi(300, 0.5, planted=0, seed=1)
+    src = np.repeat(np.arange(d.n, dtype=np.int64), np.diff(d.row_ptr))
+    keep = src < d.col_idx
+    p = np.arange(d.n, d.n + tail - 1)
+    return gg.from_edges(d.n + tail, np.concatenate([src[keep], p]), np.concatenate([d.col_idx[keep], p + 1]))
+
+
+def test_learned_ordering_accepts_any_float_score(mc):
+    """Scores of -inf, +inf, NaN of either sign and the most negative finite
+    float order the roots like any other value, so no root is lost: on a
+    graph where the heuristic stops one short of omega and most vertices
+    are pruned, omega is still found."""
+    g = _dense_core_and_path()
+    om_ref = oracle.max_clique(g)[0]
+    assert len(oracle.heuristic_clique(g, mode=1)) < om_ref
+    s = np.random.default_rng(1).standard_normal(g.n).astype(np.float32)
+    s[::3] = -np.inf
+    s[1::5] = _bits(0x7FC00000)   # NaN
+    s[2::7] = _bits(0xFFC00000)   # NaN, sign bit set
+    s[5::9] = _bits(0xFFFFFFFF)   # NaN, every bit set
+    s[3::11] = np.inf
+    s[4::13] = np.finfo(np.float32).min
+    h = mc.mc_load_csr(g.row_ptr, g.col_idx)
+    for sc in (s, np.full(g.n, -np.inf, dtype=np.float32), np.full(g.n, _bits(0xFFFFFFFF), dtype=np.float32)):
+        om, wit, st = mc.mc_max_clique(h, heuristic=1, ordering=1, scores=sc)
+        assert st["heuristic_size"] < om_ref and st["pruned_n"] == 300
+        assert om == om_ref and oracle.is_clique(g, wit) and len(wit) == om
+    h.close()
+
+
+def test_graph_replay_with_host_scores(mc):
+    """A captured solve with learned scores in host memory: every replay
+    copies the array's current contents, and omega stays exact."""
+    g = gg.rmat(14, 16, planted=30, seed=16)
+    om_ref = oracle.max_clique(g)[0]
+    rng = np.random.default_rng(3)
+    s = rng.random(g.n).astype(np.float32)
+    h = mc.mc_load_csr(g.row_ptr, g.col_idx)
+    for _ in range(3):
+        s[:] = rng.random(g.n)
+        om, wit, st = mc.mc_max_clique(h, ordering=1, scores=s, seeds=16, graph=True)
+        assert om == om_ref and oracle.is_clique(g, wit) and len(wit) == om
+    h.close()
+
+
 def test_trained_network_raises_the_lower_bound(mc):
     """What the committed network (trained on 2,000 generated Chung-Lu and
     R-MAT graphs, seed 7) gains over the method without it, on 60 held-out

@@ -1,6 +1,5 @@
 """mc_core_numbers_noalloc: core numbers for callers that cannot allocate
-device memory (graph capture that forbids allocation, allocator hooks, hosts
-that own the whole device budget).  It must give exactly what
+device memory (allocator hooks, hosts that own the whole device budget).  It must give exactly what
 mc_core_numbers gives, call after call, although every call reuses the same
 fixed device array.  This file is collected last on purpose."""
 import ctypes
