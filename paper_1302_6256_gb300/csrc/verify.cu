@@ -81,7 +81,12 @@ __global__ void validate_kernel(int64_t n, int64_t nnz, const int64_t *rp, const
       int u = ci[e];
       if (u < lo || u >= hi || u == v) ok = false;
       else if (e > e0 && ci[e - 1] >= u) ok = false;
-      else if (!adjacent(rp, ci, u, (int)v)) ok = false;
+      else {
+        // row u is searched only inside [0, nnz): a broken row_ptr is
+        // reported (by u's own warp) instead of read out of bounds
+        const int64_t u0 = rp[u], u1 = rp[u + 1];
+        if (u0 < 0 || u1 < u0 || u1 > nnz || !adjacent(rp, ci, u, (int)v)) ok = false;
+      }
     }
     if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicExch(bad, 1);
   }
@@ -96,6 +101,10 @@ __global__ void gid_kernel(int32_t count, const int64_t *voff, int32_t *gid) {
 __global__ void verify_one_kernel(int64_t n, const int64_t *rp, const int32_t *ci, const int32_t *best,
                                   const int32_t *wit, int32_t *ok) {
   const int k = best[0];
+  if (k < 0 || k > n) {
+    *ok = 0;
+    return;
+  }
   const int64_t pairs = (int64_t)k * k;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < pairs; t += (int64_t)gridDim.x * blockDim.x) {
     int i = (int)(t / k), j = (int)(t % k);
