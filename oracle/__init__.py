@@ -44,26 +44,28 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+def configure(lib):
+    """Declare the C signatures on a loaded oracle library (also used by the
+    tests that load a copy of the oracle with a planted mistake)."""
+    i64, i32, vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p
+    lib.orc_core_numbers.argtypes = [i64, vp, vp, vp, vp]
+    lib.orc_core_numbers.restype = ctypes.c_int
+    lib.orc_greedy_colors.argtypes = [i64, vp, vp, vp, vp]
+    lib.orc_greedy_colors.restype = i32
+    lib.orc_heuristic_clique.argtypes = [i64, vp, vp, vp, ctypes.c_int, vp, i32, vp]
+    lib.orc_heuristic_clique.restype = ctypes.c_int
+    lib.orc_max_clique.argtypes = [i64, vp, vp, vp, vp, i32, vp]
+    lib.orc_max_clique.restype = ctypes.c_int
+    lib.orc_is_clique.argtypes = [i64, vp, vp, vp, i32]
+    lib.orc_is_clique.restype = ctypes.c_int
+    return lib
+
+
 def _L():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            i64, i32, vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p
-            lib.orc_core_numbers.argtypes = [i64, vp, vp, vp, vp]
-            lib.orc_core_numbers.restype = ctypes.c_int
-            lib.orc_greedy_colors.argtypes = [i64, vp, vp, vp, vp]
-            lib.orc_greedy_colors.restype = i32
-            lib.orc_heuristic_clique.argtypes = [i64, vp, vp, vp, ctypes.c_int, vp, i32, vp]
-            lib.orc_heuristic_clique.restype = ctypes.c_int
-            lib.orc_max_clique.argtypes = [i64, vp, vp, vp, vp, i32, vp]
-            lib.orc_max_clique.restype = ctypes.c_int
-            lib.orc_is_clique.argtypes = [i64, vp, vp, vp, i32]
-            lib.orc_is_clique.restype = ctypes.c_int
-            if hasattr(lib, "orc_in_max_clique"):
-                lib.orc_in_max_clique.argtypes = [i64, vp, vp, i32, vp]
-                lib.orc_in_max_clique.restype = ctypes.c_int
-            _lib = lib
+            _lib = configure(ctypes.CDLL(build()))
     return _lib
 
 

@@ -83,3 +83,17 @@ def test_features_closed_forms():
     # isolated vertex
     f = OL.features(gg.empty(3), np.zeros(3, np.int32))
     assert np.allclose(f, 0.0)
+
+
+def test_features_mixed_neighbour_cores():
+    """K4 on {0,1,2,3} with the path 0-4-5 attached: vertex 0 sees core
+    numbers 3, 3, 3, 1, so the maximum, the mean and the count of
+    neighbours at its own core number all differ (Kmax = 3, Dmax = 4)."""
+    g = gg.from_edges(6, [0, 0, 0, 1, 1, 2, 0, 4], [1, 2, 3, 2, 3, 3, 4, 5])
+    K = oracle.core_numbers(g)
+    assert K.tolist() == [3, 3, 3, 3, 1, 1]
+    f = OL.features(g, K)
+    L4 = np.log1p(4)
+    assert np.allclose(f[0], [1.0, 1.0, np.log1p(3) / L4, 1.0, 2.5 / 3, 3 / 4])
+    assert np.allclose(f[4], [np.log1p(2) / L4, 1 / 3, np.log1p(2) / L4, 1.0, 2 / 3, 1.0])
+    assert np.allclose(f[5], [np.log1p(1) / L4, 1 / 3, np.log1p(1) / L4, 1 / 3, 1 / 3, 1.0])

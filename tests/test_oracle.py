@@ -239,3 +239,102 @@ def test_heuristic_mode1_is_max_over_start_vertices():
     H = oracle.heuristic_clique(g, mode=1)
     assert len(H) == 15
     assert np.array_equal(H, np.sort(g.planted))
+
+
+# ------------------------------------------ tight cases and tie-breaks --
+
+def test_greedy_colouring_closed_forms():
+    """Greedy colouring (Section 3): a complete graph needs n colours in any
+    order; an edgeless graph one; disjoint cliques the largest clique; a
+    cycle visited along the cycle 2 (even) or 3 (odd); a complete bipartite
+    graph visited one side first 2."""
+    rng = np.random.default_rng(0)
+    assert oracle.greedy_colors(gg.complete(7), rng.permutation(7)) == 7
+    assert oracle.greedy_colors(gg.empty(5), np.arange(5)) == 1
+    g = gg.disjoint_cliques([3, 6, 2])
+    assert oracle.greedy_colors(g, rng.permutation(g.n)) == 6
+    assert oracle.greedy_colors(gg.cycle(10), np.arange(10)) == 2
+    assert oracle.greedy_colors(gg.cycle(11), np.arange(11)) == 3
+    assert oracle.greedy_colors(gg.complete_bipartite(4, 6), np.arange(10)) == 2
+    assert oracle.greedy_colors(gg.star(8), np.arange(8)) == 2
+
+
+def test_is_clique_definition_cases():
+    """A clique is a set of distinct vertices, every pair adjacent."""
+    k5, p = gg.complete(5), gg.path(4)
+    assert oracle.is_clique(k5, [0, 1, 2, 3, 4]) and oracle.is_clique(k5, [3])
+    assert oracle.is_clique(p, [1, 2])
+    assert not oracle.is_clique(p, [0, 1, 2])       # 0 and 2 are not adjacent
+    assert not oracle.is_clique(p, [0, 1, 3])       # only the last pair fails
+    assert not oracle.is_clique(k5, [1, 2, 2])      # a repeated vertex
+    assert not oracle.is_clique(k5, [2, 1, 2])
+    assert not oracle.is_clique(k5, [0, 5])         # out of range
+    assert not oracle.is_clique(gg.empty(3), [0, 1])
+
+
+def tight_instance(k):
+    """A k-clique Q whose members have core number exactly k-1, each also
+    joined to one vertex of a triangle-free (k-1)-regular graph that has a
+    smaller id, the same core number and the same degree, so Algorithm 1's
+    greedy step from any member of Q takes that vertex first and stops at
+    two; for k >= 4 a separate (k-1)-clique.  Algorithm 1 then ends one short
+    of omega = k, and every member of the maximum clique sits exactly on the
+    pruning bound K(v) >= |H|."""
+    if k == 3:
+        base_n, edges, attach = 9, [(i, (i + 1) % 9) for i in range(9)], [0, 3, 6]
+    else:
+        pg = gg.petersen()
+        src = np.repeat(np.arange(pg.n), pg.degrees())
+        keep = src < pg.col_idx
+        base_n, edges, attach = pg.n, list(zip(src[keep].tolist(), pg.col_idx[keep].tolist())), [0, 2, 4, 6]
+    Q = list(range(base_n, base_n + k))
+    edges += [(a, b) for i, a in enumerate(Q) for b in Q[i + 1:]] + list(zip(Q, attach))
+    n = base_n + k
+    if k >= 4:
+        R = list(range(n, n + k - 1))
+        edges += [(a, b) for i, a in enumerate(R) for b in R[i + 1:]]
+        n += k - 1
+    s, d = zip(*edges)
+    return gg.from_edges(n, s, d), Q
+
+
+@pytest.mark.parametrize("k", [3, 4])
+def test_tight_instances_where_the_heuristic_is_one_short(k):
+    """Every bound of Algorithm 2 is met with equality here (the pruning
+    test K(v) >= |H|, the neighbourhood core and colour tests of
+    InitialBranch, the colour test of Branch), so an off-by-one in any of
+    them loses the maximum clique."""
+    g, Q = tight_instance(k)
+    K = oracle.core_numbers(g)
+    assert K[Q].tolist() == [k - 1] * k
+    for mode in (0, 1):
+        H = oracle.heuristic_clique(g, K, mode)
+        assert len(H) == k - 1 and oracle.is_clique(g, H)
+    om, wit, st = oracle.max_clique(g)
+    assert om == k == brute_omega(g)
+    assert wit.tolist() == Q
+    assert st["heuristic"] == k - 1
+
+
+def test_heuristic_tie_breaks():
+    """Ties in Algorithm 1's core order (the reading: larger degree first,
+    then smaller id), worked by hand.  Triangles {0,1,2} and {0,3,4}, and a
+    pendant on each of 3 and 4: vertices 0-4 have core number 2, vertex 0
+    degree 4, vertices 3 and 4 degree 3, vertices 1 and 2 degree 2.  From 0
+    the candidates are taken as 3, 4, 1, 2, giving {0,3,4}; vertex 0 comes
+    first in the visiting order, and no later start beats size 3."""
+    g = gg.from_edges(7, [0, 0, 1, 0, 0, 3, 3, 4], [1, 2, 2, 3, 4, 4, 5, 6])
+    assert oracle.core_numbers(g)[:5].tolist() == [2] * 5
+    for mode in (0, 1):
+        assert oracle.heuristic_clique(g, mode=mode).tolist() == [0, 3, 4]
+
+
+def test_heuristic_running_maximum():
+    """Algorithm 1 with its running maximum: in K(3,3) plus a separate
+    triangle the bipartite vertices (core 3) come first and give max = 2;
+    the triangle's vertices (core 2, not below max) are still started, and
+    their candidates with core >= max give the triangle."""
+    src = [0, 0, 0, 1, 1, 1, 2, 2, 2, 6, 6, 7]
+    dst = [3, 4, 5, 3, 4, 5, 3, 4, 5, 7, 8, 8]
+    g = gg.from_edges(9, src, dst)
+    assert oracle.heuristic_clique(g, mode=0).tolist() == [6, 7, 8]
