@@ -48,7 +48,7 @@ extern "C" {
 #define MC_ERR_TIMEOUT (-5)       /* a device spin-wait exceeded its iteration limit */
 #define MC_ERR_CUDA (-6)          /* a CUDA runtime call failed */
 #define MC_ERR_DEVICE_CHECK (-7)  /* a device-side consistency check failed */
-#define MC_ERR_UNSUPPORTED (-8)   /* a neighbourhood exceeds the supported size */
+#define MC_ERR_UNSUPPORTED (-8)   /* K(G) above 4,096, the largest neighbourhood a worker holds */
 #define MC_ERR_TOO_LARGE (-9)     /* input larger than mc_core_numbers_noalloc's fixed scratch */
 
 /* load flags */
@@ -160,7 +160,8 @@ int mc_core_numbers(mc_graph *g, int32_t *core_out, int32_t *max_core_out);
  * running maximum shared by all workers (the result may differ from run to
  * run; it is always a clique); mode 1: deterministic -- the largest greedy
  * clique over all start vertices, ties to the smallest start vertex.
- * core: n int32 core numbers, or NULL to compute them.  clique_out: capacity
+ * core: accepted for the interface and not read -- core numbers are unique,
+ * and the library uses its own (computed on first use).  clique_out: capacity
  * int32 (sorted ascending); size_out: its size.  For a batch, graph 0 only;
  * use mc_max_clique_batch for all graphs. */
 int mc_heuristic_clique(mc_graph *g, const int32_t *core, int32_t mode, int32_t *clique_out,
@@ -169,7 +170,10 @@ int mc_heuristic_clique(mc_graph *g, const int32_t *core, int32_t mode, int32_t 
 /* Exact maximum clique (Algorithm 2: CoreNumbers, HeuristicClique, pruning,
  * InitialBranch and Branch for every root, incumbent shared by all workers).
  * opt: NULL for defaults.  omega_out: omega(G); witness_out: capacity int32, a
- * maximum clique sorted ascending and verified on the device; stats nullable. */
+ * maximum clique sorted ascending and verified on the device; stats nullable.
+ * MC_ERR_UNSUPPORTED when K(G) > 4,096: a root's candidates (at most K(G))
+ * must fit one worker's 4,096-wide adjacency matrix; nothing of the search is
+ * launched then. */
 int mc_max_clique(mc_graph *g, const mc_options *opt, int32_t *omega_out, int32_t *witness_out,
                   int32_t capacity, mc_stats *stats);
 

@@ -507,7 +507,7 @@ const char *mc_strerror(int code) {
     case MC_ERR_TIMEOUT: return "a device spin-wait exceeded its iteration limit";
     case MC_ERR_CUDA: return g_errbuf[0] ? g_errbuf : "CUDA runtime error";
     case MC_ERR_DEVICE_CHECK: return "device-side consistency check failed";
-    case MC_ERR_UNSUPPORTED: return "neighbourhood larger than the supported maximum (4096 candidates)";
+    case MC_ERR_UNSUPPORTED: return "maximum core number above 4096, the largest neighbourhood a search worker holds";
     case MC_ERR_TOO_LARGE:
       return "input larger than the fixed scratch of mc_core_numbers_noalloc (1,048,576 vertices, 67,108,864 entries)";
     default: return "unknown error";

@@ -1395,6 +1395,7 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_spli
   a.neigh_cores = no_neigh_cores ? 0 : 1;
   a.counters = ctr;
   const int kbound = std::max(g->max_core, 1);  // |P| <= |N+(u)| <= K(u) <= K(G)
+  if (kbound > 4096) return MC_ERR_UNSUPPORTED;  // refused before anything is launched
   const int wmax = g->warp_max_used;
   if (!no_split) {
     // queue sizes grow with the graph (a small graph gets a small queue; a
@@ -1498,7 +1499,6 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_spli
   }
   MC_TRY(record_event(g, 9));
   if (kbound > 1024) {
-    if (kbound > 4096) return MC_ERR_UNSUPPORTED;
     using L = BlockLayout<4, false>;
     const size_t smem = L::bytes;
     MC_CUDA_TRY(cudaFuncSetAttribute(search_block_kernel<4, false, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize,
