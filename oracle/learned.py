@@ -1,8 +1,8 @@
 """Oracle for the learned vertex ordering -- TEST INFRASTRUCTURE ONLY.
 
 Plain numpy in float64: the per-vertex features, the 6 -> 64 -> 64 -> 1 ReLU
-network's forward pass, its weighted binary cross-entropy loss and the
-analytic gradient.  The network's weights are rounded to bfloat16 (round to
+network's forward pass, its weighted binary cross-entropy loss, the
+analytic gradient and one Adam step.  The network's weights are rounded to bfloat16 (round to
 nearest even) before use, as the CUDA kernels store them; biases stay at
 float32 precision.  Nothing here is shared with the CUDA library.
 """
@@ -115,3 +115,19 @@ def gradient(params, x, y, pos_weight, bf16=True):
     g[OFF_W1:OFF_B1] = (d1.T @ x).ravel()
     g[OFF_B1:OFF_W2] = d1.sum(axis=0)
     return g
+
+
+def adam_step(params, m, v, grad, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma and Ba, 2015) in float64, the optimiser the
+    training kernels use on the float32 master parameters.  t is the step
+    number counted from 1; m and v are the first and second moment estimates
+    before the step.  Returns (params, m, v) after it:
+        m <- beta1 m + (1 - beta1) g,   v <- beta2 v + (1 - beta2) g^2,
+        params <- params - lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps)."""
+    p = np.asarray(params, dtype=np.float64)
+    g = np.asarray(grad, dtype=np.float64)
+    m = beta1 * np.asarray(m, dtype=np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, dtype=np.float64) + (1.0 - beta2) * g * g
+    mhat = m / (1.0 - beta1 ** t)
+    vhat = v / (1.0 - beta2 ** t)
+    return p - lr * mhat / (np.sqrt(vhat) + eps), m, v

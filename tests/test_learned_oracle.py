@@ -97,3 +97,27 @@ def test_features_mixed_neighbour_cores():
     assert np.allclose(f[0], [1.0, 1.0, np.log1p(3) / L4, 1.0, 2.5 / 3, 3 / 4])
     assert np.allclose(f[4], [np.log1p(2) / L4, 1 / 3, np.log1p(2) / L4, 1.0, 2 / 3, 1.0])
     assert np.allclose(f[5], [np.log1p(1) / L4, 1 / 3, np.log1p(1) / L4, 1 / 3, 1 / 3, 1.0])
+
+
+def test_adam_closed_forms():
+    """Adam's bias correction makes a constant gradient g move every
+    parameter by lr * g / (|g| + eps) at every step, the first included; a
+    zero gradient never moves it; the moments follow their geometric sums."""
+    r = np.random.default_rng(4)
+    p0 = r.standard_normal(50)
+    g = r.standard_normal(50) * 10.0 ** r.integers(-6, 2, 50)
+    g[:3] = 0.0
+    lr = 1e-3
+    p, m, v = p0.copy(), np.zeros(50), np.zeros(50)
+    for t in range(1, 6):
+        q, m, v = OL.adam_step(p, m, v, g, t, lr)
+        assert np.allclose(p - q, lr * g / (np.abs(g) + 1e-8), rtol=1e-9, atol=1e-15)
+        p = q
+    assert np.all(p[:3] == p0[:3])
+    assert np.allclose(m, (1 - 0.9 ** 5) * g) and np.allclose(v, (1 - 0.999 ** 5) * g * g)
+    # two steps with different gradients, worked out by hand for one parameter
+    q, m1, v1 = OL.adam_step([1.0], [0.0], [0.0], [2.0], 1, 0.1)
+    q, m2, v2 = OL.adam_step(q, m1, v1, [-1.0], 2, 0.1)
+    mh = (0.9 * 0.2 - 0.1) / (1 - 0.81)
+    vh = (0.999 * 0.004 + 0.001) / (1 - 0.999 ** 2)
+    assert q[0] == pytest.approx(1.0 - 0.1 * 2.0 / (2.0 + 1e-8) - 0.1 * mh / (np.sqrt(vh) + 1e-8), rel=1e-12)

@@ -86,6 +86,11 @@ PY_MUTANTS = [
     ("grad-backprop-through-W2-transposed", "d1 = (d2 @ W2) * (z1 > 0)", "d1 = (d2 @ W2.T) * (z1 > 0)", False),
     ("grad-missing-mean", "gs = w * (1.0 / (1.0 + np.exp(-s)) - y) / n", "gs = w * (1.0 / (1.0 + np.exp(-s)) - y)", False),
     ("grad-b1-dropped", "    g[OFF_B1:OFF_W2] = d1.sum(axis=0)\n", "", False),
+    ("adam-no-bias-correction", "    mhat = m / (1.0 - beta1 ** t)\n", "    mhat = m\n", False),
+    ("adam-second-moment-uncorrected", "    vhat = v / (1.0 - beta2 ** t)\n", "    vhat = v\n", False),
+    ("adam-betas-swapped", "    m = beta1 * np.asarray(m, dtype=np.float64) + (1.0 - beta1) * g\n",
+     "    m = beta2 * np.asarray(m, dtype=np.float64) + (1.0 - beta2) * g\n", False),
+    ("adam-eps-inside-root", "(np.sqrt(vhat) + eps)", "np.sqrt(vhat + eps)", False),
 ]
 
 
