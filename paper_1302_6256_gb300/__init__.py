@@ -153,6 +153,59 @@ def _ptr(a):
     return a.ctypes.data, a
 
 
+def _in(a, dtype, what):
+    """An input array as a contiguous array of `dtype`, the C type the
+    library reads: numpy input (or a sequence) is converted, a torch tensor
+    of another dtype is converted on its own device (and kept alive by the
+    caller of _ptr).  Integer conversions must keep every value."""
+    dtype = np.dtype(dtype)
+    if hasattr(a, "data_ptr"):
+        import torch
+        want = getattr(torch, dtype.name)
+        if a.dtype != want:
+            if dtype.kind == "i":
+                if a.dtype.is_floating_point or a.dtype == torch.bool:
+                    raise TypeError("%s must hold integers, got %s" % (what, a.dtype))
+                info = np.iinfo(dtype)
+                if a.numel() and (int(a.max()) > info.max or int(a.min()) < info.min):
+                    raise ValueError("%s has values outside %s" % (what, dtype.name))
+            a = a.to(want)
+        return a.contiguous()
+    arr = np.asarray(a)
+    if arr.dtype != dtype:
+        if dtype.kind == "i":
+            if arr.dtype.kind not in "iu":
+                raise TypeError("%s must hold integers, got %s" % (what, arr.dtype))
+            info = np.iinfo(dtype)
+            if arr.size and (int(arr.max()) > info.max or int(arr.min()) < info.min):
+                raise ValueError("%s has values outside %s" % (what, dtype.name))
+        arr = arr.astype(dtype)
+    return np.ascontiguousarray(arr)
+
+
+def _out(a, dtype, min_len, what):
+    """An output buffer the library writes in place: it must already have
+    the C type, be contiguous and writable, and hold at least min_len
+    values (the library cannot see its size)."""
+    dtype = np.dtype(dtype)
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != getattr(torch, dtype.name):
+            raise TypeError("%s must be %s, got %s" % (what, dtype.name, a.dtype))
+        if not a.is_contiguous():
+            raise ValueError("%s must be contiguous" % what)
+        size = a.numel()
+    else:
+        if not isinstance(a, np.ndarray) or a.dtype != dtype:
+            raise TypeError("%s must be a %s array" % (what, dtype.name))
+        if not a.flags.c_contiguous or not a.flags.writeable:
+            raise ValueError("%s must be contiguous and writable" % what)
+        size = a.size
+    if size < min_len:
+        raise ValueError("%s holds %d values, needs %d" % (what, size, min_len))
+    return a
+
+
 def _stream_handle(stream):
     if stream is None:
         return None
@@ -188,6 +241,8 @@ class Graph:
 
 def mc_load_csr(row_ptr, col_idx, flags: int = 0, stream=None) -> Graph:
     L = load_library()
+    row_ptr = _in(row_ptr, np.int64, "row_ptr")
+    col_idx = _in(col_idx, np.int32, "col_idx")
     rp, krp = _ptr(row_ptr)
     ci, kci = _ptr(col_idx)
     n = int(row_ptr.shape[0]) - 1
@@ -198,6 +253,9 @@ def mc_load_csr(row_ptr, col_idx, flags: int = 0, stream=None) -> Graph:
 
 def mc_load_batch(voff, row_ptr, col_idx, flags: int = 0, stream=None) -> Graph:
     L = load_library()
+    voff = _in(voff, np.int64, "voff")
+    row_ptr = _in(row_ptr, np.int64, "row_ptr")
+    col_idx = _in(col_idx, np.int32, "col_idx")
     vo, kvo = _ptr(voff)
     rp, krp = _ptr(row_ptr)
     ci, kci = _ptr(col_idx)
@@ -216,7 +274,7 @@ def mc_core_numbers(g: Graph, core_out=None):
     L = load_library()
     if core_out is None:
         core_out = np.zeros(max(g.n, 1), np.int32)
-    p, keep = _ptr(core_out)
+    p, keep = _ptr(_out(core_out, np.int32, g.n, "core_out"))
     mk = ctypes.c_int32(0)
     _check(L.mc_core_numbers(g.handle, p, ctypes.byref(mk)), "mc_core_numbers")
     return core_out[:g.n], mk.value
@@ -227,7 +285,7 @@ def mc_heuristic_clique(g: Graph, mode: int = 0, core=None):
     cap = g.n + 1
     out = np.zeros(cap, np.int32)
     size = ctypes.c_int32(0)
-    cp, kc = _ptr(core)
+    cp, kc = _ptr(None if core is None else _in(core, np.int32, "core"))
     _check(L.mc_heuristic_clique(g.handle, cp, mode, out.ctypes.data, cap, ctypes.byref(size)),
            "mc_heuristic_clique")
     return out[:size.value].copy()
@@ -275,8 +333,8 @@ def mc_max_clique(g: Graph, witness_out=None, **opts):
     om = ctypes.c_int32(0)
     if witness_out is None:
         witness_out = np.zeros(g.n + 1, np.int32)
-    wp, kw = _ptr(witness_out)
-    cap = int(witness_out.shape[0])
+    wp, kw = _ptr(_out(witness_out, np.int32, 0, "witness_out"))
+    cap = int(witness_out.numel() if hasattr(witness_out, "numel") else witness_out.size)
     _check(L.mc_max_clique(g.handle, ctypes.byref(o), ctypes.byref(om), wp, cap, ctypes.byref(st)), "mc_max_clique")
     return om.value, witness_out[:om.value], st.as_dict()
 
@@ -297,7 +355,8 @@ def mc_max_clique_batch(g: Graph, **opts):
 
 def mc_verify_clique(g: Graph, vertices) -> bool:
     L = load_library()
-    vp, keep = _ptr(np.ascontiguousarray(vertices, dtype=np.int32) if not hasattr(vertices, "data_ptr") else vertices)
+    vertices = _in(vertices, np.int32, "vertices")
+    vp, keep = _ptr(vertices)
     out = ctypes.c_int32(0)
     k = int(vertices.shape[0])
     _check(L.mc_verify_clique(g.handle, vp, k, ctypes.byref(out)), "mc_verify_clique")
@@ -319,7 +378,7 @@ def mc_features(g: Graph, feat_out=None):
     L = load_library()
     if feat_out is None:
         feat_out = np.zeros((max(g.n, 1), 6), np.float32)
-    p, keep = _ptr(feat_out)
+    p, keep = _ptr(_out(feat_out, np.float32, 6 * g.n, "feat_out"))
     _check(L.mc_features(g.handle, p), "mc_features")
     return feat_out[:g.n]
 
@@ -351,20 +410,36 @@ class MLP:
         return out
 
     def set_params(self, p):
-        p = np.ascontiguousarray(p, dtype=np.float32)
-        _check(load_library().mc_mlp_set_params(self._h, p.ctypes.data), "mc_mlp_set_params")
+        p = _in(p, np.float32, "params")
+        if int(p.shape[0]) != self.nparams or p.ndim != 1:
+            raise ValueError("params must hold %d values, got shape %s" % (self.nparams, tuple(p.shape)))
+        pp, kp = _ptr(p)
+        _check(load_library().mc_mlp_set_params(self._h, pp), "mc_mlp_set_params")
+
+    @staticmethod
+    def _rows(feat, label=None):
+        """Features as float32 (n, 6) rows and labels as float32 n values."""
+        feat = _in(feat, np.float32, "feat")
+        if feat.ndim != 2 or int(feat.shape[1]) != 6:
+            raise ValueError("feat must have shape (n, 6), got %s" % (tuple(feat.shape),))
+        n = int(feat.shape[0])
+        if label is not None:
+            label = _in(label, np.float32, "label")
+            if label.ndim != 1 or int(label.shape[0]) != n:
+                raise ValueError("label must have shape (%d,), got %s" % (n, tuple(label.shape)))
+        return feat, label, n
 
     def forward(self, feat, out=None):
-        n = int(feat.shape[0])
+        feat, _, n = self._rows(feat)
         if out is None:
             out = np.zeros(max(n, 1), np.float32)
         fp, kf = _ptr(feat)
-        op, ko = _ptr(out)
+        op, ko = _ptr(_out(out, np.float32, n, "out"))
         _check(load_library().mc_mlp_forward(self._h, fp, n, op), "mc_mlp_forward")
         return out[:n]
 
     def gradient(self, feat, label, pos_weight=1.0):
-        n = int(feat.shape[0])
+        feat, label, n = self._rows(feat, label)
         g = np.zeros(self.nparams, np.float32)
         loss = ctypes.c_float(0)
         fp, kf = _ptr(feat)
@@ -374,7 +449,7 @@ class MLP:
         return g, loss.value
 
     def train_step(self, feat, label, pos_weight=1.0, lr=1e-3):
-        n = int(feat.shape[0])
+        feat, label, n = self._rows(feat, label)
         loss = ctypes.c_float(0)
         fp, kf = _ptr(feat)
         lp, kl = _ptr(label)

@@ -71,3 +71,43 @@ def test_options_marshal_learned_scores():
         mc._options(4, ordering=1, scores=torch.zeros(4, dtype=torch.float64))
     o, keep = mc._options(4, ordering=1, scores=torch.zeros(4, dtype=torch.float32))
     assert o.scores == keep.data_ptr()
+
+
+def test_binding_converts_inputs_and_checks_outputs():
+    """Inputs reach the library in its C types (converted when they are not,
+    refused when a value would not survive the conversion); output buffers,
+    which the library writes in place without knowing their size, must have
+    the right type, layout and size already."""
+    import numpy as np
+    import paper_1302_6256_gb300 as mc
+    rp = mc._in(np.array([0, 1, 2], np.int32), np.int64, "row_ptr")
+    assert rp.dtype == np.int64 and rp.tolist() == [0, 1, 2]
+    ci = mc._in([1, 0], np.int32, "col_idx")
+    assert ci.dtype == np.int32 and ci.flags.c_contiguous
+    assert mc._in(np.arange(10, dtype=np.int32)[::2], np.int32, "x").flags.c_contiguous
+    with pytest.raises(ValueError):
+        mc._in(np.array([2 ** 31], np.int64), np.int32, "col_idx")
+    with pytest.raises(TypeError):
+        mc._in(np.array([0.5]), np.int32, "col_idx")
+    assert mc._in(np.zeros(3), np.float32, "feat").dtype == np.float32
+    core = np.zeros(4, np.int32)
+    assert mc._out(core, np.int32, 4, "core_out") is core
+    with pytest.raises(ValueError):
+        mc._out(core, np.int32, 5, "core_out")
+    with pytest.raises(TypeError):
+        mc._out(np.zeros(4, np.int64), np.int32, 4, "core_out")
+    with pytest.raises(ValueError):
+        mc._out(np.zeros(8, np.int32)[::2], np.int32, 4, "core_out")
+    feat, label, n = mc.MLP._rows(np.zeros((5, 6)), [0, 1, 0, 0, 1])
+    assert n == 5 and feat.dtype == np.float32 and label.dtype == np.float32
+    with pytest.raises(ValueError):
+        mc.MLP._rows(np.zeros((5, 4)))
+    with pytest.raises(ValueError):
+        mc.MLP._rows(np.zeros((5, 6)), np.zeros(4))
+    torch = pytest.importorskip("torch")
+    t = mc._in(torch.tensor([0, 3], dtype=torch.int32), np.int64, "row_ptr")
+    assert t.dtype == torch.int64 and t.tolist() == [0, 3]
+    with pytest.raises(TypeError):
+        mc._out(torch.zeros(4, dtype=torch.int64), np.int32, 4, "witness_out")
+    with pytest.raises(ValueError):
+        mc._in(torch.tensor([-1], dtype=torch.int64) * 2 ** 40, np.int32, "col_idx")
