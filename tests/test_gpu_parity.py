@@ -248,6 +248,30 @@ def test_rmat_s22_golden(mc):
     assert oracle.is_clique(g, wit)
 
 
+def test_er_batch_4096_golden(mc):
+    """The 4,096-graph Erdos-Renyi batch at full size (8.5 M vertices, 154 M
+    edges), loaded and solved as the benchmark does (device arrays, one
+    batched solve, then the same solve replayed as a CUDA graph): every
+    graph's omega against the stored oracle run, every witness a clique of
+    that size in its own graph."""
+    path = os.path.join(HERE, "golden", "er-batch-4096.json")
+    if not os.path.exists(path):
+        pytest.skip("oracle golden file for the 4,096-graph batch not generated")
+    from graphgen import workloads as W
+    gold = json.load(open(path))
+    b = W.er_batch_4096()
+    assert b.count == gold["graphs"] == 4096 and b.n == gold["n"] and b.m == gold["m"]
+    ref = np.array(gold["omegas"], np.int32)
+    h = mc.mc_load_batch(torch.from_numpy(b.voff).cuda(), torch.from_numpy(b.row_ptr).cuda(),
+                         torch.from_numpy(b.col_idx).cuda(), 0)
+    for replay in (False, True, True):
+        om, wits, _ = mc.mc_max_clique_batch(h, graph=replay)
+        assert np.array_equal(om, ref)
+    for i in range(0, b.count, 97):
+        assert len(wits[i]) == ref[i] and oracle.is_clique(b.graphs[i], wits[i])
+    h.close()
+
+
 @pytest.mark.slow
 def test_chung_lu_100m_golden(mc):
     """The social-network-scale workload (Chung-Lu, 10^8 vertices, about 1.8
