@@ -6,9 +6,11 @@ counts, the SHA-256 of the int32 core-number array (little endian), the
 maximum core number, the maximum clique size omega with one witness, and
 the oracle's run statistics.  Usage:
 
-    python tests/golden/make_golden.py [--out DIR] chung-lu-20k rmat-s22 ...
+    python tests/golden/make_golden.py [--out DIR] [--cores-only] chung-lu-20k rmat-s22 ...
 
-(--out: write the files to DIR instead of this folder.)
+(--out: write the files to DIR instead of this folder; --cores-only: record
+the core numbers only, with omega and its witness null, for workloads whose
+exact search is beyond the oracle's reach.)
 """
 import hashlib
 import json
@@ -55,7 +57,7 @@ def batch_golden(count):
     print("er-batch", count, "max omega", max(omegas), round(time.time() - t0, 1), flush=True)
 
 
-def main(slugs):
+def main(slugs, cores_only=False):
     for slug in slugs:
         if slug.startswith("er-batch-"):
             batch_golden(int(slug.split("-")[-1]))
@@ -65,15 +67,18 @@ def main(slugs):
         t0 = time.time()
         core = oracle.core_numbers(g)
         t1 = time.time()
-        om, wit, st = oracle.max_clique(g)
-        t2 = time.time()
-        assert oracle.is_clique(g, wit) and len(wit) == om
         out = {"workload": name, "n": g.n, "m": g.m, "core_sha256": core_hash(core),
-               "max_core": int(core.max()), "omega": int(om), "witness": [int(x) for x in wit],
-               "oracle_stats": st, "oracle_core_s": round(t1 - t0, 3), "oracle_max_clique_s": round(t2 - t1, 3)}
+               "max_core": int(core.max()), "omega": None, "witness": None, "oracle_stats": None,
+               "oracle_core_s": round(t1 - t0, 3), "oracle_max_clique_s": None}
+        if not cores_only:
+            om, wit, st = oracle.max_clique(g)
+            t2 = time.time()
+            assert oracle.is_clique(g, wit) and len(wit) == om
+            out.update({"omega": int(om), "witness": [int(x) for x in wit], "oracle_stats": st,
+                        "oracle_max_clique_s": round(t2 - t1, 3)})
         with open(os.path.join(OUT, slug + ".json"), "w") as f:
             json.dump(out, f, indent=1)
-        print(slug, om, st, round(t2 - t1, 1), flush=True)
+        print(slug, out["max_core"], out["omega"], round(time.time() - t0, 1), flush=True)
 
 
 if __name__ == "__main__":
@@ -81,4 +86,6 @@ if __name__ == "__main__":
     if len(args) >= 2 and args[0] == "--out":
         OUT = args[1]
         args = args[2:]
-    main(args or ["chung-lu-20k"])
+    only = "--cores-only" in args
+    args = [a for a in args if a != "--cores-only"]
+    main(args or ["chung-lu-20k"], cores_only=only)
