@@ -111,3 +111,37 @@ def test_binding_converts_inputs_and_checks_outputs():
         mc._out(torch.zeros(4, dtype=torch.int64), np.int32, 4, "witness_out")
     with pytest.raises(ValueError):
         mc._in(torch.tensor([-1], dtype=torch.int64) * 2 ** 40, np.int32, "col_idx")
+
+
+def test_argument_errors_before_any_cuda_call():
+    """The C entry points refuse bad arguments with MC_ERR_ARG (or, for the
+    fixed-scratch core numbers, MC_ERR_TOO_LARGE) before they touch the GPU,
+    so these calls run on a machine without one."""
+    import paper_1302_6256_gb300 as mc
+    L = mc.load_library()
+    vp = ctypes.c_void_p
+    h = vp()
+    assert L.mc_load_csr(-1, None, None, 0, None, ctypes.byref(h)) == mc.MC_ERR_ARG
+    assert L.mc_load_csr(3 * 10 ** 9, None, None, 0, None, ctypes.byref(h)) == mc.MC_ERR_ARG
+    assert L.mc_load_csr(0, None, None, 0, None, None) == mc.MC_ERR_ARG
+    assert L.mc_load_csr(5, None, None, 0, None, ctypes.byref(h)) == mc.MC_ERR_ARG  # rows missing
+    assert L.mc_load_batch(0, None, None, None, 0, None, ctypes.byref(h)) == mc.MC_ERR_ARG
+    om = ctypes.c_int32(7)
+    assert L.mc_max_clique(None, None, ctypes.byref(om), None, 0, None) == mc.MC_ERR_ARG
+    assert L.mc_max_clique_batch(None, None, None, None, 0, None, None) == mc.MC_ERR_ARG
+    assert L.mc_core_numbers(None, None, None) == mc.MC_ERR_ARG
+    size = ctypes.c_int32(0)
+    assert L.mc_heuristic_clique(None, None, 0, None, 0, ctypes.byref(size)) == mc.MC_ERR_ARG
+    assert L.mc_graph_info(None, None, None, None) == mc.MC_ERR_ARG
+    ok = ctypes.c_int32(0)
+    assert L.mc_verify_clique(None, None, 0, ctypes.byref(ok)) == mc.MC_ERR_ARG
+    assert L.mc_mlp_create(1, None, None) == mc.MC_ERR_ARG
+    L.mc_free(None)
+    L.mc_mlp_free(None)
+    L.mc_core_numbers_noalloc.argtypes = [ctypes.c_int64, vp, vp, vp, ctypes.POINTER(ctypes.c_int32), vp]
+    L.mc_core_numbers_noalloc.restype = ctypes.c_int
+    assert L.mc_core_numbers_noalloc(-1, None, None, None, None, None) == mc.MC_ERR_ARG
+    dummy = ctypes.c_int64(0)
+    p = ctypes.addressof(dummy)
+    assert L.mc_core_numbers_noalloc((1 << 20) + 1, p, p, p, None, None) == mc.MC_ERR_TOO_LARGE
+    assert L.mc_strerror(mc.MC_ERR_UNSUPPORTED).decode().startswith("maximum core number above 4096")
