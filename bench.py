@@ -141,14 +141,20 @@ class Clocks:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu: int):
+    def __init__(self, gpu: int, path: str | None = None):
+        """path: where the raw samples go (a temporary file if None)."""
         self.gpu = gpu
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % gpu)
+        if path is None:
+            import tempfile
+            fd, path = tempfile.mkstemp(prefix="clocks_gpu%d_" % gpu, suffix=".csv")
+            os.close(fd)
+        self.path = path
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            if os.path.dirname(self.path):
+                os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
                                           "-lms", "200", "-i", str(self.gpu)], stdout=self.f,
@@ -355,6 +361,8 @@ def main():
                          "per-graph: one solve per graph of a batch")
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1302_6256_gb300", "ordering_mlp.npy"))
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--clocks-csv", default=None,
+                    help="keep the raw nvidia-smi samples of the timed region in this file (rank r appends _r)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -390,7 +398,8 @@ def main():
     for _ in range(args.warmup):
         om, _, st = mc.mc_max_clique(h, witness_out=wit_h)
 
-    clocks = Clocks(local)
+    clocks = Clocks(local, None if args.clocks_csv is None else
+                    (args.clocks_csv if ws == 1 else "%s_%d" % (args.clocks_csv, rank)))
     clocks.start()
     if ws > 1:
         dist.barrier()
