@@ -361,6 +361,8 @@ def main():
                          "per-graph: one solve per graph of a batch")
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1302_6256_gb300", "ordering_mlp.npy"))
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--heuristic", type=int, default=0, choices=[0, 1, 3],
+                    help="Algorithm 1 form of the main solve: 0 printed (default), 1 deterministic, 3 warm-up only")
     ap.add_argument("--clocks-csv", default=None,
                     help="keep the raw nvidia-smi samples of the timed region in this file (rank r appends _r)")
     args = ap.parse_args()
@@ -396,7 +398,7 @@ def main():
 
     wit_h = torch.zeros(g.n + 1, dtype=torch.int32).pin_memory()
     for _ in range(args.warmup):
-        om, _, st = mc.mc_max_clique(h, witness_out=wit_h)
+        om, _, st = mc.mc_max_clique(h, witness_out=wit_h, heuristic=args.heuristic)
 
     clocks = Clocks(local, None if args.clocks_csv is None else
                     (args.clocks_csv if ws == 1 else "%s_%d" % (args.clocks_csv, rank)))
@@ -410,7 +412,7 @@ def main():
     t0.record(stream)
     stats = []
     for _ in range(args.steps):
-        om, wit, st = mc.mc_max_clique(h, witness_out=wit_h)
+        om, wit, st = mc.mc_max_clique(h, witness_out=wit_h, heuristic=args.heuristic)
         stats.append(st)
     t1.record(stream)
     torch.cuda.synchronize()
@@ -429,7 +431,7 @@ def main():
     te = time.perf_counter()
     for _ in range(e2e_steps):
         he = mc.mc_load_csr(rp_h, ci_h, 0, stream=stream)
-        om_e, wit_e, _ = mc.mc_max_clique(he, witness_out=wit_h)
+        om_e, wit_e, _ = mc.mc_max_clique(he, witness_out=wit_h, heuristic=args.heuristic)
         he.close()
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - te) * 1e3 / e2e_steps
@@ -445,7 +447,9 @@ def main():
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
         "config": {"workload": W.RMAT_S22, "n": n, "m": g.m, "omega": om, "max_core": stats[-1]["max_core"],
-                   "form": "chosen (block/warp workers, degeneracy-order colouring)", "l2": "inputs > L2 (537 MB CSR)",
+                   "form": "chosen (block/warp workers, degeneracy-order colouring)"
+                           + ("" if args.heuristic == 0 else ", heuristic %d" % args.heuristic),
+                   "l2": "inputs > L2 (537 MB CSR)",
                    "parallelism": "replicas" if ws > 1 else "1 GPU"},
         "e2e": {"value": job_value(g.m, ws, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(rp_h.numel() * 8 + ci_h.numel() * 4),

@@ -69,7 +69,11 @@ typedef struct {
    * "pmc no neigh cores" variant, Section 5); 0 = use it (default) */
   int32_t no_neigh_cores;
   /* heuristic: 0 = Algorithm 1 with the running maximum shared by all
-   * workers (default); 1 = deterministic form; 2 = skip (start from 0) */
+   * workers (default); 1 = deterministic form; 2 = skip (start from 0);
+   * 3 = its warm-up part only: the printed algorithm from the seeds and the
+   * 256 start vertices of highest core number, each grown by a whole block
+   * (on graphs whose densest core holds a maximum clique this reaches the
+   * full heuristic's bound at a fraction of its cost) */
   int32_t heuristic;
   /* worker split: neighbourhoods with more than this many candidates go to
    * block workers; 0 = tuned default */

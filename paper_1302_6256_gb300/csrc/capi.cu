@@ -286,7 +286,7 @@ int record_event(mc_graph *g, int i) {
 static int check_options(const mc_options *opt, mc_options *o) {
   *o = mc_options{};
   if (opt) *o = *opt;
-  if (o->ordering < 0 || o->ordering > 2 || o->heuristic < 0 || o->heuristic > 2 || o->warp_max < 0 ||
+  if (o->ordering < 0 || o->ordering > 2 || o->heuristic < 0 || o->heuristic > 3 || o->warp_max < 0 ||
       o->seeds < 0 || o->graph < 0 || o->graph > 1 || o->no_split < 0 || o->no_split > 1 ||
       o->split_nodes < 0)
     return MC_ERR_ARG;
@@ -333,7 +333,8 @@ static int enqueue_solve(mc_graph *g, const mc_options &o, Pruned *pg, SearchCou
     }
   }
   g->heur_ran = o.heuristic != 2 && g->n > 0;
-  if (g->heur_ran) MC_TRY(launch_heuristic(g, o.heuristic, spin, d_seeds, nseeds, d_scores));
+  if (g->heur_ran)
+    MC_TRY(launch_heuristic(g, o.heuristic == 3 ? 0 : o.heuristic, spin, d_seeds, nseeds, d_scores, o.heuristic == 3));
   MC_TRY(record_event(g, 2));
   int32_t *h_heur = (int32_t *)((char *)g->h_small + 1024);
   MC_CUDA_TRY(cudaMemcpyAsync(h_heur, g->best, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));

@@ -545,8 +545,9 @@ __global__ void heuristic_finalize_kernel(HA a, int32_t ngraphs) {
 }  // namespace
 
 int launch_heuristic(mc_graph *g, int mode, long long spin_limit, const int32_t *seeds, int64_t nseeds,
-                     const float *scores) {
+                     const float *scores, bool warm_only) {
   if (g->n == 0) return MC_OK;
+  if (warm_only && mode != 0) return MC_ERR_ARG;  // the deterministic form needs every start vertex
   void *p;
   // First launch: 32 warps per SM with candidate buffers that share 2 GiB;
   // start vertices with more candidates are deferred to a second launch with
@@ -623,6 +624,7 @@ int launch_heuristic(mc_graph *g, int mode, long long spin_limit, const int32_t 
   heuristic_warm_kernel<<<(int)warm_blocks, kWT, 0, g->stream>>>(a);
   g_launches++;
   MC_CUDA_TRY(cudaGetLastError());
+  if (warm_only) return MC_OK;
   a.cand_stride = cap_s;
   if (warm < total) {
     a.begin = warm;

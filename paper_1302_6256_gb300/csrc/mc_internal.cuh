@@ -72,8 +72,10 @@ int launch_core_numbers(mc_graph *g, long long spin_limit);
 
 // Heuristic (Algorithm 1).  mode 0 racy, 1 deterministic.  Raises the
 // incumbent of every graph.  seeds (nullable, device): vertices grown first.
+// warm_only (mode 0): only the warm-up launch -- the seeds and the highest
+// start vertices of the visiting order, each grown by a whole block.
 int launch_heuristic(mc_graph *g, int mode, long long spin_limit, const int32_t *seeds, int64_t nseeds,
-                     const float *scores);
+                     const float *scores, bool warm_only = false);
 
 // Pruned, oriented graph and the root lists (see prune.cu).
 struct Pruned {

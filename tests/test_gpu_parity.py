@@ -108,8 +108,8 @@ def test_heuristic_racy_is_valid(mc, g):
 
 
 @pytest.mark.parametrize("opts", [dict(ordering=2), dict(no_neigh_cores=True), dict(heuristic=1),
-                                  dict(heuristic=2), dict(warp_max=16), dict(warp_max=1), dict(no_split=True),
-                                  dict(heuristic=2, warp_max=16)],
+                                  dict(heuristic=2), dict(heuristic=3), dict(warp_max=16), dict(warp_max=1),
+                                  dict(no_split=True), dict(heuristic=2, warp_max=16)],
                          ids=lambda o: ",".join("%s=%s" % kv for kv in o.items()))
 def test_options_keep_omega(mc, opts):
     for g in medium_graphs()[:6]:
