@@ -31,6 +31,7 @@
 // warps per SM with candidate buffers sharing 2 GiB; start vertices with more
 // candidates than a buffer holds go to a last launch with full-degree
 // buffers.  Every growth, by a block or a warp, yields the same clique.
+// The warm-up launch can also run alone (mc_options.heuristic = 3).
 #include <algorithm>
 #include <climits>
 
