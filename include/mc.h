@@ -194,7 +194,8 @@ int mc_max_clique_batch(mc_graph *g, const mc_options *opt, int32_t *omegas_out,
  * graph `repeats` times per candidate setting, one coordinate at a time,
  * starting from `base` (NULL = defaults): the work split between warp and
  * block workers (warp_max 32, 64, 128), then the task queue (no_split, or
- * split_nodes 1024, 4096, 16384), then CUDA-graph replay (graph 0, 1).  It
+ * split_nodes 1024, 4096, 16384), then, from the default heuristic, its
+ * warm-up part alone (heuristic 3), then CUDA-graph replay (graph 0, 1).  It
  * writes the fastest setting to *best_out and its mean time (ms) to
  * *best_ms_out (nullable).  Every trial is a full exact solve. */
 int mc_autotune(mc_graph *g, const mc_options *base, int32_t repeats, mc_options *best_out, double *best_ms_out);

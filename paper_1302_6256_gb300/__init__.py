@@ -459,12 +459,12 @@ class MLP:
 
 
 def mc_autotune(g: Graph, repeats: int = 2, **opts):
-    """Fastest (warp_max, no_split, split_nodes, graph) setting for this
-    graph; returns (options dict, ms)."""
+    """Fastest (warp_max, no_split, split_nodes, heuristic, graph) setting
+    for this graph; returns (options dict, ms)."""
     L = load_library()
     base, keep = _options(g.n, **opts)
     best = Options()
     ms = ctypes.c_double(0)
     _check(L.mc_autotune(g.handle, ctypes.byref(base), repeats, ctypes.byref(best), ctypes.byref(ms)), "mc_autotune")
     return {"warp_max": best.warp_max, "no_split": bool(best.no_split), "split_nodes": best.split_nodes,
-            "graph": bool(best.graph)}, ms.value
+            "heuristic": best.heuristic, "graph": bool(best.graph)}, ms.value

@@ -1,4 +1,5 @@
-"""Cached autotuning of the solve's work split, task queue and graph replay.
+"""Cached autotuning of the solve's work split, task queue, heuristic extent
+and graph replay.
 
 ``tuned(g, key)`` returns the options ``mc_autotune`` found fastest for a
 workload, keeping results in a JSON file (``_build/autotune.json``) keyed by

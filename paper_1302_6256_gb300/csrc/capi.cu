@@ -646,7 +646,8 @@ int mc_autotune(mc_graph *g, const mc_options *base, int32_t repeats, mc_options
     return MC_OK;
   };
   // one coordinate at a time: the warp/block split of the roots, the spill
-  // budget of the task queue, then direct launches vs graph replay
+  // budget of the task queue, the heuristic's extent, then direct launches
+  // vs graph replay
   mc_options bo = b;
   bo.graph = 0;
   double best = 1e300;
@@ -679,6 +680,18 @@ int mc_autotune(mc_graph *g, const mc_options *base, int32_t repeats, mc_options
   }
   bo.no_split = bs.no_split;
   bo.split_nodes = bs.nodes;
+  if (bo.heuristic == 0) {
+    // the warm-up part of Algorithm 1 alone, where it reaches a bound that
+    // prunes as well for less work
+    mc_options o = bo;
+    o.heuristic = 3;
+    double ms;
+    MC_TRY(trial(o, &ms));
+    if (ms < best) {
+      best = ms;
+      bo.heuristic = 3;
+    }
+  }
   {
     mc_options o = bo;
     o.graph = 1;
