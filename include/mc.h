@@ -217,6 +217,13 @@ int mc_verify_clique(mc_graph *g, const int32_t *vertices, int32_t k, int32_t *i
  *   read); core_out: n int32 in device memory, written; max_core_out: host
  *   int32 or NULL, receives K(G).  cuda_stream: the stream to run on.
  * Larger inputs are rejected with MC_ERR_TOO_LARGE before anything runs.
+ * What is checked: before the peel, a pass over the input checks the bounds
+ * that the peel's memory accesses rely on -- row_ptr[0] = 0, row_ptr
+ * nondecreasing, and every col_idx entry in [0, n) -- and returns
+ * MC_ERR_INVALID_GRAPH, with nothing else run, if one fails.  What is not
+ * checked: that rows are sorted, free of duplicates and self-loops, and
+ * that the pattern is symmetric; on such input the call stays within its
+ * buffers but the numbers it writes are not core numbers.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current.  The call synchronises
  * its stream before it returns (it reads K(G) and the device error word), so

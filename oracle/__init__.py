@@ -1,7 +1,7 @@
 """CPU oracle for exact maximum clique -- TEST INFRASTRUCTURE ONLY.
 
-Python access to ``oracle.c`` (plain single-threaded C written from the
-paper's definitions and algorithms).  Only ``tests/``, the smoke check and the
+Python access to ``oracle.c`` (plain C written from the paper's definitions
+and algorithms; single-threaded except for ``max_clique_threads``).  Only ``tests/``, the smoke check and the
 benchmark's CPU-baseline leg may import this package; the CUDA library never
 does, and the two share no code.
 """
@@ -15,7 +15,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "learned.c")]
+_SRCS = [os.path.join(_HERE, "oracle.c")]
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 _lib = None
 _lock = threading.Lock()
@@ -24,12 +24,12 @@ _lock = threading.Lock()
 def build(force: bool = False) -> str:
     """Compile the oracle's C sources into ``_build/liboracle.so``."""
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
-    srcs = [s for s in _SRCS if os.path.exists(s)]
+    srcs = list(_SRCS)
     newest = max(os.path.getmtime(s) for s in srcs)
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
         return _LIB_PATH
     tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
-    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared"] + srcs
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-pthread"] + srcs
                    + ["-o", tmp, "-lm"], check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -58,6 +58,8 @@ def configure(lib):
     lib.orc_max_clique.restype = ctypes.c_int
     lib.orc_is_clique.argtypes = [i64, vp, vp, vp, i32]
     lib.orc_is_clique.restype = ctypes.c_int
+    lib.orc_max_clique_threads.argtypes = [i64, vp, vp, i32, vp, vp, i32, vp]
+    lib.orc_max_clique_threads.restype = ctypes.c_int
     return lib
 
 
@@ -125,6 +127,23 @@ def max_clique(g):
                              ctypes.addressof(st))
     if rc != 0:
         raise RuntimeError("oracle max clique failed: %d" % rc)
+    return om.value, W[:om.value].copy(), st.as_dict()
+
+
+def max_clique_threads(g, threads: int):
+    """The exact search by `threads` workers sharing the incumbent (Section
+    4.5), roots in a static degeneracy order.  omega is the same as
+    max_clique's; the witness may be another maximum clique.  Returns
+    (omega, witness sorted ascending, stats dict)."""
+    rp, ci, n = _csr(g)
+    cap = n + 1
+    W = np.zeros(max(cap, 1), np.int32)
+    om = ctypes.c_int32(0)
+    st = Stats()
+    rc = _L().orc_max_clique_threads(n, rp.ctypes.data, ci.ctypes.data, int(threads), ctypes.addressof(om),
+                                     W.ctypes.data, cap, ctypes.addressof(st))
+    if rc != 0:
+        raise RuntimeError("oracle threaded max clique failed: %d" % rc)
     return om.value, W[:om.value].copy(), st.as_dict()
 
 

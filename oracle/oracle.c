@@ -3,8 +3,9 @@
  * "Parallel Maximum Clique Algorithms with Applications to Network Analysis
  * and Storage").
  *
- * TEST INFRASTRUCTURE ONLY.  Plain, slow, single-threaded C that follows the
- * paper's definitions and algorithms step by step.  Only the tests, the smoke
+ * TEST INFRASTRUCTURE ONLY.  Plain, slow C that follows the paper's
+ * definitions and algorithms step by step (single-threaded, except for the
+ * threaded search at the end, which exists to reach the largest inputs).  Only the tests, the smoke
  * check and the benchmark's CPU-baseline leg use it; the product path never
  * calls it, and it shares no code, header or table with the CUDA library.
  *
@@ -16,6 +17,9 @@
  *   orc_max_clique        Algorithm 2 (MaxClique, InitialBranch, Branch),
  *                         Sections 4.2-4.3.
  *   orc_is_clique         the definition of a clique.
+ *   orc_max_clique_threads the same exact search by several workers sharing
+ *                         the incumbent (Section 4.5), roots in a static
+ *                         degeneracy order.
  *
  * Readings of points the paper leaves open (each is exact: omega and K do not
  * depend on them):
@@ -521,5 +525,383 @@ out:
   free(K0); free(H); free(newid); free(rp2); free(orig); free(K2); free(ci2);
   free(s.searched); free(s.H); free(s.P); free(s.C);
   free(rd); free(head); free(nxt); free(prv); free(gone); free(byk);
+  return rc;
+}
+
+/* ------------------------------ threaded exact search (Section 4.5) --- */
+
+/*
+ * orc_max_clique_threads: the exact search of Algorithm 2 run by `threads`
+ * workers that share the incumbent, as in the paper's parallel method
+ * (Section 4.5: each worker reads the current |H| before every pruning test
+ * and raises it under a lock).  It exists for graphs whose single-threaded
+ * search above takes hours; it shares no code with the CUDA library either.
+ *
+ *  1. K(v) and a degeneracy order by Batagelj-Zaversnik (orc_core_numbers);
+ *     rank(v) = the position of v in that order.
+ *  2. Algorithm 1 as printed, its start vertices handed to the workers in
+ *     decreasing core order, with the running maximum shared by all.
+ *  3. Vertices with K(v) < |H| removed (Section 4.2); the rest numbered by
+ *     rank, each keeping its later neighbours N+(v) (rank(w) > rank(v)).
+ *  4. Each worker takes the next root u in rank order and looks for cliques
+ *     larger than |H| whose lowest-ranked member is u:
+ *       P = {w in N+(u) : K(w) >= |H|}; skip if |P| + 1 <= |H|;
+ *       core numbers K_P of the subgraph induced by P -- with u, which is
+ *       adjacent to all of P, every one of them is one larger -- so keep
+ *       w with K_P(w) + 1 >= |H| and skip if |kept| + 1 <= |H|;
+ *       greedy colouring of the kept vertices in decreasing K_P (ties:
+ *       smaller vertex id); skip if 1 + L <= |H|;
+ *       Branch({u}, kept), with the colour bound, as in orc_max_clique.
+ *  Every clique has exactly one lowest-ranked member, so each clique larger
+ *  than the final |H| falls in exactly one root's search: omega is exact for
+ *  any root order and any interleaving of the workers (only the witness and
+ *  the work counts can differ from run to run).
+ */
+#include <pthread.h>
+
+static int cmp_i32_asc(const void *x, const void *y) {
+  int32_t a = *(const int32_t *)x, b = *(const int32_t *)y;
+  return (a > b) - (a < b);
+}
+
+typedef struct {
+  /* Algorithm 1 (printed form) over the shared visiting order */
+  int64_t n;
+  const int64_t *rp;
+  const int32_t *ci;
+  const int32_t *core;
+  const vkey *ord;
+  int64_t maxd;
+  int64_t next;   /* next position of ord, taken with __atomic_fetch_add */
+  int32_t max;    /* running maximum, __atomic loads and stores */
+  int32_t *best;  /* its clique, written under mu */
+  pthread_mutex_t mu;
+  int err;
+} th_heur;
+
+static void *heur_worker(void *arg) {
+  th_heur *h = (th_heur *)arg;
+  vkey *S = (vkey *)malloc(((size_t)h->maxd + 1) * sizeof(vkey));
+  int32_t *C = (int32_t *)malloc(((size_t)h->maxd + 2) * sizeof(int32_t));
+  if (!S || !C) { h->err = ORC_ERR_OOM; free(S); free(C); return NULL; }
+  for (;;) {
+    int64_t i = __atomic_fetch_add(&h->next, 1, __ATOMIC_RELAXED);
+    if (i >= h->n) break;
+    int32_t v = h->ord[i].v;
+    int32_t T = __atomic_load_n(&h->max, __ATOMIC_ACQUIRE);
+    /* K(v) >= max is the visiting condition; the order is by decreasing
+     * core and max only grows, so no later start vertex passes either */
+    if (h->core[v] < T) break;
+    int64_t ns = 0;
+    for (int64_t e = h->rp[v]; e < h->rp[v + 1]; e++) {
+      int32_t u = h->ci[e];
+      if (h->core[u] >= T) { S[ns].v = u; S[ns].k = h->core[u]; S[ns].d = h->rp[u + 1] - h->rp[u]; ns++; }
+    }
+    qsort(S, (size_t)ns, sizeof(vkey), cmp_vkey);
+    int32_t c = 0;
+    C[c++] = v;
+    for (int64_t j = 0; j < ns; j++) {
+      int32_t u = S[j].v, ok = 1;
+      for (int32_t t = 0; t < c && ok; t++) ok = adjacent(h->rp, h->ci, u, C[t]);
+      if (ok) C[c++] = u;
+    }
+    if (c > __atomic_load_n(&h->max, __ATOMIC_ACQUIRE)) {
+      pthread_mutex_lock(&h->mu);
+      if (c > h->max) {
+        memcpy(h->best, C, (size_t)c * sizeof(int32_t));
+        __atomic_store_n(&h->max, c, __ATOMIC_RELEASE);
+      }
+      pthread_mutex_unlock(&h->mu);
+    }
+  }
+  free(S); free(C);
+  return NULL;
+}
+
+typedef struct {
+  int64_t n2;            /* vertices left after the explicit pruning */
+  const int64_t *orp;    /* later neighbours (new ids follow rank) */
+  const int32_t *oci;
+  const int32_t *K;      /* core numbers, new numbering */
+  const int32_t *orig;   /* original vertex id */
+  int32_t kmax;
+  int64_t next;          /* next root, __atomic_fetch_add */
+  int32_t best;          /* |H|, __atomic loads and stores */
+  int32_t *H;            /* witness in original ids, written under mu */
+  pthread_mutex_t mu;
+  int64_t ib_calls, ib_full, nodes; /* summed under mu when a worker ends */
+  int err;
+} th_search;
+
+typedef struct {
+  th_search *sh;
+  int32_t *mark;   /* per new id: 0, or 1 + its index in P */
+  int32_t *P;      /* new ids of P */
+  int32_t np;
+  uint8_t *adj;    /* np x np byte matrix of G[P] */
+  int32_t *C;      /* the current clique, new ids */
+  int64_t nodes, ib_calls, ib_full;
+  int err;
+} th_worker;
+
+static int32_t th_best(const th_worker *w) { return __atomic_load_n(&w->sh->best, __ATOMIC_ACQUIRE); }
+
+/* greedy colouring of idx[0..cnt) (indices into P) in that order */
+static int32_t th_color_list(const th_worker *w, const int32_t *idx, int32_t cnt, int32_t *colors, int32_t *scratch) {
+  int32_t L = 0;
+  for (int32_t i = 0; i < cnt; i++) {
+    int32_t a = idx[i];
+    for (int32_t c = 0; c <= cnt + 1; c++) scratch[c] = 0;
+    for (int32_t j = 0; j < i; j++)
+      if (w->adj[(int64_t)a * w->np + idx[j]]) scratch[colors[j]] = 1;
+    int32_t c = 1;
+    while (scratch[c]) c++;
+    colors[i] = c;
+    if (c > L) L = c;
+  }
+  return L;
+}
+
+static void th_raise(th_worker *w, int32_t size) {
+  th_search *sh = w->sh;
+  pthread_mutex_lock(&sh->mu);
+  if (size > sh->best) {
+    for (int32_t i = 0; i < size; i++) sh->H[i] = sh->orig[w->C[i]];
+    __atomic_store_n(&sh->best, size, __ATOMIC_RELEASE);
+  }
+  pthread_mutex_unlock(&sh->mu);
+}
+
+/* Branch(C, P) with |C| = csize, P = idx[0..cnt) in natural order with
+ * their colours; the incumbent is re-read before every test */
+static void th_branch(th_worker *w, int32_t csize, int32_t *idx, int32_t *colors, int32_t cnt) {
+  w->nodes++;
+  int32_t *pidx = (int32_t *)malloc(((size_t)cnt + 1) * sizeof(int32_t));
+  int32_t *pcol = (int32_t *)malloc(((size_t)cnt + 1) * sizeof(int32_t));
+  int32_t *scr = (int32_t *)malloc(((size_t)cnt + 3) * sizeof(int32_t));
+  if (!pidx || !pcol || !scr) { w->err = ORC_ERR_OOM; free(pidx); free(pcol); free(scr); return; }
+  while (cnt > 0 && cnt + csize > th_best(w)) {
+    int32_t at = 0;
+    for (int32_t i = 1; i < cnt; i++) if (colors[i] >= colors[at]) at = i;
+    int32_t u = idx[at], cu = colors[at];
+    for (int32_t i = at; i + 1 < cnt; i++) { idx[i] = idx[i + 1]; colors[i] = colors[i + 1]; }
+    cnt--;
+    if (csize + cu <= th_best(w)) break;
+    w->C[csize] = w->P[u];
+    int32_t c2 = csize + 1;
+    int32_t np2 = 0;
+    for (int32_t i = 0; i < cnt; i++)
+      if (w->adj[(int64_t)u * w->np + idx[i]]) pidx[np2++] = idx[i];
+    if (np2 > 0) {
+      int32_t L = th_color_list(w, pidx, np2, pcol, scr);
+      if (c2 + L > th_best(w)) {
+        th_branch(w, c2, pidx, pcol, np2);
+        if (w->err) break;
+      }
+    } else if (c2 > th_best(w)) {
+      th_raise(w, c2);
+    }
+  }
+  free(pidx); free(pcol); free(scr);
+}
+
+/* the search rooted at u (new id): cliques whose lowest-ranked member is u */
+static void th_root(th_worker *w, int32_t u, int32_t *kn, uint8_t *in, int32_t *idx, int32_t *col, int32_t *scr,
+                    knkey *ord, int32_t *nat, int32_t *ncol) {
+  th_search *sh = w->sh;
+  int32_t h = th_best(w);
+  if (sh->K[u] < h) return; /* K(u) + 1 <= |H| */
+  w->ib_calls++;
+  int32_t np = 0;
+  for (int64_t e = sh->orp[u]; e < sh->orp[u + 1]; e++)
+    if (sh->K[sh->oci[e]] >= h) w->P[np++] = sh->oci[e];
+  if (np + 1 <= h) return;
+  w->ib_full++;
+  w->np = np;
+  /* G[P]: each pair {a, b} of P appears in the later-neighbour list of the
+   * one of lower rank */
+  for (int32_t a = 0; a < np; a++) w->mark[w->P[a]] = a + 1;
+  memset(w->adj, 0, (size_t)np * (size_t)np);
+  for (int32_t a = 0; a < np; a++) {
+    int32_t x = w->P[a];
+    for (int64_t e = sh->orp[x]; e < sh->orp[x + 1]; e++) {
+      int32_t b = w->mark[sh->oci[e]];
+      if (b) {
+        w->adj[(int64_t)a * np + (b - 1)] = 1;
+        w->adj[(int64_t)(b - 1) * np + a] = 1;
+      }
+    }
+  }
+  for (int32_t a = 0; a < np; a++) w->mark[w->P[a]] = 0;
+  for (int32_t a = 0; a < np; a++) in[a] = 1;
+  small_cores(w->adj, np, in, kn);
+  h = th_best(w);
+  int32_t cnt = 0;
+  for (int32_t a = 0; a < np; a++)
+    if (kn[a] + 1 >= h) { ord[cnt].i = a; ord[cnt].kn = kn[a]; ord[cnt].id = sh->orig[w->P[a]]; cnt++; }
+  if (cnt + 1 <= h) return;
+  qsort(ord, (size_t)cnt, sizeof(knkey), cmp_knkey);
+  for (int32_t j = 0; j < cnt; j++) idx[j] = ord[j].i;
+  int32_t L = th_color_list(w, idx, cnt, col, scr);
+  if (1 + L <= th_best(w)) return;
+  /* Branch({u}, kept) with the kept vertices in natural (rank) order */
+  for (int32_t a = 0; a < np; a++) in[a] = 0;
+  for (int32_t j = 0; j < cnt; j++) { in[idx[j]] = 1; kn[idx[j]] = col[j]; }
+  int32_t c = 0;
+  for (int32_t a = 0; a < np; a++) if (in[a]) { nat[c] = a; ncol[c] = kn[a]; c++; }
+  w->C[0] = u;
+  th_branch(w, 1, nat, ncol, c);
+}
+
+static void *search_worker(void *arg) {
+  th_worker *w = (th_worker *)arg;
+  th_search *sh = w->sh;
+  size_t kp = (size_t)sh->kmax + 2;
+  int32_t *kn = (int32_t *)malloc(kp * sizeof(int32_t));
+  uint8_t *in = (uint8_t *)malloc(kp);
+  int32_t *idx = (int32_t *)malloc(kp * sizeof(int32_t));
+  int32_t *col = (int32_t *)malloc(kp * sizeof(int32_t));
+  int32_t *scr = (int32_t *)malloc((kp + 3) * sizeof(int32_t));
+  knkey *ord = (knkey *)malloc(kp * sizeof(knkey));
+  int32_t *nat = (int32_t *)malloc(kp * sizeof(int32_t));
+  int32_t *ncol = (int32_t *)malloc(kp * sizeof(int32_t));
+  if (!kn || !in || !idx || !col || !scr || !ord || !nat || !ncol) {
+    w->err = ORC_ERR_OOM;
+  } else {
+    for (;;) {
+      int64_t i = __atomic_fetch_add(&sh->next, 1, __ATOMIC_RELAXED);
+      if (i >= sh->n2) break;
+      th_root(w, (int32_t)i, kn, in, idx, col, scr, ord, nat, ncol);
+      if (w->err) break;
+    }
+  }
+  free(kn); free(in); free(idx); free(col); free(scr); free(ord); free(nat); free(ncol);
+  pthread_mutex_lock(&sh->mu);
+  sh->ib_calls += w->ib_calls;
+  sh->ib_full += w->ib_full;
+  sh->nodes += w->nodes;
+  if (w->err) sh->err = w->err;
+  pthread_mutex_unlock(&sh->mu);
+  return NULL;
+}
+
+static int run_threads(int threads, void *(*fn)(void *), void *args, size_t stride) {
+  pthread_t *th = (pthread_t *)malloc((size_t)threads * sizeof(pthread_t));
+  if (!th) return ORC_ERR_OOM;
+  int started = 0, rc = ORC_OK;
+  for (int t = 0; t < threads; t++) {
+    if (pthread_create(&th[t], NULL, fn, (char *)args + (size_t)t * stride) != 0) { rc = ORC_ERR_OOM; break; }
+    started++;
+  }
+  for (int t = 0; t < started; t++) pthread_join(th[t], NULL);
+  free(th);
+  return rc;
+}
+
+int orc_max_clique_threads(int64_t n, const int64_t *rp, const int32_t *ci, int32_t threads, int32_t *omega_out,
+                           int32_t *witness, int32_t cap, orc_stats *st) {
+  if (n < 0 || threads < 1 || threads > 1024) return ORC_ERR_ARG;
+  orc_stats local;
+  if (!st) st = &local;
+  memset(st, 0, sizeof(*st));
+  *omega_out = 0;
+  if (n == 0) return ORC_OK;
+  int rc = ORC_OK;
+  int32_t *K0 = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  int32_t *order = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  vkey *hord = (vkey *)malloc((size_t)n * sizeof(vkey));
+  int32_t *newid = NULL, *orig = NULL, *K2 = NULL, *oci = NULL, *H = NULL;
+  int64_t *orp = NULL;
+  th_worker *wk = NULL;
+  th_heur hh;
+  th_search sh;
+  memset(&hh, 0, sizeof(hh));
+  memset(&sh, 0, sizeof(sh));
+  pthread_mutex_init(&hh.mu, NULL);
+  pthread_mutex_init(&sh.mu, NULL);
+  if (!K0 || !order || !hord) { rc = ORC_ERR_OOM; goto out; }
+  /* 1. core numbers and the degeneracy order */
+  if ((rc = orc_core_numbers(n, rp, ci, K0, order)) != ORC_OK) goto out;
+  int32_t kmax = 0;
+  int64_t maxd = 0;
+  for (int64_t v = 0; v < n; v++) {
+    if (K0[v] > kmax) kmax = K0[v];
+    if (rp[v + 1] - rp[v] > maxd) maxd = rp[v + 1] - rp[v];
+  }
+  st->max_core = kmax;
+  H = (int32_t *)malloc(((size_t)kmax + 2) * sizeof(int32_t));
+  if (!H) { rc = ORC_ERR_OOM; goto out; }
+  /* 2. Algorithm 1, printed form, shared running maximum */
+  for (int64_t v = 0; v < n; v++) { hord[v].v = (int32_t)v; hord[v].k = K0[v]; hord[v].d = rp[v + 1] - rp[v]; }
+  qsort(hord, (size_t)n, sizeof(vkey), cmp_vkey);
+  hh.n = n; hh.rp = rp; hh.ci = ci; hh.core = K0; hh.ord = hord; hh.maxd = maxd; hh.best = H;
+  /* every worker gets the same shared record (stride 0) */
+  if ((rc = run_threads(threads, heur_worker, &hh, 0)) != ORC_OK) goto out;
+  if (hh.err) { rc = hh.err; goto out; }
+  free(hord); hord = NULL;
+  int32_t hs = hh.max;
+  st->heuristic = hs;
+  /* 3. explicit pruning; new ids in degeneracy order, later neighbours only */
+  newid = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  if (!newid) { rc = ORC_ERR_OOM; goto out; }
+  int64_t n2 = 0;
+  for (int64_t v = 0; v < n; v++) newid[v] = -1;
+  for (int64_t i = 0; i < n; i++) if (K0[order[i]] >= hs) newid[order[i]] = (int32_t)n2++;
+  st->pruned_n = n2;
+  orp = (int64_t *)malloc(((size_t)n2 + 1) * sizeof(int64_t));
+  orig = (int32_t *)malloc(((size_t)n2 + 1) * sizeof(int32_t));
+  K2 = (int32_t *)malloc(((size_t)n2 + 1) * sizeof(int32_t));
+  if (!orp || !orig || !K2) { rc = ORC_ERR_OOM; goto out; }
+  orp[0] = 0;
+  for (int64_t i = 0; i < n; i++) {
+    int32_t v = order[i];
+    if (newid[v] < 0) continue;
+    int64_t d = 0;
+    for (int64_t e = rp[v]; e < rp[v + 1]; e++) if (newid[ci[e]] > newid[v]) d++;
+    orig[newid[v]] = v;
+    K2[newid[v]] = K0[v];
+    orp[newid[v] + 1] = orp[newid[v]] + d;
+  }
+  oci = (int32_t *)malloc(((size_t)orp[n2] + 1) * sizeof(int32_t));
+  if (!oci) { rc = ORC_ERR_OOM; goto out; }
+  for (int64_t i = 0; i < n; i++) {
+    int32_t v = order[i];
+    if (newid[v] < 0) continue;
+    int64_t o = orp[newid[v]];
+    for (int64_t e = rp[v]; e < rp[v + 1]; e++) if (newid[ci[e]] > newid[v]) oci[o++] = newid[ci[e]];
+    qsort(oci + orp[newid[v]], (size_t)(o - orp[newid[v]]), sizeof(int32_t), cmp_i32_asc);
+  }
+  free(newid); newid = NULL;
+  /* 4. the roots, shared by the workers */
+  sh.n2 = n2; sh.orp = orp; sh.oci = oci; sh.K = K2; sh.orig = orig; sh.kmax = kmax;
+  sh.best = hs; sh.H = H;
+  wk = (th_worker *)calloc((size_t)threads, sizeof(th_worker));
+  if (!wk) { rc = ORC_ERR_OOM; goto out; }
+  for (int t = 0; t < threads; t++) {
+    wk[t].sh = &sh;
+    wk[t].mark = (int32_t *)calloc((size_t)n2 + 1, sizeof(int32_t));
+    wk[t].P = (int32_t *)malloc(((size_t)kmax + 2) * sizeof(int32_t));
+    wk[t].C = (int32_t *)malloc(((size_t)kmax + 2) * sizeof(int32_t));
+    wk[t].adj = (uint8_t *)malloc(((size_t)kmax + 2) * ((size_t)kmax + 2));
+    if (!wk[t].mark || !wk[t].P || !wk[t].C || !wk[t].adj) { rc = ORC_ERR_OOM; goto out; }
+  }
+  if ((rc = run_threads(threads, search_worker, wk, sizeof(th_worker))) != ORC_OK) goto out;
+  if (sh.err) { rc = sh.err; goto out; }
+  st->initial_branch = sh.ib_calls;
+  st->full_branch = sh.ib_full;
+  st->nodes = sh.nodes;
+  *omega_out = sh.best;
+  if (sh.best > cap) rc = ORC_ERR_BUFFER;
+  else {
+    qsort(H, (size_t)sh.best, sizeof(int32_t), cmp_i32_asc);
+    memcpy(witness, H, (size_t)sh.best * sizeof(int32_t));
+  }
+out:
+  if (wk)
+    for (int t = 0; t < threads; t++) { free(wk[t].mark); free(wk[t].P); free(wk[t].C); free(wk[t].adj); }
+  free(wk);
+  free(K0); free(order); free(hord); free(newid); free(orig); free(K2); free(oci); free(orp); free(H);
+  pthread_mutex_destroy(&hh.mu);
+  pthread_mutex_destroy(&sh.mu);
   return rc;
 }

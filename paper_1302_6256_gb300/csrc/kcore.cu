@@ -514,6 +514,26 @@ constexpr size_t kNoAllocBytes = kNaOffWq + 8 * kNoAllocWq;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
+// The bounds the peel's memory accesses rely on, checked before it runs:
+// row_ptr[0] = 0, row_ptr nondecreasing (so every row lies inside
+// [0, row_ptr[n]) = [0, nnz)), and every column index in [0, n).  Reads
+// only row_ptr[0..n] and col_idx[0..nnz); a failure sets *bad.
+__global__ void csr_bounds_kernel(int64_t n, int64_t nnz, const int64_t *__restrict__ rp,
+                                  const int32_t *__restrict__ ci, int32_t *bad) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  bool ok = true;
+  for (int64_t v = t0; v < n; v += stride) {
+    const int64_t a = rp[v], b = rp[v + 1];
+    if (b < a || (v == 0 && a != 0)) ok = false;
+  }
+  for (int64_t e = t0; e < nnz; e += stride) {
+    const int32_t u = ci[e];
+    if (u < 0 || (int64_t)u >= n) ok = false;
+  }
+  if (!ok) atomicExch(bad, 1);
+}
+
 // device address of g_noalloc_scratch, per device (set up on first use)
 static void *g_noalloc_ptr[64];
 static std::mutex g_noalloc_mu;
@@ -559,6 +579,7 @@ extern "C" int mc_core_numbers_noalloc(int64_t n, const int64_t *row_ptr, const 
   KcoreCtl *ctl = (KcoreCtl *)base;
   int32_t *maxdeg = (int32_t *)(base + 1024);  // [0] max degree, [1] max core
   int32_t *err = (int32_t *)(base + 2048);
+  int32_t *bad = (int32_t *)(base + 3072);
   int32_t *deg = (int32_t *)(base + kNaOffDeg);
   int32_t *live0 = (int32_t *)(base + kNaOffLive), *live1 = live0 + n;
   int32_t *order = (int32_t *)(base + kNaOffOrder);
@@ -566,6 +587,17 @@ extern "C" int mc_core_numbers_noalloc(int64_t n, const int64_t *row_ptr, const 
   long long *wq = (long long *)(base + kNaOffWq);
   // the array keeps the previous call's contents: clear the control block
   MC_CUDA_TRY(cudaMemsetAsync(base, 0, kNoAllocCtlBytes, s));
+
+  // the peel indexes its arrays by row offsets and column entries, so those
+  // are checked first; the caller's graph is not otherwise validated
+  const int cb = (int)std::min<int64_t>((std::max(n, nnz) + 255) / 256, (int64_t)sms * 8);
+  csr_bounds_kernel<<<cb, 256, 0, s>>>(n, nnz, row_ptr, col_idx, bad);
+  g_launches++;
+  MC_CUDA_TRY(cudaGetLastError());
+  int32_t h_bad = 0;
+  MC_CUDA_TRY(cudaMemcpyAsync(&h_bad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  MC_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h_bad) return MC_ERR_INVALID_GRAPH;
 
   const int ib = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
   degree_init_kernel<<<ib, 256, 0, s>>>(n, row_ptr, deg, maxdeg);

@@ -6,11 +6,12 @@ counts, the SHA-256 of the int32 core-number array (little endian), the
 maximum core number, the maximum clique size omega with one witness, and
 the oracle's run statistics.  Usage:
 
-    python tests/golden/make_golden.py [--out DIR] [--cores-only] chung-lu-20k rmat-s22 ...
+    python tests/golden/make_golden.py [--out DIR] [--cores-only] [--threads N] chung-lu-20k rmat-s22 ...
 
 (--out: write the files to DIR instead of this folder; --cores-only: record
-the core numbers only, with omega and its witness null, for workloads whose
-exact search is beyond the oracle's reach.)
+the core numbers only, with omega and its witness null; --threads N: find
+omega with the oracle's threaded search, N workers sharing the incumbent,
+for workloads whose single-threaded search takes too long.)
 """
 import hashlib
 import json
@@ -57,7 +58,7 @@ def batch_golden(count):
     print("er-batch", count, "max omega", max(omegas), round(time.time() - t0, 1), flush=True)
 
 
-def main(slugs, cores_only=False):
+def main(slugs, cores_only=False, threads=0):
     for slug in slugs:
         if slug.startswith("er-batch-"):
             batch_golden(int(slug.split("-")[-1]))
@@ -71,11 +72,15 @@ def main(slugs, cores_only=False):
                "max_core": int(core.max()), "omega": None, "witness": None, "oracle_stats": None,
                "oracle_core_s": round(t1 - t0, 3), "oracle_max_clique_s": None}
         if not cores_only:
-            om, wit, st = oracle.max_clique(g)
+            if threads > 0:
+                om, wit, st = oracle.max_clique_threads(g, threads)
+            else:
+                om, wit, st = oracle.max_clique(g)
             t2 = time.time()
             assert oracle.is_clique(g, wit) and len(wit) == om
             out.update({"omega": int(om), "witness": [int(x) for x in wit], "oracle_stats": st,
-                        "oracle_max_clique_s": round(t2 - t1, 3)})
+                        "oracle_max_clique_s": round(t2 - t1, 3),
+                        "oracle_search": ("threaded, %d workers" % threads) if threads > 0 else "single thread"})
         with open(os.path.join(OUT, slug + ".json"), "w") as f:
             json.dump(out, f, indent=1)
         print(slug, out["max_core"], out["omega"], round(time.time() - t0, 1), flush=True)
@@ -88,4 +93,9 @@ if __name__ == "__main__":
         args = args[2:]
     only = "--cores-only" in args
     args = [a for a in args if a != "--cores-only"]
-    main(args or ["chung-lu-20k"], cores_only=only)
+    nthreads = 0
+    if "--threads" in args:
+        i = args.index("--threads")
+        nthreads = int(args[i + 1])
+        args = args[:i] + args[i + 2:]
+    main(args or ["chung-lu-20k"], cores_only=only, threads=nthreads)

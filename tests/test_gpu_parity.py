@@ -13,6 +13,7 @@ import pytest
 
 import graphgen as gg
 import oracle
+from test_oracle import tight_instance
 
 pytestmark = pytest.mark.gpu
 
@@ -53,6 +54,13 @@ def small_graphs():
            gg.disjoint_cliques([4, 17, 9, 17]), gg.mycielski(5), gg.mycielski(7)]
     for s in range(12):
         out.append(gg.random_small(5 + s, 0.2 + 0.06 * s, 500 + s))
+    # every bound of Algorithm 2 met with equality by the maximum clique, the
+    # heuristic one short (test_oracle.tight_instance); relabelled copies too
+    for k in (3, 4, 5):
+        g = tight_instance(k)[0]
+        g.name = "tight%d" % k
+        out.append(g)
+        out.append(gg.relabel(g, 7))
     return out
 
 
@@ -192,6 +200,21 @@ def test_invalid_graph_rejected(mc):
     ci = np.array([0, 1, 0], np.int32)
     with pytest.raises(mc.MCError):
         mc.mc_load_csr(rp, ci, mc.MC_VALIDATE)
+    # a duplicate entry, an unsorted row, a column equal to n, a decreasing
+    # row_ptr, row_ptr[0] != 0 (each array holds row_ptr[n] entries, so the
+    # check reads only inside them)
+    bad = [([0, 2, 3], [1, 1, 0]),
+           ([0, 2, 3, 4], [2, 1, 0, 0]),
+           ([0, 1, 2], [2, 0]),
+           ([0, 2, 1, 4], [1, 2, 0, 0]),
+           ([1, 2, 3], [1, 0, 0])]
+    for rp, ci in bad:
+        with pytest.raises(mc.MCError) as e:
+            mc.mc_load_csr(np.array(rp, np.int64), np.array(ci, np.int32), mc.MC_VALIDATE)
+        assert e.value.code == mc.MC_ERR_INVALID_GRAPH, (rp, ci)
+    # a valid graph still loads after the refusals
+    h = mc.mc_load_csr(np.array([0, 1, 2], np.int64), np.array([1, 0], np.int32), mc.MC_VALIDATE)
+    assert mc.mc_max_clique(h)[0] == 2
 
 
 def test_buffer_too_small_reports_size(mc):

@@ -282,6 +282,9 @@ def tight_instance(k):
     pruning bound K(v) >= |H|."""
     if k == 3:
         base_n, edges, attach = 9, [(i, (i + 1) % 9) for i in range(9)], [0, 3, 6]
+    elif k == 5:
+        # K_{4,4}: triangle-free and 4-regular
+        base_n, edges, attach = 8, [(a, b) for a in range(4) for b in range(4, 8)], [0, 1, 2, 4, 5]
     else:
         pg = gg.petersen()
         src = np.repeat(np.arange(pg.n), pg.degrees())
@@ -298,7 +301,7 @@ def tight_instance(k):
     return gg.from_edges(n, s, d), Q
 
 
-@pytest.mark.parametrize("k", [3, 4])
+@pytest.mark.parametrize("k", [3, 4, 5])
 def test_tight_instances_where_the_heuristic_is_one_short(k):
     """Every bound of Algorithm 2 is met with equality here (the pruning
     test K(v) >= |H|, the neighbourhood core and colour tests of
@@ -338,3 +341,83 @@ def test_heuristic_running_maximum():
     dst = [3, 4, 5, 3, 4, 5, 3, 4, 5, 7, 8, 8]
     g = gg.from_edges(9, src, dst)
     assert oracle.heuristic_clique(g, mode=0).tolist() == [6, 7, 8]
+
+
+# ------------------------------------------------- threaded exact search --
+# The threaded search (Section 4.5: workers sharing the incumbent) must give
+# the same omega as the definition for every interleaving, so each pin runs
+# it with 1, 2 and 4 workers.
+
+THREADS = (1, 2, 4)
+
+
+@pytest.mark.parametrize("g", small_random_graphs(), ids=lambda g: g.name)
+def test_threaded_omega_matches_bruteforce(g):
+    om = brute_omega(g)
+    for t in THREADS:
+        o, wit, st = oracle.max_clique_threads(g, t)
+        assert o == om, t
+        assert len(wit) == o and oracle.is_clique(g, wit)
+        assert st["heuristic"] <= om
+
+
+def test_threaded_omega_closed_forms():
+    cases = [
+        (gg.empty(0), 0), (gg.empty(1), 1), (gg.empty(6), 1),
+        (gg.complete(2), 2), (gg.complete(17), 17),
+        (gg.cycle(3), 3), (gg.cycle(4), 2), (gg.cycle(9), 2),
+        (gg.path(10), 2), (gg.star(20), 2), (gg.petersen(), 2),
+        (gg.complete_bipartite(6, 9), 2),
+        (gg.turan(20, 4), 4), (gg.turan(31, 7), 7), (gg.turan(60, 11), 11),
+        (gg.disjoint_cliques([4, 9, 3, 9, 2]), 9),
+        (gg.mycielski(4), 2), (gg.mycielski(6), 2),
+    ]
+    for g, want in cases:
+        for t in THREADS:
+            om, wit, _ = oracle.max_clique_threads(g, t)
+            assert om == want, (g.name, t)
+            assert len(wit) == om and oracle.is_clique(g, wit)
+
+
+@pytest.mark.parametrize("k", [3, 4, 5])
+def test_threaded_tight_instances(k):
+    """Every bound of the threaded search (the pruning K >= |H|, the root's
+    |P| + 1 test, the neighbourhood-core filter, both colour tests) is met
+    with equality by the maximum clique Q, so an off-by-one in any of them
+    loses it; the maximum clique is unique, so the witness is Q."""
+    g, Q = tight_instance(k)
+    for t in THREADS:
+        om, wit, st = oracle.max_clique_threads(g, t)
+        assert om == k and wit.tolist() == Q, t
+        assert st["heuristic"] == k - 1
+    h = gg.relabel(g, 3)
+    for t in THREADS:
+        om, wit, _ = oracle.max_clique_threads(h, t)
+        assert om == k and oracle.is_clique(h, wit)
+
+
+def test_threaded_heuristic_is_the_printed_algorithm():
+    """The threaded search's Algorithm 1 (start vertices shared by the
+    workers in decreasing core order, running maximum shared): exact on
+    disjoint cliques, and the running-maximum graph of
+    test_heuristic_running_maximum still gives the triangle."""
+    g = gg.disjoint_cliques([5, 12, 7, 12, 3])
+    src = [0, 0, 0, 1, 1, 1, 2, 2, 2, 6, 6, 7]
+    dst = [3, 4, 5, 3, 4, 5, 3, 4, 5, 7, 8, 8]
+    r = gg.from_edges(9, src, dst)
+    for t in THREADS:
+        assert oracle.max_clique_threads(g, t)[2]["heuristic"] == 12
+        assert oracle.max_clique_threads(r, t)[2]["heuristic"] == 3
+
+
+def test_threaded_matches_single_thread_on_generated_graphs():
+    for g in [gg.chung_lu(3000, 2.5, 8.0, 300.0, planted=9, seed=7),
+              gg.rmat(11, 8, planted=12, seed=3),
+              gg.erdos_renyi(500, 0.05, planted=10, seed=5),
+              gg.rmat(12, 16, planted=14, seed=2)]:
+        om, _, st1 = oracle.max_clique(g)
+        for t in THREADS:
+            o, wit, st = oracle.max_clique_threads(g, t)
+            assert o == om and oracle.is_clique(g, wit) and len(wit) == o
+            assert st["max_core"] == st1["max_core"]
+            assert st["heuristic"] <= om

@@ -30,15 +30,19 @@ C_MUTANTS = [
      "    int32_t c = 2;\n    while (mark[c] == i) c++;", False),
     ("colours-ignore-neighbours", "if (c > 0 && c <= n + 1) mark[c] = i;", "if (c > 0 && c <= n + 1) mark[c] = i - 1;", False),
     # Algorithm 1
-    ("heuristic-C-starts-empty", "    C[c++] = v;\n    for (int64_t j = 0; j < ns; j++) {",
-     "    for (int64_t j = 0; j < ns; j++) {", False),
+    ("heuristic-C-starts-empty",
+     "    C[c++] = v;\n    for (int64_t j = 0; j < ns; j++) {\n      int32_t u = S[j].v, ok = 1;\n"
+     "      for (int32_t t = 0; t < c && ok; t++) ok = adjacent(rp,",
+     "    for (int64_t j = 0; j < ns; j++) {\n      int32_t u = S[j].v, ok = 1;\n"
+     "      for (int32_t t = 0; t < c && ok; t++) ok = adjacent(rp,", False),
     ("heuristic-increasing-core", "if (a->k != b->k) return a->k > b->k ? -1 : 1;",
      "if (a->k != b->k) return a->k < b->k ? -1 : 1;", False),
     ("heuristic-smaller-degree-first", "if (a->d != b->d) return a->d > b->d ? -1 : 1;",
      "if (a->d != b->d) return a->d < b->d ? -1 : 1;", False),
     ("heuristic-larger-id-first", "return (a->v > b->v) - (a->v < b->v);", "return (a->v < b->v) - (a->v > b->v);", False),
     ("heuristic-skip-at-equal-core", "if (mode == 0 && core[v] < max) continue;", "if (mode == 0 && core[v] <= max) continue;", False),
-    ("heuristic-skips-last-member", "for (int32_t t = 0; t < c && ok; t++)", "for (int32_t t = 0; t + 1 < c && ok; t++)", False),
+    ("heuristic-skips-last-member", "for (int32_t t = 0; t < c && ok; t++) ok = adjacent(rp,",
+     "for (int32_t t = 0; t + 1 < c && ok; t++) ok = adjacent(rp,", False),
     ("heuristic-strict-candidate-filter", "if (core[u] >= T) {", "if (core[u] > T) {", False),
     ("heuristic-mode1-ties-to-largest", "(mode == 1 && c == max && v < best_v)", "(mode == 1 && c == max && v > best_v)", False),
     # Algorithm 2
@@ -49,7 +53,13 @@ C_MUTANTS = [
     ("initialbranch-u-left-out", "    if (!inserted && w > u) { s->P[np++] = u; inserted = 1; }\n",
      "    if (!inserted && w > u) { inserted = 1; }\n", False),
     ("branch-colour-bound-off-by-one", "if (csize + cu <= s->hsize) break;", "if (csize + cu <= s->hsize + 1) break;", False),
-    ("branch-picks-smallest-colour", "if (colors[i] >= colors[at]) at = i;", "if (colors[i] <= colors[at]) at = i;", False),
+    ("branch-picks-smallest-colour",
+     "if (colors[i] >= colors[at]) at = i;\n    int32_t u = idx[at], cu = colors[at];\n"
+     "    for (int32_t i = at; i + 1 < cnt; i++) { idx[i] = idx[i + 1]; colors[i] = colors[i + 1]; }\n"
+     "    cnt--;\n    if (csize + cu <= s->hsize)",
+     "if (colors[i] <= colors[at]) at = i;\n    int32_t u = idx[at], cu = colors[at];\n"
+     "    for (int32_t i = at; i + 1 < cnt; i++) { idx[i] = idx[i + 1]; colors[i] = colors[i + 1]; }\n"
+     "    cnt--;\n    if (csize + cu <= s->hsize)", False),
     ("branch-P-index-as-vertex", "&& alive(s, s->P[w])) pidx[np2++] = w;", "&& alive(s, w)) pidx[np2++] = w;", False),
     ("branch-no-adjacency-filter", "if (s->adj[(int64_t)u * s->np + w] && alive(s, s->P[w]))", "if (alive(s, s->P[w]))", False),
     ("branch-witness-from-P-index", "s->H[i] = s->orig[s->P[s->C[i]]];", "s->H[i] = s->orig[s->C[i]];", False),
@@ -60,6 +70,28 @@ C_MUTANTS = [
     ("adjacency-search-overshoots", "if (ci[mid] < b) lo = mid + 1; else hi = mid;",
      "if (ci[mid] <= b) lo = mid + 1; else hi = mid;", False),
     ("is-clique-skips-a-pair", "for (int32_t j = i + 1; j < k; j++) {", "for (int32_t j = i + 2; j < k; j++) {", False),
+    # the threaded search (Section 4.5)
+    ("threads-heuristic-C-starts-empty", "    C[c++] = v;\n    for (int64_t j = 0; j < ns; j++) {\n      int32_t u = S[j].v, ok = 1;\n"
+     "      for (int32_t t = 0; t < c && ok; t++) ok = adjacent(h->rp,",
+     "    for (int64_t j = 0; j < ns; j++) {\n      int32_t u = S[j].v, ok = 1;\n"
+     "      for (int32_t t = 0; t < c && ok; t++) ok = adjacent(h->rp,", False),
+    ("threads-heuristic-skips-last-member", "for (int32_t t = 0; t < c && ok; t++) ok = adjacent(h->rp,",
+     "for (int32_t t = 0; t + 1 < c && ok; t++) ok = adjacent(h->rp,", False),
+    ("threads-heuristic-stops-at-equal-core", "if (h->core[v] < T) break;", "if (h->core[v] <= T) break;", False),
+    ("threads-prune-strict", "if (K0[order[i]] >= hs) newid", "if (K0[order[i]] > hs) newid", False),
+    ("threads-root-filter-strict", "if (sh->K[sh->oci[e]] >= h) w->P[np++]", "if (sh->K[sh->oci[e]] > h) w->P[np++]", False),
+    ("threads-root-size-test-off-by-one", "if (np + 1 <= h) return;", "if (np + 1 <= h + 1) return;", False),
+    ("threads-adjacency-one-direction", "        w->adj[(int64_t)(b - 1) * np + a] = 1;\n", "", False),
+    ("threads-neighbourhood-core-strict", "if (kn[a] + 1 >= h)", "if (kn[a] + 1 > h)", False),
+    ("threads-kept-count-off-by-one", "if (cnt + 1 <= h) return;", "if (cnt + 1 <= h + 1) return;", False),
+    ("threads-colour-test-without-u", "if (1 + L <= th_best(w)) return;", "if (L <= th_best(w)) return;", False),
+    ("threads-branch-colour-bound-off-by-one", "if (csize + cu <= th_best(w)) break;",
+     "if (csize + cu <= th_best(w) + 1) break;", False),
+    ("threads-branch-no-adjacency-filter", "      if (w->adj[(int64_t)u * w->np + idx[i]]) pidx[np2++] = idx[i];",
+     "      pidx[np2++] = idx[i];", False),
+    ("threads-clique-member-as-index", "w->C[csize] = w->P[u];", "w->C[csize] = u;", False),
+    ("threads-witness-in-new-ids", "sh->H[i] = sh->orig[w->C[i]];", "sh->H[i] = w->C[i];", False),
+    ("threads-incumbent-not-published", "    __atomic_store_n(&sh->best, size, __ATOMIC_RELEASE);\n", "", False),
 ]
 
 PY_MUTANTS = [
@@ -121,8 +153,8 @@ def _c_case(tmp, name, old, new, every):
     so = os.path.join(tmp, name + ".so")
     with open(c, "w") as f:
         f.write(src)
-    subprocess.run(["gcc", "-O1", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", c, "-o", so, "-lm"],
-                   check=True)
+    subprocess.run(["gcc", "-O1", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-pthread", c, "-o", so,
+                    "-lm"], check=True)
     script = textwrap.dedent("""
         import ctypes, sys
         sys.path.insert(0, %r)
