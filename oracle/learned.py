@@ -28,27 +28,52 @@ def bf16_round(x):
     return r.astype(np.uint32).view(np.float32)
 
 
+T = 16  # neighbours that the triangle and colouring features look at
+
+
 def features(g, core):
-    """The six features of every vertex, by their definitions:
-    f0 = log(1+d)/log(1+Dmax), f1 = K/Kmax, f2 = log(1+c)/log(1+Dmax),
-    f3 = max neighbour K / Kmax, f4 = mean neighbour K / Kmax, f5 = c/max(d,1),
-    with c = number of neighbours whose core number is at least K(v)."""
+    """The six features of every vertex, by their definitions.  With d the
+    degree, K = K(v), Kmax = K(G), Dmax the largest degree, c the number of
+    neighbours whose core number is at least K(v), and Q(v) the first
+    min(T, c) of those neighbours in increasing vertex id:
+      f0 = log(1+d)/log(1+Dmax)           degree
+      f1 = K/Kmax                         core number
+      f2 = t/(T(T-1)/2)                   triangle count: t = edges among Q(v)
+      f3 = (chi+1)/(T+1)                  neighbourhood colouring bound: chi =
+                                          colours of the greedy colouring of
+                                          G[Q(v)] in increasing id (0 if Q is
+                                          empty), so chi+1 bounds a clique
+                                          containing v inside Q(v) + v
+      f4 = c/max(d,1),  f5 = log(1+c)/log(1+Dmax)."""
     n = g.n
     deg = np.diff(g.row_ptr).astype(np.float64)
     kmax = float(max(int(core.max()) if n else 0, 1))
     ldmax = np.log1p(float(max(int(deg.max()) if n else 0, 1)))
+    nbsets = [set(g.col_idx[g.row_ptr[v]:g.row_ptr[v + 1]].tolist()) for v in range(n)]
     out = np.zeros((n, F), np.float64)
     for v in range(n):
         nb = g.col_idx[g.row_ptr[v]:g.row_ptr[v + 1]]
-        kn = core[nb].astype(np.float64)
-        c = float(np.sum(kn >= core[v]))
+        qual = nb[core[nb] >= core[v]]
+        c = float(len(qual))
         d = deg[v]
+        Q = qual[:T].tolist()
+        q = len(Q)
+        adj = [[Q[j] in nbsets[Q[i]] for j in range(q)] for i in range(q)]
+        t = sum(1 for i in range(q) for j in range(i + 1, q) if adj[i][j])
+        col = [0] * q
+        for i in range(q):
+            used = {col[j] for j in range(i) if adj[i][j]}
+            k = 1
+            while k in used:
+                k += 1
+            col[i] = k
+        chi = max(col) if q else 0
         out[v, 0] = np.log1p(d) / ldmax
         out[v, 1] = core[v] / kmax
-        out[v, 2] = np.log1p(c) / ldmax
-        out[v, 3] = (kn.max() if d > 0 else 0.0) / kmax
-        out[v, 4] = (kn.mean() if d > 0 else 0.0) / kmax
-        out[v, 5] = c / max(d, 1.0)
+        out[v, 2] = t / (T * (T - 1) / 2)
+        out[v, 3] = (chi + 1) / (T + 1)
+        out[v, 4] = c / max(d, 1.0)
+        out[v, 5] = np.log1p(c) / ldmax
     return out
 
 

@@ -66,37 +66,126 @@ def test_gradient_uses_bf16_weights():
     assert np.allclose(OL.gradient(p, x, y, 2.0, bf16=True), OL.gradient(q, x, y, 2.0, bf16=False))
 
 
+def _f(d, dmax, k, kmax, t, chi, c):
+    """The feature row for the given quantities (the definitions)."""
+    T = OL.T
+    return [np.log1p(d) / np.log1p(dmax), k / kmax, t / (T * (T - 1) / 2), (chi + 1) / (T + 1), c / max(d, 1),
+            np.log1p(c) / np.log1p(dmax)]
+
+
 def test_features_closed_forms():
-    # star: centre 0 with n-1 leaves; every core number is 1
+    # star: centre 0 with n-1 leaves, every core number 1; the leaves are
+    # pairwise non-adjacent, so no triangle and one colour
     n = 9
     g = gg.star(n)
-    K = oracle.core_numbers(g)
-    f = OL.features(g, K)
-    assert np.allclose(f[0], [1.0, 1.0, 1.0, 1.0, 1.0, 1.0])
-    leaf = [np.log1p(1) / np.log1p(n - 1), 1.0, np.log1p(1) / np.log1p(n - 1), 1.0, 1.0, 1.0]
-    assert np.allclose(f[1:], leaf)
+    f = OL.features(g, oracle.core_numbers(g))
+    assert np.allclose(f[0], _f(8, 8, 1, 1, 0, 1, 8))
+    assert np.allclose(f[1:], _f(1, 8, 1, 1, 0, 1, 1))
+    # K_n: Q is the first min(T, n-1) other vertices, all adjacent
+    for n in (5, 17, 20):
+        g = gg.complete(n)
+        f = OL.features(g, oracle.core_numbers(g))
+        q = min(OL.T, n - 1)
+        assert np.allclose(f, _f(n - 1, n - 1, n - 1, n - 1, q * (q - 1) // 2, q, n - 1))
+    # cycles: the two neighbours are adjacent only in C_3
+    g = gg.cycle(3)
+    assert np.allclose(OL.features(g, oracle.core_numbers(g)), _f(2, 2, 2, 2, 1, 2, 2))
+    g = gg.cycle(8)
+    assert np.allclose(OL.features(g, oracle.core_numbers(g)), _f(2, 2, 2, 2, 0, 1, 2))
     # disjoint K4 and K2: Kmax = 3, Dmax = 3
     g = gg.disjoint_cliques([4, 2])
     f = OL.features(g, oracle.core_numbers(g))
-    assert np.allclose(f[0], [1.0, 1.0, 1.0, 1.0, 1.0, 1.0])
-    assert np.allclose(f[4], [np.log1p(1) / np.log1p(3), 1 / 3, np.log1p(1) / np.log1p(3), 1 / 3, 1 / 3, 1.0])
-    # isolated vertex
+    assert np.allclose(f[0], _f(3, 3, 3, 3, 3, 3, 3))
+    assert np.allclose(f[4], _f(1, 3, 1, 3, 0, 1, 1))
+    # isolated vertices: no neighbour, chi = 0
     f = OL.features(gg.empty(3), np.zeros(3, np.int32))
-    assert np.allclose(f, 0.0)
+    assert np.allclose(f, [[0.0, 0.0, 0.0, 1 / (OL.T + 1), 0.0, 0.0]] * 3)
+
+
+def test_features_turan_worked_by_hand():
+    """Turan T(32, 4), parts = id mod 4, 24-regular (every core number 24).
+    Vertex 0's first 16 neighbours are 1 2 3 5 6 7 9 10 11 13 14 15 17 18 19
+    21: parts 1, 2, 3 with 6, 5 and 5 members.  Edges among them join
+    different parts: C(16,2) - C(6,2) - 2 C(5,2) = 120 - 15 - 20 = 85.  The
+    greedy colouring of a complete multipartite graph gives each part one
+    colour: 3 colours."""
+    g = gg.turan(32, 4)
+    f = OL.features(g, oracle.core_numbers(g))
+    assert np.allclose(f[0], _f(24, 24, 24, 24, 85, 3, 24))
+    # vertex 5 (part 1): neighbours 0 2 3 4 6 7 8 10 11 12 14 15 16 18 19 20,
+    # parts 0, 2, 3 with 6, 5, 5 members again
+    assert np.allclose(f[5], _f(24, 24, 24, 24, 85, 3, 24))
+
+
+def test_features_first_T_in_id_order():
+    """Q(v) is the FIRST T qualifying neighbours in id order.  Vertex 0 is
+    joined to 1..20; 1..16 are pairwise adjacent; each of 17..20 is joined to
+    all of 1..16 and to nothing else.  Degrees: 20 (0 and 1..16), 17
+    (17..20); the whole graph is a 17-core and no 18-core exists, so every
+    core number is 17.  Q(0) = 1..16, a clique: 120 edges, 16 colours.  (The
+    last 16 neighbours, 5..20, would give 66 + 48 = 114 edges and 13
+    colours.)  Q(17) = 0..15: again a clique."""
+    src, dst = [], []
+    for u in range(1, 21):
+        src.append(0)
+        dst.append(u)
+    for a in range(1, 17):
+        for b in range(a + 1, 17):
+            src.append(a)
+            dst.append(b)
+        for b in range(17, 21):
+            src.append(a)
+            dst.append(b)
+    g = gg.from_edges(21, src, dst)
+    K = oracle.core_numbers(g)
+    assert np.all(K == 17)
+    f = OL.features(g, K)
+    assert OL.T == 16
+    assert np.allclose(f[0], _f(20, 20, 17, 17, 120, 16, 20))
+    assert np.allclose(f[17], _f(17, 20, 17, 17, 120, 16, 17))
+    assert np.allclose(f[1], _f(20, 20, 17, 17, 120, 16, 20))
 
 
 def test_features_mixed_neighbour_cores():
-    """K4 on {0,1,2,3} with the path 0-4-5 attached: vertex 0 sees core
-    numbers 3, 3, 3, 1, so the maximum, the mean and the count of
-    neighbours at its own core number all differ (Kmax = 3, Dmax = 4)."""
+    """K4 on {0,1,2,3} with the path 0-4-5 attached: vertex 0 (K = 3) keeps
+    its three K4 neighbours (a triangle, three colours) and not vertex 4
+    (K = 1); vertex 4 keeps both neighbours 0 and 5, which are not adjacent
+    (Kmax = 3, Dmax = 4)."""
     g = gg.from_edges(6, [0, 0, 0, 1, 1, 2, 0, 4], [1, 2, 3, 2, 3, 3, 4, 5])
     K = oracle.core_numbers(g)
     assert K.tolist() == [3, 3, 3, 3, 1, 1]
     f = OL.features(g, K)
-    L4 = np.log1p(4)
-    assert np.allclose(f[0], [1.0, 1.0, np.log1p(3) / L4, 1.0, 2.5 / 3, 3 / 4])
-    assert np.allclose(f[4], [np.log1p(2) / L4, 1 / 3, np.log1p(2) / L4, 1.0, 2 / 3, 1.0])
-    assert np.allclose(f[5], [np.log1p(1) / L4, 1 / 3, np.log1p(1) / L4, 1 / 3, 1 / 3, 1.0])
+    assert np.allclose(f[0], _f(4, 4, 3, 3, 3, 3, 3))
+    assert np.allclose(f[1], _f(3, 4, 3, 3, 3, 3, 3))
+    assert np.allclose(f[4], _f(2, 4, 1, 3, 0, 1, 2))
+    assert np.allclose(f[5], _f(1, 4, 1, 3, 0, 1, 1))
+
+
+def test_features_core_filter_before_truncation():
+    """Q(v) takes the first T neighbours among those with K(u) >= K(v), not
+    the first T neighbours: vertex 0 is joined to T leaves (ids 1..T) and is
+    in a (T+1)-clique with ids T+1..2T.  The leaves come first in id order
+    but have core number 1 < K(0) = T, so Q(0) is the T clique members (all
+    adjacent, T colours)."""
+    T = OL.T
+    # vertices 1..T: independent, each joined to 0; vertices T+1..2T: K_T with 0
+    src, dst = [], []
+    for u in range(1, T + 1):
+        src.append(0)
+        dst.append(u)
+    clique = [0] + list(range(T + 1, 2 * T + 1))
+    for a in range(len(clique)):
+        for b in range(a + 1, len(clique)):
+            src.append(clique[a])
+            dst.append(clique[b])
+    g = gg.from_edges(2 * T + 1, src, dst)
+    K = oracle.core_numbers(g)
+    assert K[0] == T and K[1] == 1 and K[T + 1] == T
+    f = OL.features(g, K)
+    # vertex 0: degree 2T, c = T (the clique members), Q = the clique members
+    assert np.allclose(f[0], _f(2 * T, 2 * T, T, T, T * (T - 1) // 2, T, T))
+    # a leaf (K = 1): its one neighbour 0 has K >= 1
+    assert np.allclose(f[1], _f(1, 2 * T, 1, T, 0, 1, 1))
 
 
 def test_adam_closed_forms():

@@ -97,12 +97,17 @@ C_MUTANTS = [
 PY_MUTANTS = [
     ("bf16-truncates", "(a + 0x7FFF + ((a >> 16) & 1)) >> 16", "a >> 16", False),
     ("bf16-ties-away", "(a + 0x7FFF + ((a >> 16) & 1)) >> 16", "(a + 0x8000) >> 16", False),
-    ("features-min-neighbour-core", "out[v, 3] = (kn.max() if d > 0 else 0.0) / kmax",
-     "out[v, 3] = (kn.min() if d > 0 else 0.0) / kmax", False),
-    ("features-max-for-mean", "out[v, 4] = (kn.mean() if d > 0 else 0.0) / kmax",
-     "out[v, 4] = (kn.max() if d > 0 else 0.0) / kmax", False),
-    ("features-strict-core-count", "c = float(np.sum(kn >= core[v]))", "c = float(np.sum(kn > core[v]))", False),
-    ("features-degree-for-count", "out[v, 2] = np.log1p(c) / ldmax", "out[v, 2] = np.log1p(d) / ldmax", False),
+    ("features-strict-core-filter", "qual = nb[core[nb] >= core[v]]", "qual = nb[core[nb] > core[v]]", False),
+    ("features-degree-for-count", "out[v, 5] = np.log1p(c) / ldmax", "out[v, 5] = np.log1p(d) / ldmax", False),
+    ("features-Q-without-core-filter", "Q = qual[:T].tolist()", "Q = nb[:T].tolist()", False),
+    ("features-Q-last-neighbours", "Q = qual[:T].tolist()", "Q = qual[-T:].tolist()", False),
+    ("features-triangles-counted-twice", "t = sum(1 for i in range(q) for j in range(i + 1, q) if adj[i][j])",
+     "t = sum(1 for i in range(q) for j in range(q) if i != j and adj[i][j])", False),
+    ("features-colouring-ignores-edges", "used = {col[j] for j in range(i) if adj[i][j]}",
+     "used = {col[j] for j in range(i) if not adj[i][j]}", False),
+    ("features-bound-without-v", "out[v, 3] = (chi + 1) / (T + 1)", "out[v, 3] = chi / (T + 1)", False),
+    ("features-density-not-count", "out[v, 2] = t / (T * (T - 1) / 2)",
+     "out[v, 2] = t / max(q * (q - 1) / 2, 1)", False),
     ("w1-transposed", "W1 = w[OFF_W1:OFF_B1].reshape(H, F)", "W1 = w[OFF_W1:OFF_B1].reshape(F, H).T", False),
     ("w2-transposed", "W2 = w[OFF_W2:OFF_B2].reshape(H, H)", "W2 = w[OFF_W2:OFF_B2].reshape(H, H).T", False),
     ("biases-rounded-to-bf16", "    b1 = p[OFF_B1:OFF_W2]\n", "    b1 = w[OFF_B1:OFF_W2]\n", False),
