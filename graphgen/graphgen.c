@@ -312,25 +312,43 @@ static void sort_body(void *p, int64_t lo, int64_t hi) {
 /* Symmetrise, drop self-loops and duplicates, sort rows ascending.
  * row_ptr has n+1 entries; col must hold 2*m entries (the result uses the
  * first row_ptr[n] of them).  Returns row_ptr[n] (the CSR entry count). */
+/* Endpoint counts and the scatter into rows run in parallel with atomic
+ * counters: the order of entries inside a row then depends on timing, but
+ * every row is sorted and deduplicated afterwards, so the CSR does not. */
+typedef struct { int64_t n; const int32_t *src, *dst; int64_t *cnt; int32_t *col; } edge_arg;
+
+static void count_body(void *p, int64_t lo, int64_t hi) {
+  edge_arg *a = (edge_arg *)p;
+  for (int64_t e = lo; e < hi; e++) {
+    int32_t u = a->src[e], v = a->dst[e];
+    if (u == v || u < 0 || v < 0 || u >= a->n || v >= a->n) continue;
+    __atomic_fetch_add(&a->cnt[u], 1, __ATOMIC_RELAXED);
+    __atomic_fetch_add(&a->cnt[v], 1, __ATOMIC_RELAXED);
+  }
+}
+
+static void scatter_body(void *p, int64_t lo, int64_t hi) {
+  edge_arg *a = (edge_arg *)p;
+  for (int64_t e = lo; e < hi; e++) {
+    int32_t u = a->src[e], v = a->dst[e];
+    if (u == v || u < 0 || v < 0 || u >= a->n || v >= a->n) continue;
+    a->col[__atomic_fetch_add(&a->cnt[u], 1, __ATOMIC_RELAXED)] = v;
+    a->col[__atomic_fetch_add(&a->cnt[v], 1, __ATOMIC_RELAXED)] = u;
+  }
+}
+
 int64_t gg_csr_from_edges(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, int threads,
                           int64_t *row_ptr, int32_t *col) {
   int64_t *cnt = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
   if (!cnt) return -3;
-  for (int64_t e = 0; e < m; e++) {
-    int32_t u = src[e], v = dst[e];
-    if (u == v || u < 0 || v < 0 || u >= n || v >= n) continue;
-    cnt[u]++; cnt[v]++;
-  }
+  edge_arg ea = {n, src, dst, cnt, col};
+  par_for(threads, m, count_body, &ea);
   int64_t *rp = (int64_t *)malloc(((size_t)n + 1) * sizeof(int64_t));
   if (!rp) { free(cnt); return -3; }
   rp[0] = 0;
   for (int64_t v = 0; v < n; v++) rp[v + 1] = rp[v] + cnt[v];
   for (int64_t v = 0; v < n; v++) cnt[v] = rp[v];
-  for (int64_t e = 0; e < m; e++) {
-    int32_t u = src[e], v = dst[e];
-    if (u == v || u < 0 || v < 0 || u >= n || v >= n) continue;
-    col[cnt[u]++] = v; col[cnt[v]++] = u;
-  }
+  par_for(threads, m, scatter_body, &ea);
   sort_arg sa = {rp, col, cnt};
   par_for(threads, n, sort_body, &sa);
   /* compact rows in place (rows only move left) */

@@ -57,6 +57,7 @@ extern "C" {
                           they must stay valid and unchanged until mc_free */
 
 typedef struct mc_graph mc_graph;
+typedef struct mc_mlp mc_mlp; /* the learned ordering's scoring network (below) */
 
 /* Search options.  Zero-initialise for the defaults. */
 typedef struct {
@@ -105,6 +106,21 @@ typedef struct {
    * rest of its tree to the task queue (a block worker: four times as
    * many); 0 = default (4096) */
   int32_t split_nodes;
+  /* The learned form (an extension; the paper has no learned part): a
+   * scoring network from mc_mlp_create, or NULL.  With a network, the solve
+   * first runs the warm-up part of Algorithm 1, then scores only the
+   * vertices that can still be in a clique larger than its bound (K(v) >=
+   * bound; features and network fused in one kernel, nothing written for
+   * the others), grows the `seeds` best-scored of them first (for a batch:
+   * of every graph; 0 = 64 for one graph, 2 per graph for a batch; at most
+   * 1,024 for one graph), each by Algorithm 1's greedy step with the next
+   * member chosen by score, and then the rest of Algorithm 1 (heuristic 0)
+   * or nothing more (heuristic 3; other heuristic values are refused).
+   * Roots stay in degeneracy order unless ordering = 1, which orders them by
+   * these scores (scores must be NULL).  omega is exact whatever the
+   * network predicts.  The network must not be freed or changed while a
+   * captured solve (graph = 1) that uses it can be replayed. */
+  const mc_mlp *mlp;
 } mc_options;
 
 /* Per-call statistics (all times in milliseconds, CUDA events). */
@@ -129,6 +145,10 @@ typedef struct {
   int64_t heuristic_tests;     /* adjacency tests of its greedy steps */
   int64_t heuristic_row_entries; /* CSR row entries it read (gathers, merges) */
   int32_t max_core, heuristic_size, omega, verified;
+  int64_t prune_row_entries;   /* CSR row entries the pruning read (the kept vertices' rows) */
+  double ms_learned;           /* of ms_heuristic: scoring the candidates and picking the seeds
+                                  (the learned form only) */
+  int64_t learned_scored;      /* vertices the learned form scored */
 } mc_stats;
 
 /* ------------------------------------------------------------ graphs --- */
@@ -242,11 +262,12 @@ int mc_core_numbers_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *co
  * the mean binary cross-entropy of the logit, positives weighted by
  * pos_weight.  Parameters are a flat float array of mc_mlp_num_params()
  * entries: W1[64][6], b1[64], W2[64][64], b2[64], w3[64], b3. */
-typedef struct mc_mlp mc_mlp;
-
-/* Per-vertex features (n x 6 float, row-major, host or device): log1p(deg)
- * and core-based neighbourhood statistics normalised to [0, 1] (see
- * learned.cu).  Computes the core numbers if needed. */
+/* Per-vertex features (n x 6 float, row-major, host or device), each in
+ * [0, 1]: degree, core number, a triangle count and a neighbourhood
+ * colouring bound over the first 16 neighbours of core number >= K(v), and
+ * the count of those neighbours (as a fraction of the degree and log-scaled);
+ * the exact definitions are in learned.cu.  Computes the core numbers if
+ * needed. */
 int mc_features(mc_graph *g, float *feat_out);
 /* Create a network with He-uniform weights from `seed` on `cuda_stream`. */
 int mc_mlp_create(uint64_t seed, void *cuda_stream, mc_mlp **out);

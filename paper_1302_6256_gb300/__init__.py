@@ -47,7 +47,8 @@ class Options(ctypes.Structure):
                 ("heuristic", ctypes.c_int32), ("warp_max", ctypes.c_int32),
                 ("spin_limit", ctypes.c_int64), ("scores", ctypes.c_void_p),
                 ("seeds", ctypes.c_int32), ("graph", ctypes.c_int32),
-                ("no_split", ctypes.c_int32), ("split_nodes", ctypes.c_int32)]
+                ("no_split", ctypes.c_int32), ("split_nodes", ctypes.c_int32),
+                ("mlp", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -64,7 +65,9 @@ class Stats(ctypes.Structure):
                 ("tasks", ctypes.c_int64), ("heuristic_grows", ctypes.c_int64),
                 ("heuristic_tests", ctypes.c_int64), ("heuristic_row_entries", ctypes.c_int64),
                 ("max_core", ctypes.c_int32), ("heuristic_size", ctypes.c_int32),
-                ("omega", ctypes.c_int32), ("verified", ctypes.c_int32)]
+                ("omega", ctypes.c_int32), ("verified", ctypes.c_int32),
+                ("prune_row_entries", ctypes.c_int64), ("ms_learned", ctypes.c_double),
+                ("learned_scored", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -307,9 +310,13 @@ def _scores_arg(scores, n):
 
 
 def _options(n, ordering=0, no_neigh_cores=False, heuristic=0, warp_max=0, spin_limit=0, scores=None, seeds=0,
-             graph=False, no_split=False, split_nodes=0):
+             graph=False, no_split=False, split_nodes=0, mlp=None):
     scores = _scores_arg(scores, n)
     o = Options()
+    if mlp is not None:
+        if not isinstance(mlp, MLP):
+            raise TypeError("mlp must be an MLP handle")
+        o.mlp = mlp._h.value
     o.split_nodes = split_nodes
     o.graph = 1 if graph else 0
     o.no_split = 1 if no_split else 0
@@ -321,6 +328,7 @@ def _options(n, ordering=0, no_neigh_cores=False, heuristic=0, warp_max=0, spin_
     sp, keep = _ptr(scores)
     o.scores = sp
     o.seeds = seeds
+    o._mlp_ref = mlp  # keeps the network alive as long as the options
     return o, keep
 
 

@@ -23,8 +23,13 @@ def _gpu_name() -> str:
         return "unknown"
 
 
+# Version of the tuner's coordinate list: cached results from an older list
+# are tuned again, so a coordinate added later is never hidden by the cache.
+COORDS = "v3:warp_max,split,heuristic,layout,graph"
+
+
 def tuned(g, key: str, repeats: int = 2, cache: str = CACHE, **base):
-    ck = "%s|%s" % (_gpu_name(), key)
+    ck = "%s|%s|%s" % (COORDS, _gpu_name(), key)
     data = {}
     if os.path.exists(cache):
         try:

@@ -290,7 +290,8 @@ static int check_options(const mc_options *opt, mc_options *o) {
       o->seeds < 0 || o->graph < 0 || o->graph > 1 || o->no_split < 0 || o->no_split > 1 ||
       o->split_nodes < 0)
     return MC_ERR_ARG;
-  if (o->ordering == 1 && !o->scores) return MC_ERR_ARG;
+  if (o->ordering == 1 && !o->scores && !o->mlp) return MC_ERR_ARG;
+  if (o->mlp && (o->scores || (o->heuristic != 0 && o->heuristic != 3) || o->seeds > 1024)) return MC_ERR_ARG;
   return MC_OK;
 }
 
@@ -333,8 +334,29 @@ static int enqueue_solve(mc_graph *g, const mc_options &o, Pruned *pg, SearchCou
     }
   }
   g->heur_ran = o.heuristic != 2 && g->n > 0;
-  if (g->heur_ran)
+  g->learned_ran = o.mlp != nullptr && g->n > 0;
+  if (g->learned_ran) {
+    // The learned form: the warm-up part of Algorithm 1 sets a bound, only
+    // the vertices that can still beat it are scored, and the best-scored
+    // of them are grown first; then the rest of Algorithm 1 (heuristic 0)
+    // or nothing more (heuristic 3).
+    int64_t grown = 0;
+    MC_TRY(launch_heuristic(g, 0, spin, nullptr, 0, nullptr, true, 0, -1, &grown));
+    MC_TRY(record_event(g, 13));
+    MC_TRY(ws_get(g, "ln.score", g->n * sizeof(float), &p));
+    float *sc = (float *)p;
+    MC_TRY(learned_scores(g, o.mlp, sc));
+    const int32_t per = o.seeds > 0 ? o.seeds : (g->count > 1 ? 2 : 64);
+    nseeds = g->count > 1 ? (int64_t)per * g->count : per;
+    MC_TRY(ws_get(g, "cp.seeds", (nseeds + 1) * sizeof(int32_t), &p));
+    int32_t *seeds = (int32_t *)p;
+    MC_TRY(learned_seeds(g, sc, per, seeds));
+    MC_TRY(record_event(g, 14));
+    MC_TRY(launch_heuristic(g, 0, spin, seeds, nseeds, sc, o.heuristic == 3, grown, 0, nullptr));
+    d_scores = sc;  // ordering = 1 orders the roots by these scores
+  } else if (g->heur_ran) {
     MC_TRY(launch_heuristic(g, o.heuristic == 3 ? 0 : o.heuristic, spin, d_seeds, nseeds, d_scores, o.heuristic == 3));
+  }
   MC_TRY(record_event(g, 2));
   int32_t *h_heur = (int32_t *)((char *)g->h_small + 1024);
   MC_CUDA_TRY(cudaMemcpyAsync(h_heur, g->best, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
@@ -365,6 +387,12 @@ static int finish_solve(mc_graph *g, Pruned *pg, SearchCounters *sc, const int32
   st->ms_search = elapsed(g->ev[3], g->ev[4]);
   st->ms_verify = elapsed(g->ev[4], g->ev[5]);
   st->ms_total = elapsed(g->ev[0], g->ev[5]);
+  if (g->learned_ran) {
+    st->ms_learned = elapsed(g->ev[13], g->ev[14]);
+    auto it = g->ws.find("ln.ctl");
+    if (it != g->ws.end() && it->second.p)
+      MC_CUDA_TRY(cudaMemcpy(&st->learned_scored, it->second.p, sizeof(int64_t), cudaMemcpyDeviceToHost));
+  }
   if (g->n > 0) {
     st->ms_search_block = elapsed(g->ev[8], g->ev[9]);
     st->ms_search_big = elapsed(g->ev[9], g->ev[10]);
@@ -376,6 +404,7 @@ static int finish_solve(mc_graph *g, Pruned *pg, SearchCounters *sc, const int32
     st->pruned_n = pg->n;
     st->pruned_arcs = pg->arcs;
     st->roots = pg->nroots_small + pg->nroots_block + pg->nroots_big;
+    st->prune_row_entries = pg->row_entries;
   }
   if (g->n > 0 && sc->d_counters) {
     MC_TRY(read_search_counters(g, sc));
@@ -427,6 +456,7 @@ static uint64_t options_key(const mc_options &o) {
   mix((uint64_t)o.seeds);
   mix((uint64_t)o.no_split);
   mix((uint64_t)o.split_nodes);
+  mix((uint64_t)(uintptr_t)o.mlp);
   return k;
 }
 

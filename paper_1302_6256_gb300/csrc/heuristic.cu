@@ -77,6 +77,9 @@ struct HA {
   int32_t count;
   int64_t max_graph_n;
   int interleave;
+  // positions of the visiting order (after the seeds) grown by an earlier
+  // launch of the same solve: position i >= nseeds maps to i - nseeds + skip
+  int64_t skip;
 };
 
 struct Key {
@@ -248,13 +251,16 @@ __device__ __forceinline__ bool pick_vertex(const HA &a, int64_t i, int *v) {
     *v = a.list[i];
   } else if (i < a.nseeds) {
     *v = a.seeds[i];
+    return *v >= 0;  // an empty seed slot (a graph with fewer candidates)
   } else if (a.interleave) {
-    const int64_t r = i - a.nseeds, gi = r % a.count, j = r / a.count;
+    const int64_t r = i - a.nseeds + a.skip, gi = r % a.count, j = r / a.count;
     const int64_t v0 = a.voff[gi], v1 = a.voff[gi + 1];
     if (j >= v1 - v0) return false;
     *v = a.order[v1 - 1 - j];
   } else {
-    *v = a.order[a.n - 1 - (i - a.nseeds)];
+    const int64_t r = i - a.nseeds + a.skip;
+    if (r >= a.n) return false;
+    *v = a.order[a.n - 1 - r];
   }
   return true;
 }
@@ -546,7 +552,8 @@ __global__ void heuristic_finalize_kernel(HA a, int32_t ngraphs) {
 }  // namespace
 
 int launch_heuristic(mc_graph *g, int mode, long long spin_limit, const int32_t *seeds, int64_t nseeds,
-                     const float *scores, bool warm_only) {
+                     const float *scores, bool warm_only, int64_t skip, int64_t warm_top, int64_t *grown_top) {
+  if (grown_top) *grown_top = 0;
   if (g->n == 0) return MC_OK;
   if (warm_only && mode != 0) return MC_ERR_ARG;  // the deterministic form needs every start vertex
   void *p;
@@ -614,22 +621,31 @@ int launch_heuristic(mc_graph *g, int mode, long long spin_limit, const int32_t 
   a.count = g->count;
   a.max_graph_n = g->max_graph_n;
   a.interleave = (g->count > 1 && g->max_graph_n <= kBatchPeelCap) ? 1 : 0;
-  const int64_t total = a.interleave ? (int64_t)g->count * g->max_graph_n + a.nseeds : g->n + a.nseeds;
-  // A warm-up launch grows the first kWarm start vertices (the seeds and the
-  // largest core numbers), each with a whole block, so the shared maximum is
-  // already high when the warps start and prunes their candidate sets.
-  const int64_t warm = std::min<int64_t>(total, kWarm);
+  a.skip = skip;
+  const int64_t order_len = a.interleave ? (int64_t)g->count * g->max_graph_n : g->n;
+  const int64_t total = std::max<int64_t>(order_len - skip, 0) + a.nseeds;
+  // The warm-up part: the seeds, then the first positions of the visiting
+  // order (the largest core numbers; for an interleaved batch, each graph's
+  // highest vertex), kWarm of them by default.  Its first kWarm positions
+  // are grown with a whole block each, so the shared maximum is already high
+  // when the warps start and prunes their candidate sets.
+  const int64_t top = warm_top >= 0 ? warm_top : (a.interleave ? std::max<int64_t>(kWarm, g->count) : kWarm);
+  const int64_t warm_end = std::min<int64_t>(total, a.nseeds + top);
+  const int64_t warm = std::min<int64_t>(warm_end, kWarm);
+  if (grown_top) *grown_top = std::max<int64_t>(warm_end - a.nseeds, 0);
   a.begin = 0;
   a.limit = warm;
   a.cand_stride = full;
-  heuristic_warm_kernel<<<(int)warm_blocks, kWT, 0, g->stream>>>(a);
-  g_launches++;
-  MC_CUDA_TRY(cudaGetLastError());
-  if (warm_only) return MC_OK;
+  if (warm > 0) {
+    heuristic_warm_kernel<<<(int)warm_blocks, kWT, 0, g->stream>>>(a);
+    g_launches++;
+    MC_CUDA_TRY(cudaGetLastError());
+  }
   a.cand_stride = cap_s;
-  if (warm < total) {
+  const int64_t main_end = warm_only ? warm_end : total;
+  if (warm < main_end) {
     a.begin = warm;
-    a.limit = total;
+    a.limit = main_end;
     a.next = next + 2;
     heuristic_kernel<<<(int)((warps_s * 32 + kHT - 1) / kHT), kHT, 0, g->stream>>>(a);
     g_launches++;
@@ -640,7 +656,7 @@ int launch_heuristic(mc_graph *g, int mode, long long spin_limit, const int32_t 
   a.cand_stride = full;
   a.cap = full;
   const int blocks_b = (int)((warps_b * 32 + kHT - 1) / kHT);
-  if (two) {
+  if (two && warm < main_end) {
     a.list = defer;
     a.nlist = ndefer;
     a.next = next + 1;

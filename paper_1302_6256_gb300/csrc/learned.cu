@@ -4,11 +4,16 @@
 // stays exact whatever the network predicts.
 //
 // Features of vertex v (d = degree, K = core number, Kmax = K(G), Dmax =
-// maximum degree, c = number of neighbours with K >= K(v)):
-//   f0 = log1p(d) / log1p(Dmax)        f3 = max_{u in N(v)} K(u) / Kmax
-//   f1 = K(v) / Kmax                   f4 = mean_{u in N(v)} K(u) / Kmax
-//   f2 = log1p(c) / log1p(Dmax)        f5 = c / max(d, 1)
-// All are one pass over the CSR (warp per vertex).
+// maximum degree, c = number of neighbours with K >= K(v), Q = the first
+// min(16, c) of those neighbours in increasing id):
+//   f0 = log1p(d) / log1p(Dmax)        f3 = (chi + 1) / 17, chi = colours of
+//   f1 = K(v) / Kmax                        the greedy colouring of G[Q] in
+//   f2 = t / 120, t = edges among Q         increasing id (a bound on a
+//                                           clique through v inside Q + v)
+//   f4 = c / max(d, 1)                 f5 = log1p(c) / log1p(Dmax)
+// One warp per vertex: a coalesced pass over the row (c and Q), then the
+// 120 pairs of Q tested by binary search in the shorter row, then the
+// colouring with one colour class per lane.
 //
 // Parameters, flat fp32 (4673): W1[64][6], b1[64], W2[64][64], b2[64],
 // w3[64], b3.  Loss: binary cross-entropy on the logit s with weight
@@ -59,37 +64,186 @@ __host__ __device__ __forceinline__ uint16_t f32_to_bf16(float f) {
   return (uint16_t)(r >> 16);
 }
 
-__global__ void features_kernel(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                                const int32_t *__restrict__ core, float kmax, float ldmax, float *__restrict__ f) {
+constexpr int kQ = 16;  // neighbours of the triangle and colouring features
+constexpr int64_t kScanRow = 1024;  // rows up to this length are read whole
+
+// per-warp scratch of vertex_features
+struct FeatScratch {
+  int q[kQ];
+  uint32_t adj[kQ];
+};
+
+// The six features of vertex v, computed by one warp (all lanes call; every
+// lane returns them).
+__device__ void vertex_features(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                const int32_t *__restrict__ core, float kmax, float ldmax, int64_t v,
+                                FeatScratch &S, float f[kF]) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int kv = core[v];
+  const int64_t e0 = rp[v], e1 = rp[v + 1];
+  int c = 0;
+  for (int64_t eb = e0; eb < e1; eb += 32) {
+    const int64_t e = eb + lane;
+    int u = -1;
+    bool ok = false;
+    if (e < e1) {
+      u = ci[e];
+      ok = core[u] >= kv;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, ok);
+    if (ok) {
+      const int pos = c + __popc(m & lt);
+      if (pos < kQ) S.q[pos] = u;
+    }
+    c += __popc(m);
+  }
+  if (lane < kQ) S.adj[lane] = 0u;
+  __syncwarp();
+  const int q = min(c, kQ);
+  // G[Q]: the warp's four groups of eight lanes take one member's row each.
+  // A short row is read whole (coalesced) and each entry looked up in Q,
+  // which is sorted (row order); in a long row each later member of Q is
+  // found by binary search.  Either way bit j of adj[i] is set for every
+  // member j > i adjacent to member i.
+  const int grp = lane >> 3, gl = lane & 7;
+  for (int i = grp; i < q; i += 4) {
+    const int x = S.q[i];
+    const int64_t r0 = rp[x], r1 = rp[x + 1];
+    uint32_t bits = 0u;
+    if (r1 - r0 <= kScanRow) {
+      for (int64_t e = r0 + gl; e < r1; e += 8) {
+        const int y = ci[e];
+        int lo = i + 1, hi = q;  // members after i: ids above x
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (S.q[mid] < y) lo = mid + 1; else hi = mid;
+        }
+        if (lo < q && S.q[lo] == y) bits |= 1u << lo;
+      }
+    } else {
+      for (int j = i + 1 + gl; j < q; j += 8) {
+        const int y = S.q[j];
+        int64_t lo = r0, hi = r1;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi) >> 1;
+          if (ci[mid] < y) lo = mid + 1; else hi = mid;
+        }
+        if (lo < r1 && ci[lo] == y) bits |= 1u << j;
+      }
+    }
+    if (bits) atomicOr(&S.adj[i], bits);
+  }
+  __syncwarp();
+  // mirror the upper triangle: lane j gathers bit j of every row above it
+  uint32_t low = 0u;
+  if (lane < q)
+    for (int i = 0; i < lane; i++) low |= ((S.adj[i] >> lane) & 1u) << i;
+  __syncwarp();
+  if (lane < q) S.adj[lane] |= low;
+  __syncwarp();
+  const uint32_t row = lane < q ? S.adj[lane] : 0u;
+  const int t = dev::warp_sum(__popc(row)) / 2;
+  // greedy colouring in index order: lane k holds colour class k; vertex i
+  // joins the first class with none of its neighbours
+  uint32_t cls = 0u;
+  for (int i = 0; i < q; i++) {
+    const uint32_t ai = __shfl_sync(0xffffffffu, row, i);
+    const unsigned clash = __ballot_sync(0xffffffffu, (cls & ai) != 0u);
+    const int k = __ffs(~clash) - 1;
+    if (lane == k) cls |= 1u << i;
+  }
+  const int chi = __popc(__ballot_sync(0xffffffffu, cls != 0u));
+  const float d = (float)(e1 - e0);
+  f[0] = log1pf(d) / ldmax;
+  f[1] = (float)kv / kmax;
+  f[2] = (float)t / (float)(kQ * (kQ - 1) / 2);
+  f[3] = (float)(chi + 1) / (float)(kQ + 1);
+  f[4] = (float)c / fmaxf(d, 1.f);
+  f[5] = log1pf((float)c) / ldmax;
+}
+
+// features of every vertex (list == nullptr) or of list[0 .. *count)
+__global__ void __launch_bounds__(256) features_kernel(int64_t n, const int32_t *__restrict__ list,
+                                                       const int64_t *__restrict__ count,
+                                                       const int64_t *__restrict__ rp,
+                                                       const int32_t *__restrict__ ci,
+                                                       const int32_t *__restrict__ core, float kmax, float ldmax,
+                                                       float *__restrict__ f) {
+  __shared__ FeatScratch fs[8];
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t v = w0; v < n; v += nw) {
-    const int kv = core[v];
-    const int64_t e0 = rp[v], e1 = rp[v + 1];
-    int c = 0, mx = 0;
-    long long sum = 0;
-    for (int64_t e = e0 + lane; e < e1; e += 32) {
-      const int k = core[ci[e]];
-      c += k >= kv ? 1 : 0;
-      mx = max(mx, k);
-      sum += k;
-    }
-    c = dev::warp_sum(c);
-    mx = dev::warp_max(mx);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  const int64_t total = list ? *count : n;
+  for (int64_t r = w0; r < total; r += nw) {
+    const int64_t v = list ? list[r] : r;
+    float x[kF];
+    vertex_features(rp, ci, core, kmax, ldmax, v, fs[threadIdx.x >> 5], x);
     if (lane == 0) {
-      const float d = (float)(e1 - e0);
-      float *o = f + v * kF;
-      o[0] = log1pf(d) / ldmax;
-      o[1] = (float)kv / kmax;
-      o[2] = log1pf((float)c) / ldmax;
-      o[3] = (float)mx / kmax;
-      o[4] = d > 0 ? (float)((double)sum / (double)d) / kmax : 0.f;
-      o[5] = (float)c / fmaxf(d, 1.f);
+#pragma unroll
+      for (int i = 0; i < kF; i++) f[v * kF + i] = x[i];
     }
   }
+}
+
+// The network in shared memory, laid out for one warp per row: lane j owns
+// hidden units j and j + 32; the first two layers are stored input-major so
+// that a warp's reads of one input's weights are consecutive words.
+struct MlpSmem {
+  float w1t[kF][kH];  // w1t[i][j] = W1[j][i]
+  float b1[kH];
+  float w2t[kH][kH];  // w2t[k][j] = W2[j][k]
+  float b2[kH];
+  float w3[kH];
+  float b3;
+};
+
+__device__ void load_mlp(const uint16_t *__restrict__ wbf, const float *__restrict__ master, MlpSmem &S) {
+  for (int e = threadIdx.x; e < kH * kF; e += blockDim.x) {
+    const int j = e / kF, i = e % kF;
+    S.w1t[i][j] = bf16_to_f32(wbf[kOffW1 + e]);
+  }
+  for (int e = threadIdx.x; e < kH * kH; e += blockDim.x) {
+    const int j = e / kH, k = e % kH;
+    S.w2t[k][j] = bf16_to_f32(wbf[kOffW2 + e]);
+  }
+  for (int j = threadIdx.x; j < kH; j += blockDim.x) {
+    S.b1[j] = master[kOffB1 + j];  // biases stay fp32
+    S.b2[j] = master[kOffB2 + j];
+    S.w3[j] = bf16_to_f32(wbf[kOffW3 + j]);
+  }
+  if (threadIdx.x == 0) S.b3 = master[kOffB3];
+  __syncthreads();
+}
+
+// The logit of one row x (every lane holds x), by one warp.
+__device__ __forceinline__ float mlp_logit_warp(const MlpSmem &S, const float x[kF]) {
+  const int lane = threadIdx.x & 31;
+  float h0 = S.b1[lane], h1 = S.b1[lane + 32];
+#pragma unroll
+  for (int i = 0; i < kF; i++) {
+    h0 = fmaf(S.w1t[i][lane], x[i], h0);
+    h1 = fmaf(S.w1t[i][lane + 32], x[i], h1);
+  }
+  h0 = fmaxf(h0, 0.f);
+  h1 = fmaxf(h1, 0.f);
+  float z0 = S.b2[lane], z1 = S.b2[lane + 32];
+#pragma unroll 8
+  for (int k = 0; k < 32; k++) {
+    const float hk = __shfl_sync(0xffffffffu, h0, k);
+    z0 = fmaf(S.w2t[k][lane], hk, z0);
+    z1 = fmaf(S.w2t[k][lane + 32], hk, z1);
+  }
+#pragma unroll 8
+  for (int k = 0; k < 32; k++) {
+    const float hk = __shfl_sync(0xffffffffu, h1, k);
+    z0 = fmaf(S.w2t[k + 32][lane], hk, z0);
+    z1 = fmaf(S.w2t[k + 32][lane + 32], hk, z1);
+  }
+  float sum = S.w3[lane] * fmaxf(z0, 0.f) + S.w3[lane + 32] * fmaxf(z1, 0.f);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  return sum + S.b3;
 }
 
 // weights into shared memory as fp32 (from the bf16 copies)
@@ -102,35 +256,45 @@ __device__ __forceinline__ void load_weights(const uint16_t *__restrict__ wbf, c
   __syncthreads();
 }
 
-// forward for one row: returns the logit; h1 in registers
-__device__ __forceinline__ float forward_row(const float *sw, const float *x, float *h1) {
-#pragma unroll
-  for (int j = 0; j < kH; j++) {
-    float z = sw[kOffB1 + j];
-#pragma unroll
-    for (int i = 0; i < kF; i++) z = fmaf(sw[kOffW1 + j * kF + i], x[i], z);
-    h1[j] = fmaxf(z, 0.f);
-  }
-  float s = sw[kOffB3];
-  for (int j = 0; j < kH; j++) {
-    float z = sw[kOffB2 + j];
-#pragma unroll
-    for (int k = 0; k < kH; k++) z = fmaf(sw[kOffW2 + j * kH + k], h1[k], z);
-    s = fmaf(sw[kOffW3 + j], fmaxf(z, 0.f), s);
-  }
-  return s;
-}
-
+// logits of n feature rows, one warp per row
 __global__ void __launch_bounds__(256) forward_kernel(int64_t n, const float *__restrict__ feat,
                                                       const uint16_t *__restrict__ wbf,
                                                       const float *__restrict__ master, float *__restrict__ out) {
-  __shared__ float sw[kParams];
-  load_weights(wbf, master, sw);
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-    float x[kF], h1[kH];
+  __shared__ MlpSmem S;
+  load_mlp(wbf, master, S);
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = w0; r < n; r += nw) {
+    const float mine = lane < kF ? feat[r * kF + lane] : 0.f;
+    float x[kF];
 #pragma unroll
-    for (int i = 0; i < kF; i++) x[i] = feat[r * kF + i];
-    out[r] = forward_row(sw, x, h1);
+    for (int i = 0; i < kF; i++) x[i] = __shfl_sync(0xffffffffu, mine, i);
+    const float s = mlp_logit_warp(S, x);
+    if (lane == 0) out[r] = s;
+  }
+}
+
+// Learned scores of list[0 .. *count): features and logit fused, one warp
+// per vertex; the n x 6 feature rows never reach memory.
+__global__ void __launch_bounds__(256) score_kernel(const int32_t *__restrict__ list, const int64_t *__restrict__ count,
+                                                    const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                                    const int32_t *__restrict__ core, float kmax, float ldmax,
+                                                    const uint16_t *__restrict__ wbf, const float *__restrict__ master,
+                                                    float *__restrict__ score) {
+  __shared__ MlpSmem S;
+  __shared__ FeatScratch fs[8];
+  load_mlp(wbf, master, S);
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t total = *count;
+  for (int64_t r = w0; r < total; r += nw) {
+    const int v = list[r];
+    float x[kF];
+    vertex_features(rp, ci, core, kmax, ldmax, v, fs[threadIdx.x >> 5], x);
+    const float s = mlp_logit_warp(S, x);
+    if (lane == 0) score[v] = s;
   }
 }
 
@@ -300,7 +464,288 @@ int stage(mc_mlp *m, const void *src, size_t bytes, const void **dev) {
   return MC_OK;
 }
 
+// ------------------------------------------- the learned form of a solve ---
+
+// Vertices that can still be in a clique larger than their graph's current
+// bound (K(v) >= best), appended to list (warp-aggregated); *count holds the
+// number (zeroed by the caller).
+__global__ void subset_kernel(int64_t n, const int32_t *__restrict__ core, const int32_t *__restrict__ gid,
+                              const int32_t *__restrict__ best, const int32_t *__restrict__ kfloor,
+                              int32_t *__restrict__ list, unsigned long long *__restrict__ count) {
+  const int kf = kfloor ? *kfloor : 0;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~(int64_t)31; b < n; b += stride) {
+    const int64_t v = b + lane;
+    bool in = false;
+    if (v < n) in = core[v] >= max(best[gid ? gid[v] : 0], kf);
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    if (!m) continue;
+    unsigned long long at = 0;
+    if (lane == 0) at = atomicAdd(count, (unsigned long long)__popc(m));
+    at = __shfl_sync(0xffffffffu, at, 0);
+    if (in) list[at + __popc(m & lt)] = (int32_t)v;
+  }
+}
+
+__global__ void fill_kernel(int64_t n, float x, float *__restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = x;
+}
+
+// Histogram of the core numbers (bins 0..kmax).
+__global__ void core_hist_kernel(int64_t n, const int32_t *__restrict__ core, int kmax, unsigned int *__restrict__ hist) {
+  extern __shared__ unsigned int sh[];
+  const bool local = kmax < 8192;
+  if (local) {
+    for (int i = threadIdx.x; i <= kmax; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+  }
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int k = min(core[v], kmax);
+    atomicAdd(local ? &sh[k] : &hist[k], 1u);
+  }
+  if (local) {
+    __syncthreads();
+    for (int i = threadIdx.x; i <= kmax; i += blockDim.x)
+      if (sh[i]) atomicAdd(&hist[i], sh[i]);
+  }
+}
+
+// The core floor of the scored subset: the smallest k such that at most
+// `budget` vertices have K(v) >= k (at least the top shell, K(G)).
+__global__ void core_floor_kernel(const unsigned int *__restrict__ hist, int kmax, long long budget,
+                                  int32_t *__restrict__ kfloor) {
+  if (threadIdx.x != 0) return;
+  long long above = 0;
+  int k = kmax;
+  above = hist[kmax];
+  while (k > 0 && above + (long long)hist[k - 1] <= budget) {
+    k--;
+    above += hist[k];
+  }
+  *kfloor = k;
+}
+
+// Selection key of a scored vertex: the score's order as an unsigned
+// integer (larger score, larger key; raised to at least 1) in the high
+// word, and the complement of the vertex id in the low word, so keys are
+// unique and ties go to the smaller id.
+__device__ __forceinline__ unsigned long long seed_key(float s, int v) {
+  const uint32_t b = __float_as_uint(s);
+  const uint32_t k = max((b & 0x80000000u) ? ~b : (b | 0x80000000u), 1u);
+  return ((unsigned long long)k << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)v);
+}
+
+struct SelectCtl {
+  unsigned long long prefix, mask;  // key bits fixed so far
+  long long need;                   // keys still to take at or below the prefix
+  long long taken;                  // keys collected
+  int all;                          // fewer keys than k: take every key
+  int pad;
+  unsigned int hist[256];
+};
+
+__global__ void select_init_kernel(SelectCtl *ctl, int k) {
+  if (threadIdx.x == 0) ctl->need = k;
+}
+
+// one 8-bit digit of the k-th largest key: histogram of the keys that match
+// the prefix so far
+__global__ void select_hist_kernel(const int32_t *__restrict__ list, const unsigned long long *__restrict__ count,
+                                   const float *__restrict__ score, SelectCtl *ctl, int shift) {
+  __shared__ unsigned int h[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  const unsigned long long prefix = ctl->prefix, mask = ctl->mask;
+  const int64_t total = (int64_t)*count;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < total; r += (int64_t)gridDim.x * blockDim.x) {
+    const int v = list[r];
+    const unsigned long long key = seed_key(score[v], v);
+    if ((key & mask) == prefix) atomicAdd(&h[(key >> shift) & 255ull], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    if (h[i]) atomicAdd(&ctl->hist[i], h[i]);
+}
+
+__global__ void select_pick_kernel(SelectCtl *ctl, int shift) {
+  if (threadIdx.x != 0 || ctl->all) return;
+  long long acc = 0;
+  int b = 255;
+  for (; b >= 0; b--) {
+    if (acc + (long long)ctl->hist[b] >= ctl->need) break;
+    acc += ctl->hist[b];
+  }
+  if (b < 0) {  // fewer matching keys than needed: only on the first digit
+    ctl->all = 1;
+  } else {
+    ctl->need -= acc;
+    ctl->prefix |= (unsigned long long)b << shift;
+    ctl->mask |= 255ull << shift;
+  }
+  for (int i = 0; i < 256; i++) ctl->hist[i] = 0;
+}
+
+__global__ void select_collect_kernel(const int32_t *__restrict__ list, const unsigned long long *__restrict__ count,
+                                      const float *__restrict__ score, SelectCtl *ctl, int k,
+                                      unsigned long long *__restrict__ keys) {
+  const unsigned long long thr = ctl->all ? 0ull : ctl->prefix;
+  const int64_t total = (int64_t)*count;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < total; r += (int64_t)gridDim.x * blockDim.x) {
+    const int v = list[r];
+    const unsigned long long key = seed_key(score[v], v);
+    if (key >= thr) {
+      const long long at = atomicAdd((unsigned long long *)&ctl->taken, 1ull);
+      if (at < k) keys[at] = key;
+    }
+  }
+}
+
+// the collected keys in decreasing order -> seed vertices; -1 pads the
+// slots past the number collected
+constexpr int kMaxSeeds = 1024;
+__global__ void __launch_bounds__(1024) select_sort_kernel(const SelectCtl *ctl, int k,
+                                                           const unsigned long long *__restrict__ keys,
+                                                           int32_t *__restrict__ seeds) {
+  __shared__ unsigned long long a[kMaxSeeds];
+  const int got = (int)(ctl->taken < (long long)k ? ctl->taken : (long long)k);
+  for (int i = threadIdx.x; i < kMaxSeeds; i += blockDim.x) a[i] = i < got ? keys[i] : 0ull;
+  __syncthreads();
+  for (int len = 2; len <= kMaxSeeds; len <<= 1) {
+    for (int j = len >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < kMaxSeeds; i += blockDim.x) {
+        const int x = i ^ j;
+        if (x > i) {
+          const unsigned long long p = a[i], q = a[x];
+          const bool desc = (i & len) == 0;
+          if (desc ? (p < q) : (p > q)) {
+            a[i] = q;
+            a[x] = p;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < k; i += blockDim.x)
+    seeds[i] = i < got ? (int32_t)(0xFFFFFFFFu - (uint32_t)(a[i] & 0xFFFFFFFFull)) : -1;
+}
+
+// Batches: the j best-scored vertices of every graph among those that can
+// beat its bound, one warp per graph (j rounds of a warp maximum, each
+// below the last key taken).  seeds[g * j + r], -1 where a graph has fewer.
+__global__ void graph_seeds_kernel(int32_t count, const int64_t *__restrict__ voff, const int32_t *__restrict__ core,
+                                   const int32_t *__restrict__ best, const float *__restrict__ score, int j,
+                                   int32_t *__restrict__ seeds) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t g = w0; g < count; g += nw) {
+    const int64_t v0 = voff[g], v1 = voff[g + 1];
+    const int bg = best[g];
+    unsigned long long last = ~0ull;
+    for (int r = 0; r < j; r++) {
+      unsigned long long mx = 0ull;
+      for (int64_t v = v0 + lane; v < v1; v += 32) {
+        if (core[v] < bg) continue;
+        const unsigned long long key = seed_key(score[v], (int)v);
+        if (key < last && key > mx) mx = key;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
+        if (y > mx) mx = y;
+      }
+      if (lane == 0) seeds[g * j + r] = mx ? (int32_t)(0xFFFFFFFFu - (uint32_t)(mx & 0xFFFFFFFFull)) : -1;
+      last = mx;
+      if (!mx) last = 0ull;
+    }
+  }
+}
+
 }  // namespace
+
+// Scores of the vertices that can still be in a clique larger than their
+// graph's current bound -- for one graph, of at most kLearnedBudget of them,
+// those of highest core number.  The other vertices get the lowest score
+// (they are read only as candidates of a seeded growth, which then takes
+// them last).
+constexpr long long kLearnedBudget = 1ll << 22;
+int learned_scores(mc_graph *g, const mc_mlp *m, float *score) {
+  if (g->n == 0) return MC_OK;
+  void *p;
+  MC_TRY(ws_get(g, "ln.list", (size_t)g->n * 4, &p));
+  int32_t *list = (int32_t *)p;
+  MC_TRY(ws_get(g, "ln.ctl", 64 + sizeof(SelectCtl), &p));
+  unsigned long long *count = (unsigned long long *)p;
+  int32_t *kfloor = (int32_t *)((char *)p + 8);
+  MC_CUDA_TRY(cudaMemsetAsync(count, 0, 16, g->stream));
+  const int blocks = (int)std::min<int64_t>((g->n + 255) / 256, (int64_t)g->sm_count * 8);
+  if (g->count == 1 && g->n > kLearnedBudget) {
+    // one graph: score at most kLearnedBudget vertices, those of highest
+    // core number (a vertex of core number K is in no clique above K + 1)
+    const int kmax = std::max(g->max_core, 0);
+    MC_TRY(ws_get(g, "ln.hist", (size_t)(kmax + 2) * 4, &p));
+    unsigned int *hist = (unsigned int *)p;
+    MC_CUDA_TRY(cudaMemsetAsync(hist, 0, (size_t)(kmax + 2) * 4, g->stream));
+    const size_t shm = kmax < 8192 ? (size_t)(kmax + 1) * 4 : 0;
+    core_hist_kernel<<<blocks, 256, shm, g->stream>>>(g->n, g->core, kmax, hist);
+    core_floor_kernel<<<1, 32, 0, g->stream>>>(hist, kmax, kLearnedBudget, kfloor);
+    g_launches += 2;
+  }
+  subset_kernel<<<blocks, 256, 0, g->stream>>>(g->n, g->core, g->gid, g->best, kfloor, list, count);
+  fill_kernel<<<blocks, 256, 0, g->stream>>>(g->n, -INFINITY, score);
+  g_launches += 2;
+  const float kmax = (float)std::max(g->max_core, 1);
+  const float ldmax = log1pf((float)std::max(g->max_degree, 1));
+  const int sblocks = g->sm_count * 8;
+  score_kernel<<<sblocks, 256, 0, g->stream>>>(list, (const int64_t *)count, g->row_ptr, g->col_idx, g->core, kmax,
+                                               ldmax, m->wbf, m->master, score);
+  g_launches++;
+  MC_CUDA_TRY(cudaGetLastError());
+  return MC_OK;
+}
+
+// Seeds of the learned heuristic: for one graph the k best-scored vertices
+// of the subset that learned_scores scored (exact selection by 8-bit digits
+// of a unique 64-bit key, best first); for a batch the k best of every
+// graph.  Writes seeds (k or count * k slots, -1 for missing ones).
+int learned_seeds(mc_graph *g, const float *score, int32_t k, int32_t *seeds) {
+  if (g->n == 0 || k <= 0) return MC_OK;
+  void *p;
+  if (g->count > 1) {
+    const int blocks = (int)std::min<int64_t>(((int64_t)g->count * 32 + 255) / 256, (int64_t)g->sm_count * 16);
+    graph_seeds_kernel<<<blocks, 256, 0, g->stream>>>(g->count, g->voff, g->core, g->best, score, k, seeds);
+    g_launches++;
+    MC_CUDA_TRY(cudaGetLastError());
+    return MC_OK;
+  }
+  if (k > kMaxSeeds) return MC_ERR_ARG;
+  MC_TRY(ws_get(g, "ln.list", (size_t)g->n * 4, &p));
+  const int32_t *list = (const int32_t *)p;
+  MC_TRY(ws_get(g, "ln.ctl", 64 + sizeof(SelectCtl), &p));
+  const unsigned long long *count = (const unsigned long long *)p;
+  SelectCtl *ctl = (SelectCtl *)((char *)p + 64);
+  MC_TRY(ws_get(g, "ln.keys", (size_t)kMaxSeeds * 8, &p));
+  unsigned long long *keys = (unsigned long long *)p;
+  MC_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(SelectCtl), g->stream));
+  select_init_kernel<<<1, 32, 0, g->stream>>>(ctl, k);
+  g_launches++;
+  const int blocks = g->sm_count * 4;
+  for (int shift = 56; shift >= 0; shift -= 8) {
+    select_hist_kernel<<<blocks, 256, 0, g->stream>>>(list, count, score, ctl, shift);
+    select_pick_kernel<<<1, 32, 0, g->stream>>>(ctl, shift);
+    g_launches += 2;
+  }
+  select_collect_kernel<<<blocks, 256, 0, g->stream>>>(list, count, score, ctl, k, keys);
+  select_sort_kernel<<<1, 1024, 0, g->stream>>>(ctl, k, keys, seeds);
+  g_launches += 2;
+  MC_CUDA_TRY(cudaGetLastError());
+  return MC_OK;
+}
+
 }  // namespace mc
 
 using namespace mc;
@@ -387,7 +832,8 @@ int mc_features(mc_graph *g, float *feat_out) {
   const float kmax = (float)std::max(g->max_core, 1);
   const float ldmax = log1pf((float)std::max(g->max_degree, 1));
   const int blocks = (int)std::min<int64_t>((g->n * 32 + 255) / 256, (int64_t)g->sm_count * 16);
-  features_kernel<<<blocks, 256, 0, g->stream>>>(g->n, g->row_ptr, g->col_idx, g->core, kmax, ldmax, dst);
+  features_kernel<<<blocks, 256, 0, g->stream>>>(g->n, nullptr, nullptr, g->row_ptr, g->col_idx, g->core, kmax,
+                                                 ldmax, dst);
   g_launches++;
   MC_CUDA_TRY(cudaGetLastError());
   if (!dev_out) MC_CUDA_TRY(cudaMemcpyAsync(feat_out, dst, (size_t)g->n * kF * 4, cudaMemcpyDeviceToHost, g->stream));
@@ -407,7 +853,7 @@ int mc_mlp_forward(mc_mlp *m, const float *feat, int64_t n, float *score_out) {
     MC_CUDA_TRY(cudaMallocAsync((void **)&tmp, (size_t)n * 4, m->stream));
     out = tmp;
   }
-  const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)m->sm_count * 8);
+  const int blocks = (int)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)m->sm_count * 16);
   forward_kernel<<<blocks, 256, 0, m->stream>>>(n, (const float *)df, m->wbf, m->master, out);
   g_launches++;
   MC_CUDA_TRY(cudaGetLastError());

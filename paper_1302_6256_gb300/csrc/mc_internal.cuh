@@ -71,17 +71,28 @@ bool is_device_ptr(const void *p);
 int launch_core_numbers(mc_graph *g, long long spin_limit);
 
 // Heuristic (Algorithm 1).  mode 0 racy, 1 deterministic.  Raises the
-// incumbent of every graph.  seeds (nullable, device): vertices grown first.
-// warm_only (mode 0): only the warm-up launch -- the seeds and the highest
-// start vertices of the visiting order, each grown by a whole block.
+// incumbent of every graph.  seeds (nullable, device; -1 = empty slot):
+// vertices grown first.  warm_only (mode 0): only the warm-up part -- the
+// seeds and the first warm_top positions of the visiting order (-1: 256, or
+// one per graph of an interleaved batch if more).  skip: positions of the
+// visiting order an earlier launch of this solve has grown already.
+// grown_top (nullable): how many visiting-order positions the warm-up part
+// covered.
 int launch_heuristic(mc_graph *g, int mode, long long spin_limit, const int32_t *seeds, int64_t nseeds,
-                     const float *scores, bool warm_only = false);
+                     const float *scores, bool warm_only = false, int64_t skip = 0, int64_t warm_top = -1,
+                     int64_t *grown_top = nullptr);
+// The learned form (learned.cu): scores of the vertices with K(v) >= their
+// graph's current bound (features and network fused), and the seeds -- the
+// k best-scored of them (of every graph of a batch: k per graph).
+int learned_scores(mc_graph *g, const mc_mlp *m, float *score);
+int learned_seeds(mc_graph *g, const float *score, int32_t k, int32_t *seeds);
 
 // Pruned, oriented graph and the root lists (see prune.cu).
 struct Pruned {
   int64_t n = 0, arcs = 0;         // vertices and arcs of the oriented graph
   int32_t max_out = 0;             // largest out-degree
   int64_t nroots_small = 0, nroots_block = 0, nroots_big = 0;
+  int64_t row_entries = 0;         // CSR row entries read for the kept vertices
   int64_t *orow = nullptr;         // n+1, each row start a multiple of 4 (int4 loads)
   int32_t *ocol = nullptr;         // arcs (padded rows, pad = -1)
   int32_t *ocore = nullptr;        // core number per pruned vertex
@@ -132,6 +143,7 @@ struct mc_graph {
   int32_t heur0 = 0;  // heuristic clique size of graph 0 in the last solve
   unsigned long long *d_heur_ctr = nullptr;  // heuristic work counters of the last solve (device)
   bool heur_ran = false;                     // the last solve ran the heuristic
+  bool learned_ran = false;                  // the last solve was the learned form
   int32_t warp_max_used = 128;  // warp/block split of the current solve
   bool capturing = false;       // inside CUDA graph capture: no host synchronisation
   int32_t *core = nullptr, *order = nullptr, *pos = nullptr;  // n each (device)
@@ -143,7 +155,7 @@ struct mc_graph {
   std::map<std::string, mc::DevBuf> ws;
   // pinned host staging for small results
   void *h_small = nullptr;
-  cudaEvent_t ev[13] = {};  // 0-5 stages, 6-7 graph replay order, 8-12 search kernels
+  cudaEvent_t ev[15] = {};  // 0-5 stages, 6-7 graph replay order, 8-12 search kernels, 13-14 learned scoring
   // captured solve (CUDA graph replay) and what it was captured with
   cudaGraphExec_t graph_exec = nullptr;
   cudaStream_t cap_stream = nullptr;

@@ -80,12 +80,14 @@ struct KeepG {
 // out-degree in the oriented pruned graph (warp per vertex)
 __global__ void outdeg_kernel(const int64_t *__restrict__ d_np, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                               const int32_t *__restrict__ oold, const int32_t *__restrict__ nid,
-                              int32_t *__restrict__ odeg, int32_t *__restrict__ maxout) {
+                              int32_t *__restrict__ odeg, int32_t *__restrict__ maxout,
+                              unsigned long long *__restrict__ scanned) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t np = *d_np;
   int lmax = 0;
+  unsigned long long rows = 0;
   for (int64_t j = w0; j < np; j += nw) {
     int v = oold[j];
     int c = 0;
@@ -93,8 +95,12 @@ __global__ void outdeg_kernel(const int64_t *__restrict__ d_np, const int64_t *_
     c = dev::warp_sum(c);
     if (lane == 0) odeg[j] = c;
     lmax = max(lmax, c);
+    rows += (unsigned long long)(rp[v + 1] - rp[v]);
   }
-  if (lane == 0) atomicMax(maxout, lmax);
+  if (lane == 0) {
+    atomicMax(maxout, lmax);
+    if (rows) atomicAdd(scanned, rows);
+  }
 }
 
 struct PadF {
@@ -231,7 +237,8 @@ int launch_prune(mc_graph *g, int ordering, const float *scores, int32_t warp_ma
     ogid = (int32_t *)p;
   }
   MC_TRY(ws_get(g, "pr.small", 16 * sizeof(int64_t), &p));
-  int64_t *dsm = (int64_t *)p;  // [0] n', [1] arcs, [2] maxout (int32 in low), [3..5] class counts
+  int64_t *dsm = (int64_t *)p;  // [0] n', [1] arcs, [2] maxout (int32 in low), [3..5] class counts,
+                                // [6] row entries of the kept vertices
   MC_CUDA_TRY(cudaMemsetAsync(dsm, 0, 16 * sizeof(int64_t), g->stream));
   out->d_counts = dsm;
   out->n = n;  // upper bound until read back
@@ -248,7 +255,8 @@ int launch_prune(mc_graph *g, int ordering, const float *scores, int32_t warp_ma
   int32_t *odeg = (int32_t *)p;
   int32_t *maxout = (int32_t *)(dsm + 2);
   const int blocks = (int)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)g->sm_count * 16);
-  outdeg_kernel<<<blocks, 256, 0, g->stream>>>(dsm + 0, g->row_ptr, g->col_idx, oold, nid, odeg, maxout);
+  outdeg_kernel<<<blocks, 256, 0, g->stream>>>(dsm + 0, g->row_ptr, g->col_idx, oold, nid, odeg, maxout,
+                                               (unsigned long long *)(dsm + 6));
   g_launches++;
   MC_CUDA_TRY(cudaGetLastError());
   MC_TRY(ws_get(g, "pr.orow", (n + 1) * sizeof(int64_t), &p));
@@ -314,7 +322,7 @@ int launch_prune(mc_graph *g, int ordering, const float *scores, int32_t warp_ma
 // Host copy of the pruned graph's sizes (one small device-to-host read).
 int read_pruned_counts(mc_graph *g, Pruned *out) {
   int64_t *h = (int64_t *)g->h_small;
-  MC_CUDA_TRY(cudaMemcpyAsync(h, out->d_counts, 6 * sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream));
+  MC_CUDA_TRY(cudaMemcpyAsync(h, out->d_counts, 7 * sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream));
   MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
   out->n = h[0];
   out->arcs = h[1];
@@ -322,6 +330,7 @@ int read_pruned_counts(mc_graph *g, Pruned *out) {
   out->nroots_small = h[3];
   out->nroots_block = h[4];
   out->nroots_big = h[5];
+  out->row_entries = h[6];
   return MC_OK;
 }
 

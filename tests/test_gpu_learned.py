@@ -23,13 +23,23 @@ def mc():
 
 
 def test_features_match_oracle(mc):
+    """Every feature of every vertex against the oracle's definitions, on
+    graphs where Q(v) is cut at 16 neighbours (K_20, Turan, the dense R-MAT
+    core) and where it is short or empty (stars, paths, isolated vertices).
+    The triangle count and the colouring bound are integers before the
+    division, so they must agree exactly; the float tolerance covers the
+    float32 logarithms and divisions."""
     for g in [gg.chung_lu(3000, 2.4, 10.0, 300.0, planted=12, seed=3), gg.rmat(12, 16, planted=20, seed=4),
-              gg.star(40), gg.empty(5)]:
+              gg.star(40), gg.empty(5), gg.complete(20), gg.turan(64, 5), gg.relabel(gg.turan(90, 7), 2),
+              gg.path(7), gg.erdos_renyi(500, 0.1, planted=14, seed=6)]:
         h = mc.mc_load_csr(g.row_ptr, g.col_idx)
         f = mc.mc_features(h)
         ref = OL.features(g, oracle.core_numbers(g))
         assert f.shape == ref.shape
-        assert np.allclose(f, ref, rtol=2e-6, atol=2e-6)
+        assert np.allclose(f, ref, rtol=2e-6, atol=2e-6), g.name
+        T = OL.T
+        assert np.array_equal(np.rint(f[:, 2] * (T * (T - 1) / 2)), np.rint(ref[:, 2] * (T * (T - 1) / 2)))
+        assert np.array_equal(np.rint(f[:, 3] * (T + 1)), np.rint(ref[:, 3] * (T + 1)))
 
 
 def test_forward_and_gradient_match_oracle(mc):
@@ -76,6 +86,62 @@ def test_learned_ordering_keeps_omega_exact(mc, kind):
         om, wit, st = mc.mc_max_clique(h, ordering=1, scores=s, seeds=16)
         assert om == oracle.max_clique(g)[0]
         assert oracle.is_clique(g, wit)
+
+
+@pytest.mark.parametrize("heuristic", [0, 3])
+@pytest.mark.parametrize("ordering", [0, 1])
+def test_learned_form_keeps_omega_exact(mc, heuristic, ordering):
+    """The learned form (mlp option): warm-up bound, scores of the vertices
+    that can beat it, seeds grown first, then the rest of Algorithm 1 or
+    not; omega equals the oracle's for an untrained and a trained network,
+    and the scored vertices are a subset of the graph that contains every
+    vertex the pruning keeps."""
+    import os
+    w = np.load(os.path.join(os.path.dirname(mc.__file__), "ordering_mlp.npy"))
+    nets = [mc.MLP(seed=3), mc.MLP(seed=0)]
+    nets[1].set_params(w)
+    graphs = [gg.chung_lu(20000, 2.3, 12.0, 800.0, planted=18, seed=15), gg.rmat(14, 16, planted=30, seed=16),
+              gg.erdos_renyi(400, 0.5, planted=0, seed=19), _dense_core_and_path(), gg.relabel(gg.turan(300, 33), 3)]
+    for g in graphs:
+        ref = oracle.max_clique(g)[0]
+        h = mc.mc_load_csr(g.row_ptr, g.col_idx)
+        for net in nets:
+            for seeds in (0, 5, 300):
+                om, wit, st = mc.mc_max_clique(h, mlp=net, heuristic=heuristic, ordering=ordering, seeds=seeds)
+                assert om == ref, (g.name, seeds)
+                assert oracle.is_clique(g, wit) and len(wit) == om
+                assert st["pruned_n"] <= st["learned_scored"] <= g.n
+                assert st["verified"] == 1
+        h.close()
+
+
+def test_learned_form_batch_and_replay(mc):
+    """The learned form on a batch (seeds per graph) and replayed as a CUDA
+    graph: every graph's omega equals the oracle's."""
+    b = gg.er_batch(48, seed=3)
+    ref = np.array([oracle.max_clique(g)[0] for g in b.graphs], np.int32)
+    h = mc.mc_load_batch(torch.from_numpy(b.voff).cuda(), torch.from_numpy(b.row_ptr).cuda(),
+                         torch.from_numpy(b.col_idx).cuda(), mc.MC_VALIDATE)
+    net = mc.MLP(seed=4)
+    for opts in (dict(heuristic=0), dict(heuristic=3), dict(heuristic=3, seeds=1), dict(heuristic=3, graph=True),
+                 dict(heuristic=3, graph=True)):
+        om, wits, st = mc.mc_max_clique_batch(h, mlp=net, **opts)
+        assert np.array_equal(om, ref), opts
+        for i, g in enumerate(b.graphs):
+            assert len(wits[i]) == om[i] and oracle.is_clique(g, wits[i])
+    h.close()
+
+
+def test_learned_form_refuses_bad_options(mc):
+    g = gg.rmat(10, 8, planted=10, seed=1)
+    h = mc.mc_load_csr(g.row_ptr, g.col_idx)
+    net = mc.MLP(seed=1)
+    for opts in (dict(heuristic=1), dict(heuristic=2), dict(seeds=1025),
+                 dict(scores=np.zeros(g.n, np.float32))):
+        with pytest.raises(mc.MCError) as e:
+            mc.mc_max_clique(h, mlp=net, **opts)
+        assert e.value.code == mc.MC_ERR_ARG
+    h.close()
 
 
 def _bits(u):
