@@ -28,7 +28,7 @@ def bf16_round(x):
     return r.astype(np.uint32).view(np.float32)
 
 
-T = 16  # neighbours that the triangle and colouring features look at
+T = 8  # neighbours that the triangle and colouring features look at
 
 
 def features(g, core):

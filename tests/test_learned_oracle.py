@@ -104,17 +104,20 @@ def test_features_closed_forms():
 
 def test_features_turan_worked_by_hand():
     """Turan T(32, 4), parts = id mod 4, 24-regular (every core number 24).
-    Vertex 0's first 16 neighbours are 1 2 3 5 6 7 9 10 11 13 14 15 17 18 19
-    21: parts 1, 2, 3 with 6, 5 and 5 members.  Edges among them join
-    different parts: C(16,2) - C(6,2) - 2 C(5,2) = 120 - 15 - 20 = 85.  The
-    greedy colouring of a complete multipartite graph gives each part one
-    colour: 3 colours."""
+    Vertex 0's first 8 neighbours are 1 2 3 5 6 7 9 10: parts 1, 2, 3 with
+    3, 3 and 2 members.  Edges among them join different parts:
+    C(8,2) - 2 C(3,2) - C(2,2) = 28 - 6 - 1 = 21.  The greedy colouring of a
+    complete multipartite graph gives each part one colour: 3 colours."""
+    assert OL.T == 8
     g = gg.turan(32, 4)
     f = OL.features(g, oracle.core_numbers(g))
-    assert np.allclose(f[0], _f(24, 24, 24, 24, 85, 3, 24))
-    # vertex 5 (part 1): neighbours 0 2 3 4 6 7 8 10 11 12 14 15 16 18 19 20,
-    # parts 0, 2, 3 with 6, 5, 5 members again
-    assert np.allclose(f[5], _f(24, 24, 24, 24, 85, 3, 24))
+    assert np.allclose(f[0], _f(24, 24, 24, 24, 21, 3, 24))
+    # vertex 5 (part 1): first neighbours 0 2 3 4 6 7 8 10, parts 0, 2, 3
+    # with 3, 3, 2 members again
+    assert np.allclose(f[5], _f(24, 24, 24, 24, 21, 3, 24))
+    # vertex 31 (part 3): first neighbours 0 1 2 4 5 6 8 9, parts 0, 1, 2
+    # with 3, 3, 2 members
+    assert np.allclose(f[31], _f(24, 24, 24, 24, 21, 3, 24))
 
 
 def test_features_first_T_in_id_order():
@@ -122,9 +125,10 @@ def test_features_first_T_in_id_order():
     joined to 1..20; 1..16 are pairwise adjacent; each of 17..20 is joined to
     all of 1..16 and to nothing else.  Degrees: 20 (0 and 1..16), 17
     (17..20); the whole graph is a 17-core and no 18-core exists, so every
-    core number is 17.  Q(0) = 1..16, a clique: 120 edges, 16 colours.  (The
-    last 16 neighbours, 5..20, would give 66 + 48 = 114 edges and 13
-    colours.)  Q(17) = 0..15: again a clique."""
+    core number is 17.  With T = 8, Q(0) = 1..8, a clique: 28 edges, 8
+    colours.  (The last 8 neighbours, 13..20, would give C(4,2) + 4 * 4 = 22
+    edges and 5 colours.)  Q(17) = 0..7 and Q(1) = 0, 2..8: cliques too."""
+    assert OL.T == 8
     src, dst = [], []
     for u in range(1, 21):
         src.append(0)
@@ -140,10 +144,9 @@ def test_features_first_T_in_id_order():
     K = oracle.core_numbers(g)
     assert np.all(K == 17)
     f = OL.features(g, K)
-    assert OL.T == 16
-    assert np.allclose(f[0], _f(20, 20, 17, 17, 120, 16, 20))
-    assert np.allclose(f[17], _f(17, 20, 17, 17, 120, 16, 17))
-    assert np.allclose(f[1], _f(20, 20, 17, 17, 120, 16, 20))
+    assert np.allclose(f[0], _f(20, 20, 17, 17, 28, 8, 20))
+    assert np.allclose(f[17], _f(17, 20, 17, 17, 28, 8, 17))
+    assert np.allclose(f[1], _f(20, 20, 17, 17, 28, 8, 20))
 
 
 def test_features_mixed_neighbour_cores():
