@@ -60,6 +60,8 @@ def configure(lib):
     lib.orc_is_clique.restype = ctypes.c_int
     lib.orc_max_clique_threads.argtypes = [i64, vp, vp, i32, vp, vp, i32, vp]
     lib.orc_max_clique_threads.restype = ctypes.c_int
+    lib.orc_max_clique_part.argtypes = [i64, vp, vp, vp, i32, i32, i32, vp, vp, i32, vp]
+    lib.orc_max_clique_part.restype = ctypes.c_int
     return lib
 
 
@@ -144,6 +146,27 @@ def max_clique_threads(g, threads: int):
                                      W.ctypes.data, cap, ctypes.addressof(st))
     if rc != 0:
         raise RuntimeError("oracle threaded max clique failed: %d" % rc)
+    return om.value, W[:om.value].copy(), st.as_dict()
+
+
+def max_clique_part(g, part_rank: int, part_count: int, order=None, threads: int = 1):
+    """The threaded search restricted to the roots at positions part_rank,
+    part_rank + part_count, ... of `order` (a degeneracy order; None = the
+    oracle's own).  Returns (the largest clique size this part found, its
+    witness, stats); the maximum over the parts is omega."""
+    rp, ci, n = _csr(g)
+    cap = n + 1
+    W = np.zeros(max(cap, 1), np.int32)
+    om = ctypes.c_int32(0)
+    st = Stats()
+    op = None
+    if order is not None:
+        order = np.ascontiguousarray(order, dtype=np.int32)
+        op = order.ctypes.data
+    rc = _L().orc_max_clique_part(n, rp.ctypes.data, ci.ctypes.data, op, int(part_rank), int(part_count),
+                                  int(threads), ctypes.addressof(om), W.ctypes.data, cap, ctypes.addressof(st))
+    if rc != 0:
+        raise RuntimeError("oracle partitioned max clique failed: %d" % rc)
     return om.value, W[:om.value].copy(), st.as_dict()
 
 

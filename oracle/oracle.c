@@ -20,6 +20,11 @@
  *   orc_max_clique_threads the same exact search by several workers sharing
  *                         the incumbent (Section 4.5), roots in a static
  *                         degeneracy order.
+ *   orc_max_clique_part   the same, restricted to one part of a partition of
+ *                         the roots (every part_count-th position of a given
+ *                         degeneracy order): the search of one rank of several
+ *                         that split the roots (Section 4.5 distributes them
+ *                         over processors).
  *
  * Readings of points the paper leaves open (each is exact: omega and K do not
  * depend on them):
@@ -630,6 +635,8 @@ typedef struct {
   int32_t *H;            /* witness in original ids, written under mu */
   pthread_mutex_t mu;
   int64_t ib_calls, ib_full, nodes; /* summed under mu when a worker ends */
+  const int32_t *opos;   /* position of each kept vertex in the full order */
+  int32_t part_rank, part_count;
   int err;
 } th_search;
 
@@ -709,6 +716,7 @@ static void th_branch(th_worker *w, int32_t csize, int32_t *idx, int32_t *colors
 static void th_root(th_worker *w, int32_t u, int32_t *kn, uint8_t *in, int32_t *idx, int32_t *col, int32_t *scr,
                     knkey *ord, int32_t *nat, int32_t *ncol) {
   th_search *sh = w->sh;
+  if (sh->opos[u] % sh->part_count != sh->part_rank) return; /* another part's root */
   int32_t h = th_best(w);
   if (sh->K[u] < h) return; /* K(u) + 1 <= |H| */
   w->ib_calls++;
@@ -798,7 +806,47 @@ static int run_threads(int threads, void *(*fn)(void *), void *args, size_t stri
   return rc;
 }
 
+/* A degeneracy order: every vertex has at most K(v) neighbours after it. */
+static int is_degeneracy_order(int64_t n, const int64_t *rp, const int32_t *ci, const int32_t *K, const int32_t *order,
+                               int32_t *pos) {
+  for (int64_t i = 0; i < n; i++) pos[i] = -1;
+  for (int64_t i = 0; i < n; i++) {
+    if (order[i] < 0 || order[i] >= n || pos[order[i]] >= 0) return 0;
+    pos[order[i]] = (int32_t)i;
+  }
+  for (int64_t v = 0; v < n; v++) {
+    int64_t later = 0;
+    for (int64_t e = rp[v]; e < rp[v + 1]; e++) later += pos[ci[e]] > pos[v];
+    if (later > K[v]) return 0;
+  }
+  return 1;
+}
+
+static int max_clique_part(int64_t n, const int64_t *rp, const int32_t *ci, const int32_t *order_in,
+                           int32_t part_rank, int32_t part_count, int32_t threads, int32_t *omega_out,
+                           int32_t *witness, int32_t cap, orc_stats *st);
+
 int orc_max_clique_threads(int64_t n, const int64_t *rp, const int32_t *ci, int32_t threads, int32_t *omega_out,
+                           int32_t *witness, int32_t cap, orc_stats *st) {
+  return max_clique_part(n, rp, ci, NULL, 0, 1, threads, omega_out, witness, cap, st);
+}
+
+/* The threaded search over the roots at positions part_rank, part_rank +
+ * part_count, ... of `order` (a degeneracy order of the graph; NULL = the
+ * Batagelj-Zaversnik order).  omega_out and witness: the largest clique
+ * this part found, which is the heuristic's clique when no root of the part
+ * beats it; the maximum over all parts is omega(G), since every clique has
+ * exactly one lowest-ranked member.  ORC_ERR_ARG if order is not a
+ * degeneracy order. */
+int orc_max_clique_part(int64_t n, const int64_t *rp, const int32_t *ci, const int32_t *order, int32_t part_rank,
+                        int32_t part_count, int32_t threads, int32_t *omega_out, int32_t *witness, int32_t cap,
+                        orc_stats *st) {
+  if (part_count < 1 || part_rank < 0 || part_rank >= part_count) return ORC_ERR_ARG;
+  return max_clique_part(n, rp, ci, order, part_rank, part_count, threads, omega_out, witness, cap, st);
+}
+
+static int max_clique_part(int64_t n, const int64_t *rp, const int32_t *ci, const int32_t *order_in,
+                           int32_t part_rank, int32_t part_count, int32_t threads, int32_t *omega_out,
                            int32_t *witness, int32_t cap, orc_stats *st) {
   if (n < 0 || threads < 1 || threads > 1024) return ORC_ERR_ARG;
   orc_stats local;
@@ -810,7 +858,7 @@ int orc_max_clique_threads(int64_t n, const int64_t *rp, const int32_t *ci, int3
   int32_t *K0 = (int32_t *)malloc((size_t)n * sizeof(int32_t));
   int32_t *order = (int32_t *)malloc((size_t)n * sizeof(int32_t));
   vkey *hord = (vkey *)malloc((size_t)n * sizeof(vkey));
-  int32_t *newid = NULL, *orig = NULL, *K2 = NULL, *oci = NULL, *H = NULL;
+  int32_t *newid = NULL, *orig = NULL, *K2 = NULL, *oci = NULL, *H = NULL, *opos = NULL, *fpos = NULL;
   int64_t *orp = NULL;
   th_worker *wk = NULL;
   th_heur hh;
@@ -820,8 +868,15 @@ int orc_max_clique_threads(int64_t n, const int64_t *rp, const int32_t *ci, int3
   pthread_mutex_init(&hh.mu, NULL);
   pthread_mutex_init(&sh.mu, NULL);
   if (!K0 || !order || !hord) { rc = ORC_ERR_OOM; goto out; }
-  /* 1. core numbers and the degeneracy order */
+  /* 1. core numbers and the degeneracy order (the given one if any) */
   if ((rc = orc_core_numbers(n, rp, ci, K0, order)) != ORC_OK) goto out;
+  fpos = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  if (!fpos) { rc = ORC_ERR_OOM; goto out; }
+  if (order_in) {
+    if (!is_degeneracy_order(n, rp, ci, K0, order_in, fpos)) { rc = ORC_ERR_ARG; goto out; }
+    memcpy(order, order_in, (size_t)n * sizeof(int32_t));
+  }
+  for (int64_t i = 0; i < n; i++) fpos[order[i]] = (int32_t)i;
   int32_t kmax = 0;
   int64_t maxd = 0;
   for (int64_t v = 0; v < n; v++) {
@@ -851,7 +906,8 @@ int orc_max_clique_threads(int64_t n, const int64_t *rp, const int32_t *ci, int3
   orp = (int64_t *)malloc(((size_t)n2 + 1) * sizeof(int64_t));
   orig = (int32_t *)malloc(((size_t)n2 + 1) * sizeof(int32_t));
   K2 = (int32_t *)malloc(((size_t)n2 + 1) * sizeof(int32_t));
-  if (!orp || !orig || !K2) { rc = ORC_ERR_OOM; goto out; }
+  opos = (int32_t *)malloc(((size_t)n2 + 1) * sizeof(int32_t));
+  if (!orp || !orig || !K2 || !opos) { rc = ORC_ERR_OOM; goto out; }
   orp[0] = 0;
   for (int64_t i = 0; i < n; i++) {
     int32_t v = order[i];
@@ -860,6 +916,7 @@ int orc_max_clique_threads(int64_t n, const int64_t *rp, const int32_t *ci, int3
     for (int64_t e = rp[v]; e < rp[v + 1]; e++) if (newid[ci[e]] > newid[v]) d++;
     orig[newid[v]] = v;
     K2[newid[v]] = K0[v];
+    opos[newid[v]] = fpos[v];
     orp[newid[v] + 1] = orp[newid[v]] + d;
   }
   oci = (int32_t *)malloc(((size_t)orp[n2] + 1) * sizeof(int32_t));
@@ -875,6 +932,7 @@ int orc_max_clique_threads(int64_t n, const int64_t *rp, const int32_t *ci, int3
   /* 4. the roots, shared by the workers */
   sh.n2 = n2; sh.orp = orp; sh.oci = oci; sh.K = K2; sh.orig = orig; sh.kmax = kmax;
   sh.best = hs; sh.H = H;
+  sh.opos = opos; sh.part_rank = part_rank; sh.part_count = part_count;
   wk = (th_worker *)calloc((size_t)threads, sizeof(th_worker));
   if (!wk) { rc = ORC_ERR_OOM; goto out; }
   for (int t = 0; t < threads; t++) {
@@ -901,6 +959,7 @@ out:
     for (int t = 0; t < threads; t++) { free(wk[t].mark); free(wk[t].P); free(wk[t].C); free(wk[t].adj); }
   free(wk);
   free(K0); free(order); free(hord); free(newid); free(orig); free(K2); free(oci); free(orp); free(H);
+  free(opos); free(fpos);
   pthread_mutex_destroy(&hh.mu);
   pthread_mutex_destroy(&sh.mu);
   return rc;

@@ -421,3 +421,60 @@ def test_threaded_matches_single_thread_on_generated_graphs():
             assert o == om and oracle.is_clique(g, wit) and len(wit) == o
             assert st["max_core"] == st1["max_core"]
             assert st["heuristic"] <= om
+
+
+# ----------------------------------------------- partitioned search (4.5) --
+# The roots split over `parts` ranks by their position in one shared
+# degeneracy order: every clique has exactly one lowest-ranked member, so
+# the largest clique found by any part is omega.
+
+def _other_degeneracy_order(g):
+    """A degeneracy order by a different rule than Batagelj-Zaversnik's:
+    repeatedly remove a vertex of minimum remaining degree, ties to the
+    LARGEST id (a plain restatement of the definition)."""
+    adj = adj_sets(g)
+    deg = {v: len(adj[v]) for v in range(g.n)}
+    alive = set(range(g.n))
+    out = []
+    while alive:
+        v = max(alive, key=lambda x: (-deg[x], x))
+        out.append(v)
+        alive.discard(v)
+        for u in adj[v]:
+            if u in alive:
+                deg[u] -= 1
+    return np.array(out, np.int32)
+
+
+@pytest.mark.parametrize("k", [3, 4, 5])
+def test_partition_covers_every_clique(k):
+    graphs = [tight_instance(k)[0], gg.relabel(tight_instance(k)[0], 5)] + small_random_graphs()[::4]
+    for g in graphs:
+        om = brute_omega(g) if g.n <= 18 else oracle.max_clique(g)[0]
+        for parts in (1, 2, 3, 5):
+            for order in (None, _other_degeneracy_order(g)):
+                res = [oracle.max_clique_part(g, r, parts, order) for r in range(parts)]
+                assert max(o for o, _, _ in res) == om, (g.name, parts)
+                for o, wit, _ in res:
+                    assert len(wit) == o and oracle.is_clique(g, wit)
+
+
+def test_partition_on_generated_graphs():
+    for g in [gg.rmat(12, 16, planted=14, seed=2), gg.chung_lu(3000, 2.5, 8.0, 300.0, planted=9, seed=7)]:
+        om = oracle.max_clique(g)[0]
+        K, order = oracle.core_numbers(g, with_order=True)
+        for parts in (2, 4):
+            res = [oracle.max_clique_part(g, r, parts, order, threads=2) for r in range(parts)]
+            assert max(o for o, _, _ in res) == om
+            # the parts share the work: with one worker each (same heuristic,
+            # same pruning) their roots are disjoint and make up all roots
+            one = [oracle.max_clique_part(g, r, parts, order, threads=1)[2]["initial_branch"] for r in range(parts)]
+            assert sum(one) == oracle.max_clique_part(g, 0, 1, order, threads=1)[2]["initial_branch"]
+
+
+def test_partition_refuses_an_order_that_is_not_a_degeneracy_order():
+    g = gg.star(10)  # the centre first has 9 later neighbours but core number 1
+    with pytest.raises(RuntimeError):
+        oracle.max_clique_part(g, 0, 2, np.arange(10, dtype=np.int32))
+    with pytest.raises(RuntimeError):
+        oracle.max_clique_part(g, 0, 2, np.zeros(10, dtype=np.int32))  # not a permutation

@@ -92,6 +92,10 @@ C_MUTANTS = [
     ("threads-clique-member-as-index", "w->C[csize] = w->P[u];", "w->C[csize] = u;", False),
     ("threads-witness-in-new-ids", "sh->H[i] = sh->orig[w->C[i]];", "sh->H[i] = w->C[i];", False),
     ("threads-incumbent-not-published", "    __atomic_store_n(&sh->best, size, __ATOMIC_RELEASE);\n", "", False),
+    # the partitioned search
+    ("part-searches-the-other-roots", "if (sh->opos[u] % sh->part_count != sh->part_rank) return;",
+     "if (sh->opos[u] % sh->part_count == sh->part_rank) return;", False),
+    ("part-order-not-checked", "if (later > K[v]) return 0;", "if (later > K[v] + 1000000) return 0;", False),
 ]
 
 PY_MUTANTS = [
