@@ -297,12 +297,12 @@ def _timed(solve, stream, steps, warmup):
     return t0.elapsed_time(t1) / steps, out
 
 
-def _pick_heuristic(solve_with, stream, trials=2):
+def _pick_heuristic(solve_with, stream, trials=2, extents=(0, 3)):
     """The faster Algorithm 1 extent for an arm: the full algorithm (0) or
     its warm-up part only (3), each timed over `trials` solves after one
     untimed solve; omega is exact either way."""
     best = None
-    for hv in (0, 3):
+    for hv in extents:
         ms, _ = _timed(lambda: solve_with(hv), stream, trials, 1)
         if best is None or ms < best[1]:
             best = (hv, ms)
@@ -349,7 +349,8 @@ def run_batch(args):
     forms = [f for f in ("chosen", "learned") if args.form in (f, "all")]
     for f in forms:
         base = dict(graph=True) if f == "chosen" else dict(graph=True, mlp=net)
-        hv = _pick_heuristic(lambda x: mc.mc_max_clique_batch(h, heuristic=x, **base), stream)
+        hv = _pick_heuristic(lambda x: mc.mc_max_clique_batch(h, heuristic=x, **base), stream,
+                             extents=args.chosen_extents if f == "chosen" else args.learned_extents)
         opts = dict(base, heuristic=hv)
         ms, res = _timed(lambda: mc.mc_max_clique_batch(h, **opts), stream, args.steps, args.warmup)
         arms[f] = {"ms": ms, "omegas": res[-1][0], "stats": res[-1][2],
@@ -399,7 +400,8 @@ def run_single(args):
             opts = dict(no_split=True)
         else:
             base = {} if f == "chosen" else dict(mlp=net)
-            hv = _pick_heuristic(lambda x: mc.mc_max_clique(h, witness_out=wit, heuristic=x, **base), stream)
+            hv = _pick_heuristic(lambda x: mc.mc_max_clique(h, witness_out=wit, heuristic=x, **base), stream,
+                                 extents=args.chosen_extents if f == "chosen" else args.learned_extents)
             opts = dict(base, heuristic=hv)
         ms, res = _timed(lambda: mc.mc_max_clique(h, witness_out=wit, **opts), stream, args.steps, args.warmup)
         om, _, st = res[-1]
@@ -439,10 +441,15 @@ def main():
     ap.add_argument("--heuristic", type=int, default=0, choices=[0, 1, 3],
                     help="override the chosen form's Algorithm 1 extent: 1 deterministic, 3 warm-up only "
                          "(0: the autotuner's choice)")
+    ap.add_argument("--chosen-extents", default="0,3",
+                    help="Algorithm 1 extents the chosen arm of the other workloads tries (0 full, 3 warm-up only)")
+    ap.add_argument("--learned-extents", default="0,3", help="... and the learned arm")
     ap.add_argument("--clocks-csv", default=None,
                     help="keep the raw nvidia-smi samples of the timed region in this file (rank r appends _r)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    args.chosen_extents = tuple(int(x) for x in args.chosen_extents.split(","))
+    args.learned_extents = tuple(int(x) for x in args.learned_extents.split(","))
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "er-batch":

@@ -121,6 +121,19 @@ typedef struct {
    * network predicts.  The network must not be freed or changed while a
    * captured solve (graph = 1) that uses it can be replayed. */
   const mc_mlp *mlp;
+  /* Root partition over several ranks (Section 4.5 spreads the roots of the
+   * search over processors).  With part_count > 1 the search takes only the
+   * roots whose position in the degeneracy order is congruent to part_rank
+   * modulo part_count; everything else (core numbers, heuristic, pruning)
+   * runs whole.  Every clique has exactly one lowest-ranked member, so the
+   * largest clique over all parts is omega -- provided every part uses the
+   * same order: pass one rank's mc_peel_order() as `order` on every rank.
+   * order: n int32, host or device, a degeneracy order of this graph (each
+   * vertex has at most K(v) neighbours after it), or NULL for the library's
+   * own; an order that is not one is refused with MC_ERR_ARG.  Not with
+   * graph = 1 or a batch (MC_ERR_ARG).  part_count 0 or 1: every root. */
+  const int32_t *order;
+  int32_t part_rank, part_count;
 } mc_options;
 
 /* Per-call statistics (all times in milliseconds, CUDA events). */
@@ -220,6 +233,14 @@ int mc_max_clique_batch(mc_graph *g, const mc_options *opt, int32_t *omegas_out,
  * *best_ms_out (nullable).  Every trial is a full exact solve. */
 int mc_autotune(mc_graph *g, const mc_options *base, int32_t repeats, mc_options *best_out, double *best_ms_out);
 
+/* The degeneracy order of the core numbers' peel (Section 3: each vertex has
+ * at most K(v) neighbours after it), as computed by the last core-number
+ * computation of this graph (computed now if there is none).  order_out: n
+ * int32, host or device.  The order depends on the timing of the peel; pass
+ * it as mc_options.order to make other solves (on this or another GPU) use
+ * the same one. */
+int mc_peel_order(mc_graph *g, int32_t *order_out);
+
 /* Check a vertex set on the device: *is_clique_out = 1 iff the k vertices are
  * distinct, in range and pairwise adjacent (the definition of a clique). */
 int mc_verify_clique(mc_graph *g, const int32_t *vertices, int32_t k, int32_t *is_clique_out);
@@ -264,7 +285,7 @@ int mc_core_numbers_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *co
  * entries: W1[64][6], b1[64], W2[64][64], b2[64], w3[64], b3. */
 /* Per-vertex features (n x 6 float, row-major, host or device), each in
  * [0, 1]: degree, core number, a triangle count and a neighbourhood
- * colouring bound over the first 16 neighbours of core number >= K(v), and
+ * colouring bound over the first 8 neighbours of core number >= K(v), and
  * the count of those neighbours (as a fraction of the degree and log-scaled);
  * the exact definitions are in learned.cu.  Computes the core numbers if
  * needed. */

@@ -48,7 +48,8 @@ class Options(ctypes.Structure):
                 ("spin_limit", ctypes.c_int64), ("scores", ctypes.c_void_p),
                 ("seeds", ctypes.c_int32), ("graph", ctypes.c_int32),
                 ("no_split", ctypes.c_int32), ("split_nodes", ctypes.c_int32),
-                ("mlp", ctypes.c_void_p)]
+                ("mlp", ctypes.c_void_p), ("order", ctypes.c_void_p), ("part_rank", ctypes.c_int32),
+                ("part_count", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -100,6 +101,8 @@ def load_library(build_if_missing: bool = True):
         L.mc_max_clique.argtypes = [vp, vp, vp, vp, i32, vp]
         L.mc_max_clique_batch.argtypes = [vp, vp, vp, vp, i64, vp, vp]
         L.mc_verify_clique.argtypes = [vp, vp, i32, vp]
+        L.mc_peel_order.argtypes = [vp, vp]
+        L.mc_peel_order.restype = ctypes.c_int
         L.mc_strerror.argtypes = [ctypes.c_int]
         L.mc_strerror.restype = ctypes.c_char_p
         L.mc_version.restype = ctypes.c_int
@@ -310,9 +313,18 @@ def _scores_arg(scores, n):
 
 
 def _options(n, ordering=0, no_neigh_cores=False, heuristic=0, warp_max=0, spin_limit=0, scores=None, seeds=0,
-             graph=False, no_split=False, split_nodes=0, mlp=None):
+             graph=False, no_split=False, split_nodes=0, mlp=None, order=None, part_rank=0, part_count=0):
     scores = _scores_arg(scores, n)
     o = Options()
+    if order is not None:
+        order = _in(order, np.int32, "order")
+        if order.ndim != 1 or int(order.shape[0]) != n:
+            raise ValueError("order must hold one vertex per position (%d), got shape %s" % (n, tuple(order.shape)))
+        op, okeep = _ptr(order)
+        o.order = op
+        o._order_ref = okeep
+    o.part_rank = part_rank
+    o.part_count = part_count
     if mlp is not None:
         if not isinstance(mlp, MLP):
             raise TypeError("mlp must be an MLP handle")
@@ -359,6 +371,17 @@ def mc_max_clique_batch(g: Graph, **opts):
                                  offs.ctypes.data, ctypes.byref(st)), "mc_max_clique_batch")
     wits = [wit[offs[i]:offs[i + 1]].copy() for i in range(g.count)]
     return om, wits, st.as_dict()
+
+
+def mc_peel_order(g: Graph, out=None):
+    """The degeneracy order of the last core-number computation (n int32,
+    host or device output)."""
+    L = load_library()
+    if out is None:
+        out = np.zeros(max(g.n, 1), np.int32)
+    p, keep = _ptr(_out(out, np.int32, g.n, "out"))
+    _check(L.mc_peel_order(g.handle, p), "mc_peel_order")
+    return out[:g.n]
 
 
 def mc_verify_clique(g: Graph, vertices) -> bool:

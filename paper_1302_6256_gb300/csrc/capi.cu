@@ -292,6 +292,10 @@ static int check_options(const mc_options *opt, mc_options *o) {
     return MC_ERR_ARG;
   if (o->ordering == 1 && !o->scores && !o->mlp) return MC_ERR_ARG;
   if (o->mlp && (o->scores || (o->heuristic != 0 && o->heuristic != 3) || o->seeds > 1024)) return MC_ERR_ARG;
+  if (o->part_count < 0 || o->part_rank < 0 || (o->part_count > 1 && o->part_rank >= o->part_count) ||
+      (o->part_count <= 1 && o->part_rank != 0))
+    return MC_ERR_ARG;
+  if (o->order && o->graph) return MC_ERR_ARG;
   return MC_OK;
 }
 
@@ -306,6 +310,10 @@ static int enqueue_solve(mc_graph *g, const mc_options &o, Pruned *pg, SearchCou
   // every solve recomputes the core numbers (Algorithm 2, line 2)
   g->cores_valid = false;
   MC_TRY(ensure_cores(g, spin));
+  if (o.order) {
+    if (g->count > 1) return MC_ERR_ARG;
+    MC_TRY(use_order(g, o.order));
+  }
   MC_TRY(record_event(g, 1));
   MC_CUDA_TRY(cudaMemsetAsync(g->best, 0, g->count * 4, g->stream));
   MC_CUDA_TRY(cudaMemsetAsync(g->lock, 0, g->count * 4, g->stream));
@@ -360,7 +368,9 @@ static int enqueue_solve(mc_graph *g, const mc_options &o, Pruned *pg, SearchCou
   MC_TRY(record_event(g, 2));
   int32_t *h_heur = (int32_t *)((char *)g->h_small + 1024);
   MC_CUDA_TRY(cudaMemcpyAsync(h_heur, g->best, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
-  if (g->n > 0) MC_TRY(launch_prune(g, o.ordering, d_scores, g->warp_max_used, pg, spin));
+  if (g->n > 0)
+    MC_TRY(launch_prune(g, o.ordering, d_scores, g->warp_max_used, pg, spin, o.part_count > 1 ? o.part_rank : 0,
+                        std::max(o.part_count, 1)));
   MC_TRY(record_event(g, 3));
   if (g->n > 0) MC_TRY(launch_search(g, *pg, o.no_neigh_cores, o.no_split, o.split_nodes, spin, sc));
   trivial_kernel<<<std::max(1, std::min(g->count / 256 + 1, 1024)), 256, 0, g->stream>>>(
@@ -457,6 +467,8 @@ static uint64_t options_key(const mc_options &o) {
   mix((uint64_t)o.no_split);
   mix((uint64_t)o.split_nodes);
   mix((uint64_t)(uintptr_t)o.mlp);
+  mix((uint64_t)o.part_rank);
+  mix((uint64_t)o.part_count);
   return k;
 }
 
@@ -734,6 +746,15 @@ int mc_autotune(mc_graph *g, const mc_options *base, int32_t repeats, mc_options
   }
   *best_out = bo;
   if (best_ms_out) *best_ms_out = best;
+  return MC_OK;
+}
+
+int mc_peel_order(mc_graph *g, int32_t *order_out) {
+  if (!g || (g->n > 0 && !order_out)) return MC_ERR_ARG;
+  MC_TRY(ensure_cores(g, kDefaultSpinLimit));
+  if (g->n > 0)
+    MC_CUDA_TRY(cudaMemcpyAsync(order_out, g->order, g->n * sizeof(int32_t), cudaMemcpyDefault, g->stream));
+  MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
   return MC_OK;
 }
 

@@ -5,15 +5,16 @@
 //
 // Features of vertex v (d = degree, K = core number, Kmax = K(G), Dmax =
 // maximum degree, c = number of neighbours with K >= K(v), Q = the first
-// min(16, c) of those neighbours in increasing id):
-//   f0 = log1p(d) / log1p(Dmax)        f3 = (chi + 1) / 17, chi = colours of
+// min(8, c) of those neighbours in increasing id):
+//   f0 = log1p(d) / log1p(Dmax)        f3 = (chi + 1) / 9, chi = colours of
 //   f1 = K(v) / Kmax                        the greedy colouring of G[Q] in
-//   f2 = t / 120, t = edges among Q         increasing id (a bound on a
+//   f2 = t / 28, t = edges among Q          increasing id (a bound on a
 //                                           clique through v inside Q + v)
 //   f4 = c / max(d, 1)                 f5 = log1p(c) / log1p(Dmax)
-// One warp per vertex: a coalesced pass over the row (c and Q), then the
-// 120 pairs of Q tested by binary search in the shorter row, then the
-// colouring with one colour class per lane.
+// Eight lanes per vertex, four vertices per warp in flight: a pass over the
+// row (c and Q), the 28 pairs of Q each found by binary search in the
+// shorter of the two rows, the colouring with one colour class per lane,
+// and the network with eight hidden units per lane.
 //
 // Parameters, flat fp32 (4673): W1[64][6], b1[64], W2[64][64], b2[64],
 // w3[64], b3.  Loss: binary cross-entropy on the logit s with weight
@@ -64,96 +65,86 @@ __host__ __device__ __forceinline__ uint16_t f32_to_bf16(float f) {
   return (uint16_t)(r >> 16);
 }
 
-constexpr int kQ = 16;  // neighbours of the triangle and colouring features
-constexpr int64_t kScanRow = 1024;  // rows up to this length are read whole
+constexpr int kQ = 8;  // neighbours of the triangle and colouring features
 
-// per-warp scratch of vertex_features
-struct FeatScratch {
-  int q[kQ];
-  uint32_t adj[kQ];
-};
+// Sub-warp primitive over the 8 lanes of a group (mask gm covers them).
+__device__ __forceinline__ unsigned group_ballot(unsigned gm, bool x, int grp) {
+  return (__ballot_sync(gm, x) >> (grp * 8)) & 0xFFu;
+}
 
-// The six features of vertex v, computed by one warp (all lanes call; every
-// lane returns them).
+__device__ __forceinline__ bool in_row(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci, int x, int y) {
+  int64_t lo = rp[x], hi = rp[x + 1];
+  const int64_t end = hi;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (ci[mid] < y) lo = mid + 1; else hi = mid;
+  }
+  return lo < end && ci[lo] == y;
+}
+
+// The six features of vertex v, computed by the 8 lanes of one group (all
+// 8 call with the same v; every lane of the group returns them).  qs: 8
+// ints of shared memory for this group.
 __device__ void vertex_features(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                                const int32_t *__restrict__ core, float kmax, float ldmax, int64_t v,
-                                FeatScratch &S, float f[kF]) {
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
+                                const int32_t *__restrict__ core, float kmax, float ldmax, int64_t v, int *qs,
+                                float f[kF]) {
+  const int lane = threadIdx.x & 31, grp = lane >> 3, gl = lane & 7;
+  const unsigned gm = 0xFFu << (grp * 8);
+  const unsigned below = (1u << gl) - 1u;
   const int kv = core[v];
   const int64_t e0 = rp[v], e1 = rp[v + 1];
   int c = 0;
-  for (int64_t eb = e0; eb < e1; eb += 32) {
-    const int64_t e = eb + lane;
+  for (int64_t eb = e0; eb < e1; eb += 8) {
+    const int64_t e = eb + gl;
     int u = -1;
     bool ok = false;
     if (e < e1) {
       u = ci[e];
       ok = core[u] >= kv;
     }
-    const unsigned m = __ballot_sync(0xffffffffu, ok);
+    const unsigned m = group_ballot(gm, ok, grp);
     if (ok) {
-      const int pos = c + __popc(m & lt);
-      if (pos < kQ) S.q[pos] = u;
+      const int pos = c + __popc(m & below);
+      if (pos < kQ) qs[pos] = u;
     }
     c += __popc(m);
   }
-  if (lane < kQ) S.adj[lane] = 0u;
-  __syncwarp();
+  __syncwarp(gm);
   const int q = min(c, kQ);
-  // G[Q]: the warp's four groups of eight lanes take one member's row each.
-  // A short row is read whole (coalesced) and each entry looked up in Q,
-  // which is sorted (row order); in a long row each later member of Q is
-  // found by binary search.  Either way bit j of adj[i] is set for every
-  // member j > i adjacent to member i.
-  const int grp = lane >> 3, gl = lane & 7;
-  for (int i = grp; i < q; i += 4) {
-    const int x = S.q[i];
-    const int64_t r0 = rp[x], r1 = rp[x + 1];
-    uint32_t bits = 0u;
-    if (r1 - r0 <= kScanRow) {
-      for (int64_t e = r0 + gl; e < r1; e += 8) {
-        const int y = ci[e];
-        int lo = i + 1, hi = q;  // members after i: ids above x
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (S.q[mid] < y) lo = mid + 1; else hi = mid;
-        }
-        if (lo < q && S.q[lo] == y) bits |= 1u << lo;
-      }
-    } else {
-      for (int j = i + 1 + gl; j < q; j += 8) {
-        const int y = S.q[j];
-        int64_t lo = r0, hi = r1;
-        while (lo < hi) {
-          const int64_t mid = (lo + hi) >> 1;
-          if (ci[mid] < y) lo = mid + 1; else hi = mid;
-        }
-        if (lo < r1 && ci[lo] == y) bits |= 1u << j;
-      }
+  // the q(q-1)/2 pairs i < j, bit p of `pairs` for pair p (row-major over i)
+  uint32_t pairs = 0u;
+  for (int p = gl; p < q * (q - 1) / 2; p += 8) {
+    int i = 0, r = p;
+    while (r >= q - 1 - i) {
+      r -= q - 1 - i;
+      i++;
     }
-    if (bits) atomicOr(&S.adj[i], bits);
+    const int x = qs[i], y = qs[i + 1 + r];
+    // binary search in the shorter row
+    const bool adj = (rp[x + 1] - rp[x] <= rp[y + 1] - rp[y]) ? in_row(rp, ci, x, y) : in_row(rp, ci, y, x);
+    if (adj) pairs |= 1u << p;
   }
-  __syncwarp();
-  // mirror the upper triangle: lane j gathers bit j of every row above it
-  uint32_t low = 0u;
-  if (lane < q)
-    for (int i = 0; i < lane; i++) low |= ((S.adj[i] >> lane) & 1u) << i;
-  __syncwarp();
-  if (lane < q) S.adj[lane] |= low;
-  __syncwarp();
-  const uint32_t row = lane < q ? S.adj[lane] : 0u;
-  const int t = dev::warp_sum(__popc(row)) / 2;
-  // greedy colouring in index order: lane k holds colour class k; vertex i
-  // joins the first class with none of its neighbours
+  pairs = __reduce_or_sync(gm, pairs);
+  const int t = __popc(pairs);
+  // row gl of G[Q]: member j is adjacent to member gl if pair (min, max) is set
+  uint32_t row = 0u;
+  if (gl < q)
+    for (int j = 0; j < q; j++) {
+      if (j == gl) continue;
+      const int a = min(gl, j), b = max(gl, j);
+      const int pid = a * q - a * (a + 1) / 2 + (b - a - 1);
+      if ((pairs >> pid) & 1u) row |= 1u << j;
+    }
+  // greedy colouring in index order: lane gl holds colour class gl; member
+  // i joins the first class with none of its neighbours
   uint32_t cls = 0u;
   for (int i = 0; i < q; i++) {
-    const uint32_t ai = __shfl_sync(0xffffffffu, row, i);
-    const unsigned clash = __ballot_sync(0xffffffffu, (cls & ai) != 0u);
+    const uint32_t ai = __shfl_sync(gm, row, i, 8);
+    const unsigned clash = group_ballot(gm, (cls & ai) != 0u, grp);
     const int k = __ffs(~clash) - 1;
-    if (lane == k) cls |= 1u << i;
+    if (gl == k) cls |= 1u << i;
   }
-  const int chi = __popc(__ballot_sync(0xffffffffu, cls != 0u));
+  const int chi = __popc(group_ballot(gm, cls != 0u, grp));
   const float d = (float)(e1 - e0);
   f[0] = log1pf(d) / ldmax;
   f[1] = (float)kv / kmax;
@@ -170,25 +161,28 @@ __global__ void __launch_bounds__(256) features_kernel(int64_t n, const int32_t 
                                                        const int32_t *__restrict__ ci,
                                                        const int32_t *__restrict__ core, float kmax, float ldmax,
                                                        float *__restrict__ f) {
-  __shared__ FeatScratch fs[8];
-  const int lane = threadIdx.x & 31;
+  __shared__ int qs[8][4][kQ];
+  const int lane = threadIdx.x & 31, grp = lane >> 3, gl = lane & 7;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t total = list ? *count : n;
-  for (int64_t r = w0; r < total; r += nw) {
+  for (int64_t b = w0 * 4; b < total; b += nw * 4) {
+    const int64_t r = b + grp;
+    if (r >= total) continue;  // the whole group skips
     const int64_t v = list ? list[r] : r;
     float x[kF];
-    vertex_features(rp, ci, core, kmax, ldmax, v, fs[threadIdx.x >> 5], x);
-    if (lane == 0) {
+    vertex_features(rp, ci, core, kmax, ldmax, v, qs[threadIdx.x >> 5][grp], x);
+    if (gl == 0) {
 #pragma unroll
       for (int i = 0; i < kF; i++) f[v * kF + i] = x[i];
     }
   }
 }
 
-// The network in shared memory, laid out for one warp per row: lane j owns
-// hidden units j and j + 32; the first two layers are stored input-major so
-// that a warp's reads of one input's weights are consecutive words.
+// The network in shared memory, laid out for a group of eight lanes per
+// row: lane gl owns hidden units gl, gl + 8, ..., gl + 56; the first two
+// layers are stored input-major so a group's reads of one input's weights
+// are consecutive words.
 struct MlpSmem {
   float w1t[kF][kH];  // w1t[i][j] = W1[j][i]
   float b1[kH];
@@ -216,33 +210,38 @@ __device__ void load_mlp(const uint16_t *__restrict__ wbf, const float *__restri
   __syncthreads();
 }
 
-// The logit of one row x (every lane holds x), by one warp.
-__device__ __forceinline__ float mlp_logit_warp(const MlpSmem &S, const float x[kF]) {
-  const int lane = threadIdx.x & 31;
-  float h0 = S.b1[lane], h1 = S.b1[lane + 32];
+// The logit of one row x (every lane of the group holds x), by the 8 lanes
+// of a group.
+__device__ __forceinline__ float mlp_logit_group(const MlpSmem &S, const float x[kF]) {
+  const int lane = threadIdx.x & 31, grp = lane >> 3, gl = lane & 7;
+  const unsigned gm = 0xFFu << (grp * 8);
+  float h[8];
 #pragma unroll
-  for (int i = 0; i < kF; i++) {
-    h0 = fmaf(S.w1t[i][lane], x[i], h0);
-    h1 = fmaf(S.w1t[i][lane + 32], x[i], h1);
-  }
-  h0 = fmaxf(h0, 0.f);
-  h1 = fmaxf(h1, 0.f);
-  float z0 = S.b2[lane], z1 = S.b2[lane + 32];
-#pragma unroll 8
-  for (int k = 0; k < 32; k++) {
-    const float hk = __shfl_sync(0xffffffffu, h0, k);
-    z0 = fmaf(S.w2t[k][lane], hk, z0);
-    z1 = fmaf(S.w2t[k][lane + 32], hk, z1);
-  }
-#pragma unroll 8
-  for (int k = 0; k < 32; k++) {
-    const float hk = __shfl_sync(0xffffffffu, h1, k);
-    z0 = fmaf(S.w2t[k + 32][lane], hk, z0);
-    z1 = fmaf(S.w2t[k + 32][lane + 32], hk, z1);
-  }
-  float sum = S.w3[lane] * fmaxf(z0, 0.f) + S.w3[lane + 32] * fmaxf(z1, 0.f);
+  for (int t = 0; t < 8; t++) {
+    const int j = gl + 8 * t;
+    float z = S.b1[j];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    for (int i = 0; i < kF; i++) z = fmaf(S.w1t[i][j], x[i], z);
+    h[t] = fmaxf(z, 0.f);
+  }
+  float z[8];
+#pragma unroll
+  for (int t = 0; t < 8; t++) z[t] = S.b2[gl + 8 * t];
+#pragma unroll
+  for (int tk = 0; tk < 8; tk++) {
+#pragma unroll
+    for (int src = 0; src < 8; src++) {
+      const float hk = __shfl_sync(gm, h[tk], src, 8);
+      const int k = src + 8 * tk;
+#pragma unroll
+      for (int t = 0; t < 8; t++) z[t] = fmaf(S.w2t[k][gl + 8 * t], hk, z[t]);
+    }
+  }
+  float sum = 0.f;
+#pragma unroll
+  for (int t = 0; t < 8; t++) sum = fmaf(S.w3[gl + 8 * t], fmaxf(z[t], 0.f), sum);
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) sum += __shfl_xor_sync(gm, sum, o, 8);
   return sum + S.b3;
 }
 
@@ -256,45 +255,48 @@ __device__ __forceinline__ void load_weights(const uint16_t *__restrict__ wbf, c
   __syncthreads();
 }
 
-// logits of n feature rows, one warp per row
+// logits of n feature rows, eight lanes per row
 __global__ void __launch_bounds__(256) forward_kernel(int64_t n, const float *__restrict__ feat,
                                                       const uint16_t *__restrict__ wbf,
                                                       const float *__restrict__ master, float *__restrict__ out) {
   __shared__ MlpSmem S;
   load_mlp(wbf, master, S);
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, grp = lane >> 3, gl = lane & 7;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t r = w0; r < n; r += nw) {
-    const float mine = lane < kF ? feat[r * kF + lane] : 0.f;
+  for (int64_t b = w0 * 4; b < n; b += nw * 4) {
+    const int64_t r = b + grp;
+    if (r >= n) continue;
     float x[kF];
 #pragma unroll
-    for (int i = 0; i < kF; i++) x[i] = __shfl_sync(0xffffffffu, mine, i);
-    const float s = mlp_logit_warp(S, x);
-    if (lane == 0) out[r] = s;
+    for (int i = 0; i < kF; i++) x[i] = feat[r * kF + i];
+    const float s = mlp_logit_group(S, x);
+    if (gl == 0) out[r] = s;
   }
 }
 
-// Learned scores of list[0 .. *count): features and logit fused, one warp
-// per vertex; the n x 6 feature rows never reach memory.
+// Learned scores of list[0 .. *count): features and logit fused, eight
+// lanes per vertex; the n x 6 feature rows never reach memory.
 __global__ void __launch_bounds__(256) score_kernel(const int32_t *__restrict__ list, const int64_t *__restrict__ count,
                                                     const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                                     const int32_t *__restrict__ core, float kmax, float ldmax,
                                                     const uint16_t *__restrict__ wbf, const float *__restrict__ master,
                                                     float *__restrict__ score) {
   __shared__ MlpSmem S;
-  __shared__ FeatScratch fs[8];
+  __shared__ int qs[8][4][kQ];
   load_mlp(wbf, master, S);
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, grp = lane >> 3, gl = lane & 7;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t total = *count;
-  for (int64_t r = w0; r < total; r += nw) {
+  for (int64_t b = w0 * 4; b < total; b += nw * 4) {
+    const int64_t r = b + grp;
+    if (r >= total) continue;
     const int v = list[r];
     float x[kF];
-    vertex_features(rp, ci, core, kmax, ldmax, v, fs[threadIdx.x >> 5], x);
-    const float s = mlp_logit_warp(S, x);
-    if (lane == 0) score[v] = s;
+    vertex_features(rp, ci, core, kmax, ldmax, v, qs[threadIdx.x >> 5][grp], x);
+    const float s = mlp_logit_group(S, x);
+    if (gl == 0) score[v] = s;
   }
 }
 

@@ -106,8 +106,10 @@ struct Pruned {
   int64_t *d_counts = nullptr;     // device: [0] n', [1] arcs, [2] max out-degree, [3..5] roots per class
 };
 // No host synchronisation: sizes stay in pg.d_counts (see read_pruned_counts).
+// part_rank / part_count: keep only the roots whose position in the peel
+// order is part_rank modulo part_count (1: every root).
 int launch_prune(mc_graph *g, int ordering, const float *scores, int32_t warp_max, Pruned *out,
-                 long long spin_limit);
+                 long long spin_limit, int32_t part_rank = 0, int32_t part_count = 1);
 int read_pruned_counts(mc_graph *g, Pruned *out);
 
 // Search (InitialBranch + Branch) over all roots.
@@ -170,6 +172,9 @@ namespace mc {
 // Witness verification of every graph's incumbent: writes per-graph flags.
 int launch_verify(mc_graph *g, int32_t *d_ok);
 int launch_verify_set(mc_graph *g, const int32_t *d_vs, int32_t k, int32_t *d_ok);
+// Replace the peel order by the caller's (host or device) after checking that
+// it is a degeneracy order of the graph (MC_ERR_ARG otherwise).
+int use_order(mc_graph *g, const int32_t *order);
 int launch_validate(mc_graph *g, int32_t *d_bad);
 int launch_gid(mc_graph *g);
 // Indices of the k largest scores (descending), over all vertices.

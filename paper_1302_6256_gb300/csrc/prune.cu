@@ -146,8 +146,11 @@ __global__ void fill_kernel(const int64_t *__restrict__ d_np, const int64_t *__r
 struct RootInfo {
   const int32_t *odeg, *ogid, *best;
   int32_t warp_max;
+  const int32_t *oold, *pos;  // root partition: position of a pruned vertex in the peel order
+  int32_t part_rank, part_count;
   __device__ int cls(int64_t j) const {
     if (j < 0) return -1;
+    if (part_count > 1 && pos[oold[j]] % part_count != part_rank) return -1;  // another part's root
     int g = ogid ? ogid[j] : 0;
     int d = odeg[j];
     if (d < best[g] || d == 0) return -1;  // |P| >= omega~ is needed for a larger clique
@@ -217,7 +220,7 @@ __global__ void gather_scores_kernel(int64_t n, const int64_t *__restrict__ d_np
 }  // namespace
 
 int launch_prune(mc_graph *g, int ordering, const float *scores, int32_t warp_max, Pruned *out,
-                 long long spin_limit) {
+                 long long spin_limit, int32_t part_rank, int32_t part_count) {
   (void)spin_limit;
   // Everything stays on the device: the pruned size, arc count and root
   // counts are written to out->d_counts and read by the later kernels, and
@@ -275,7 +278,7 @@ int launch_prune(mc_graph *g, int ordering, const float *scores, int32_t warp_ma
   // roots in processing order, split by class
   MC_TRY(ws_get(g, "pr.roots", (3 * n + 3) * sizeof(int32_t), &p));
   int32_t *roots = (int32_t *)p;
-  RootInfo ri{odeg, ogid, g->best, warp_max};
+  RootInfo ri{odeg, ogid, g->best, warp_max, oold, g->pos, part_rank, part_count};
   int32_t *tab = nullptr;
   if (ordering == 1 || ordering == 2) {
     MC_TRY(ws_get(g, "pr.tab", (n + 1) * sizeof(int32_t), &p));

@@ -59,6 +59,7 @@ struct SA {
   const int32_t *ocol, *ocore, *oold, *ogid;
   const int32_t *roots;
   const int64_t *nroots;    // device: number of roots in this class
+  const int64_t *np_count;  // device: vertices of the pruned graph
   int32_t *best, *lock, *wit;
   const int64_t *voff;
   int32_t *err;
@@ -246,6 +247,32 @@ __device__ __forceinline__ void hash_insert(int *hk, short *hv, int mask, int ke
     s = (s + 1) & mask;
   }
 }
+
+// Index in P of a later-neighbour entry y, or -1 if y is not in P.
+// Hash form: P's members in an open-addressing table.
+struct HashLookup {
+  const int *hk;
+  const short *hv;
+  int mask;
+  __device__ __forceinline__ int operator()(int y) const { return hash_find(hk, hv, mask, y); }
+};
+// Bitmap form, for a root u whose later ranks (u, n') fit the block's
+// bitmap: bit y - base marks a member of P, pre[w] counts the members in
+// words before w, and P is sorted by decreasing id, so the member y has
+// index p - 1 - (members below y).  Every entry a build reads is a later
+// neighbour of a member, so y - base is never negative.
+struct BitmapLookup {
+  const uint32_t *bm;
+  const uint16_t *pre;
+  int base, p;
+  __device__ __forceinline__ int operator()(int y) const {
+    const int r = y - base;
+    const uint32_t w = bm[r >> 5], bit = 1u << (r & 31);
+    if (!(w & bit)) return -1;
+    return p - 1 - ((int)pre[r >> 5] + __popc(w & (bit - 1u)));
+  }
+};
+constexpr int kBitmapWords = 6144;  // later-rank window of the bitmap lookup: 196,608 ranks
 
 // bitonic sort (descending) of a[0..npow2) in shared memory by `nthr`
 // cooperating threads (thread index t); BLOCK selects the barrier.
@@ -751,9 +778,9 @@ __device__ __forceinline__ void load_P(const SA &a, int u, int om, int *Pidx, in
 // form four groups of eight, each walking a different member's row, with two
 // int4 loads per lane in flight, so a warp keeps eight rows' loads in the
 // memory system instead of one.
-__device__ __forceinline__ void build_rows(const SA &a, const int *Pidx, int p, const int *hk, const short *hv,
-                                           int hmask, uint32_t *A, int Ws, int wid, int nw,
-                                           unsigned long long *count) {
+template <class Lookup>
+__device__ __forceinline__ void build_rows(const SA &a, const int *Pidx, int p, const Lookup &find, uint32_t *A, int Ws,
+                                           int wid, int nw, unsigned long long *count) {
   const int lane = threadIdx.x & 31;
   const int grp = lane >> 3, gl = lane & 7;
   unsigned long long scanned = 0;
@@ -783,7 +810,7 @@ __device__ __forceinline__ void build_rows(const SA &a, const int *Pidx, int p, 
 #pragma unroll
         for (int j = 0; j < 4; j++) {
           if (yy[j] < 0) continue;
-          int b = hash_find(hk, hv, hmask, yy[j]);
+          int b = find(yy[j]);
           if (b >= 0) atomicOr(A + (int64_t)i * Ws + (b >> 5), 1u << (b & 31));
         }
       }
@@ -876,7 +903,7 @@ __global__ void __launch_bounds__(kSW * 32) search_warp_kernel(SA a) {
     const int W = (p + 31) >> 5, Ws = W | 1;
     for (int i = lane; i < p * Ws; i += 32) S.A[i] = 0;
     __syncwarp();
-    build_rows(a, S.Pidx, p, S.hk, S.hv, hmask, S.A, Ws, 0, 1, a.counters + 4);
+    build_rows(a, S.Pidx, p, HashLookup{S.hk, S.hv, hmask}, S.A, Ws, 0, 1, a.counters + 4);
     __syncwarp();
     symmetrize<true>(S.A, Ws, W, p, 0, 1);
     __syncwarp();
@@ -946,7 +973,9 @@ struct BlockLayout {
   static constexpr size_t off_rm = off_al + WMAX * 4;
   static constexpr size_t off_pool = off_rm + WMAX * 4;
   static constexpr size_t off_ctl = off_pool + ((sizeof(Pool<WPL>) + 15) / 16) * 16;
-  static constexpr size_t off_A = off_ctl + 64;
+  static constexpr size_t off_bm = off_ctl + 64;                        // kBitmapWords words
+  static constexpr size_t off_pre = off_bm + (size_t)kBitmapWords * 4;  // kBitmapWords uint16
+  static constexpr size_t off_A = off_pre + (size_t)kBitmapWords * 2;
   static constexpr size_t bytes = off_A + (SM ? (size_t)PCAP * WSMAX * 4 : 0);
 };
 
@@ -1066,11 +1095,15 @@ __global__ void __launch_bounds__(kBT, (SM && PC <= kMidCap) ? 2 : 1) search_blo
   Pool<WPL> *pool = (Pool<WPL> *)(smem + L::off_pool);
   int *ctl = (int *)(smem + L::off_ctl);  // [0] root idx, [1] omega, [2] count, [3] flag, [4] go, [5] error
   uint32_t *A = SM ? (uint32_t *)(smem + L::off_A) : (a.gmat + (int64_t)blockIdx.x * a.gmat_stride);
+  uint32_t *bm = (uint32_t *)(smem + L::off_bm);
+  uint16_t *pre = (uint16_t *)(smem + L::off_pre);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   uint32_t *stk = a.stack + ((int64_t)blockIdx.x * kBW + wid) * a.stack_stride;
   unsigned long long colored = 0, branched = 0, nodes = 0, don = 0;
   const int hmask = L::HCAP - 1;
   const int64_t nroots = *a.nroots;
+  const int64_t npr = *a.np_count;
+  for (int i = tid; i < kBitmapWords; i += kBT) bm[i] = 0u;  // each root clears the bits it set
 
   for (;;) {
     __syncthreads();
@@ -1088,7 +1121,12 @@ __global__ void __launch_bounds__(kBT, (SM && PC <= kMidCap) ? 2 : 1) search_blo
     __syncthreads();
     int om = ctl[1];
     if (a.ocore[u] < om) continue;
-    for (int i = tid; i < L::HCAP; i += kBT) hk[i] = -1;
+    // the later ranks (u, n') fit the bitmap: member lookups by bitmap,
+    // otherwise by hash table
+    const int base = u + 1;
+    const bool use_bm = ((npr - base + 31) >> 5) <= kBitmapWords;
+    if (!use_bm)
+      for (int i = tid; i < L::HCAP; i += kBT) hk[i] = -1;
     for (int i = tid; i < L::PCAP; i += kBT) Pidx[i] = INT_MIN;
     __syncthreads();
     load_P(a, u, om, Pidx, L::PCAP, &ctl[2], tid, kBT);
@@ -1106,14 +1144,53 @@ __global__ void __launch_bounds__(kBT, (SM && PC <= kMidCap) ? 2 : 1) search_blo
     int np2 = 32;
     while (np2 < p) np2 <<= 1;
     bitonic_desc<true>(Pidx, np2, tid, kBT);
-    for (int i = tid; i < p; i += kBT) hash_insert(hk, hv, hmask, Pidx[i], i);
+    const int wwin = (int)((npr - base + 31) >> 5);
+    if (use_bm) {
+      for (int i = tid; i < p; i += kBT) {
+        const int r = Pidx[i] - base;
+        atomicOr(&bm[r >> 5], 1u << (r & 31));
+      }
+      __syncthreads();
+      // pre[w] = members in words [0, w): each thread counts a contiguous
+      // chunk of words, the warps' totals are scanned in rm[], then each
+      // thread writes its chunk's prefixes
+      const int per = (wwin + kBT - 1) / kBT;
+      const int w0 = min(wwin, tid * per), w1 = min(wwin, w0 + per);
+      int mine = 0;
+      for (int w = w0; w < w1; w++) mine += __popc(bm[w]);
+      int incl = mine;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (lane == 31) rm[wid] = (uint32_t)incl;
+      __syncthreads();
+      int before = 0;
+      for (int w = 0; w < wid; w++) before += (int)rm[w];
+      int run = before + incl - mine;
+      for (int w = w0; w < w1; w++) {
+        pre[w] = (uint16_t)run;
+        run += __popc(bm[w]);
+      }
+    } else {
+      for (int i = tid; i < p; i += kBT) hash_insert(hk, hv, hmask, Pidx[i], i);
+    }
     const int W = (p + 31) >> 5, Ws = W | 1;
     for (int64_t i = tid; i < (int64_t)p * Ws; i += kBT) A[i] = 0;
     if (!SM) __threadfence();
     __syncthreads();
-    build_rows(a, Pidx, p, hk, hv, hmask, A, Ws, wid, kBW, a.counters + 5);
+    if (use_bm)
+      build_rows(a, Pidx, p, BitmapLookup{bm, pre, base, p}, A, Ws, wid, kBW, a.counters + 5);
+    else
+      build_rows(a, Pidx, p, HashLookup{hk, hv, hmask}, A, Ws, wid, kBW, a.counters + 5);
     if (!SM) __threadfence();
     __syncthreads();
+    if (use_bm)
+      for (int i = tid; i < p; i += kBT) {
+        const int r = Pidx[i] - base;
+        atomicAnd(&bm[r >> 5], ~(1u << (r & 31)));
+      }
     symmetrize<SM>(A, Ws, W, p, wid, kBW);
     if (!SM) __threadfence();
     __syncthreads();
@@ -1381,6 +1458,7 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_spli
   int32_t *next = (int32_t *)(ctr + 8);
   MC_CUDA_TRY(cudaMemsetAsync(ctr, 0, 16 * sizeof(unsigned long long), g->stream));
   SA a{};
+  a.np_count = pg.d_counts;
   a.orow = pg.orow;
   a.ocol = pg.ocol;
   a.ocore = pg.ocore;

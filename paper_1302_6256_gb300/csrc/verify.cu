@@ -117,6 +117,35 @@ __global__ void verify_one_kernel(int64_t n, const int64_t *rp, const int32_t *c
 
 __global__ void set_one_kernel(int32_t *p) { *p = 1; }
 
+// A caller's vertex order: positions (a duplicate or out-of-range entry sets
+// *bad), then every vertex's later neighbours counted against its core
+// number (a degeneracy order has at most K(v) of them).
+__global__ void order_pos_kernel(int64_t n, const int32_t *__restrict__ order, int32_t *__restrict__ ord,
+                                 int32_t *__restrict__ pos, int32_t *bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = order[i];
+    if (v < 0 || (int64_t)v >= n || atomicCAS(pos + v, -1, (int32_t)i) != -1) {
+      atomicExch(bad, 1);
+      continue;
+    }
+    ord[i] = v;
+  }
+}
+
+__global__ void order_check_kernel(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                   const int32_t *__restrict__ pos, const int32_t *__restrict__ core, int32_t *bad) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = w0; v < n; v += nw) {
+    const int pv = pos[v];
+    int later = 0;
+    for (int64_t e = rp[v] + lane; e < rp[v + 1]; e += 32) later += pos[ci[e]] > pv ? 1 : 0;
+    later = dev::warp_sum(later);
+    if (lane == 0 && later > core[v]) atomicExch(bad, 1);
+  }
+}
+
 }  // namespace
 
 int launch_verify(mc_graph *g, int32_t *d_ok) {
@@ -148,6 +177,34 @@ int launch_validate(mc_graph *g, int32_t *d_bad) {
   validate_kernel<<<blocks, 256, 0, g->stream>>>(g->n, g->nnz, g->row_ptr, g->col_idx, g->gid, g->voff, d_bad);
   g_launches++;
   MC_CUDA_TRY(cudaGetLastError());
+  return MC_OK;
+}
+
+int use_order(mc_graph *g, const int32_t *order) {
+  if (g->n == 0) return MC_OK;
+  void *p;
+  MC_TRY(ws_get(g, "ord.in", (size_t)g->n * 4 + 64, &p));
+  int32_t *staged = (int32_t *)p, *bad = (int32_t *)((char *)p + (size_t)g->n * 4);
+  MC_CUDA_TRY(cudaMemcpyAsync(staged, order, g->n * 4, cudaMemcpyDefault, g->stream));
+  MC_CUDA_TRY(cudaMemsetAsync(bad, 0, 4, g->stream));
+  MC_CUDA_TRY(cudaMemsetAsync(g->pos, 0xff, g->n * 4, g->stream));
+  const int blocks = (int)std::min<int64_t>((g->n + 255) / 256, (int64_t)g->sm_count * 8);
+  order_pos_kernel<<<blocks, 256, 0, g->stream>>>(g->n, staged, g->order, g->pos, bad);
+  g_launches++;
+  int32_t *h = (int32_t *)g->h_small;
+  MC_CUDA_TRY(cudaMemcpyAsync(h, bad, 4, cudaMemcpyDeviceToHost, g->stream));
+  MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (*h == 0) {
+    const int wblocks = (int)std::min<int64_t>((g->n * 32 + 255) / 256, (int64_t)g->sm_count * 16);
+    order_check_kernel<<<wblocks, 256, 0, g->stream>>>(g->n, g->row_ptr, g->col_idx, g->pos, g->core, bad);
+    g_launches++;
+    MC_CUDA_TRY(cudaMemcpyAsync(h, bad, 4, cudaMemcpyDeviceToHost, g->stream));
+    MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  }
+  if (*h) {
+    g->cores_valid = false;  // the peel order was overwritten: recompute it next time
+    return MC_ERR_ARG;
+  }
   return MC_OK;
 }
 

@@ -1,7 +1,8 @@
 """Train the vertex-scoring network of the learned ordering.
 
-Training data: generated graphs (a mix of Chung-Lu and R-MAT, n from 10k to
-200k, a planted clique of 10 to 50 vertices), each solved exactly by this
+Training data: generated graphs (a mix of Chung-Lu graphs with hub cores
+from sparse to dense and R-MAT graphs, n from 10k to 200k, a planted clique
+of 10 to 50 vertices), each solved exactly by this
 library; a vertex is labelled 1 if it is in the maximum clique the exact solve
 returns.  Rows: every positive vertex, plus negatives drawn half from all
 vertices and half from the hard ones (core number >= omega - 1), up to
@@ -32,15 +33,20 @@ DEFAULT_OUT = os.path.join(HERE, "ordering_mlp.npy")
 
 
 def graph_params(i: int, seed: int):
-    """Family and sizes of training graph i (counter-based, reproducible)."""
+    """Family and sizes of training graph i (counter-based, reproducible).
+    Chung-Lu graphs take their weight cap from the hub-to-hub edge
+    probability cap^2 / (n mean), drawn in [0.01, 0.25]: from hub cores that
+    hold small cliques only (the planted clique has a low core number, as in
+    a social network of 10^8 vertices) to dense hub cores."""
     k = gg.key(seed, 5000 + i)
-    u = [(gg.rand_u64(k, j) >> 11) / 9007199254740992.0 for j in range(5)]
+    u = [(gg.rand_u64(k, j) >> 11) / 9007199254740992.0 for j in range(6)]
     planted = 10 + int(u[1] * 41)
     if u[0] < 0.5:
         n = 10_000 + int(u[2] * 190_001)
         gamma = 2.1 + 0.7 * u[3]
-        mean = 6.0 + 14.0 * u[4]
-        return ("chung-lu", dict(n=n, gamma=gamma, mean=mean, cap=max(200.0, n ** 0.5 * 4), planted=planted,
+        mean = 6.0 + 34.0 * u[4]
+        cap = (0.1 + 0.4 * u[5]) * (n * mean) ** 0.5
+        return ("chung-lu", dict(n=n, gamma=gamma, mean=mean, cap=max(50.0, cap), planted=planted,
                                  seed=(seed << 20) + i))
     scale = 14 + int(u[2] * 4)  # 16k .. 131k vertices
     return ("rmat", dict(scale=scale, edge_factor=8 + int(u[3] * 9), planted=planted, seed=(seed << 20) + i))

@@ -394,3 +394,50 @@ def test_autotune_returns_a_working_setting(mc):
     assert opts["warp_max"] in (32, 64, 128) and ms > 0
     om, wit, _ = mc.mc_max_clique(h, **opts)
     assert om == ref_omega(g) and oracle.is_clique(g, wit)
+
+
+def test_partitioned_search_matches_oracle(mc):
+    """The root partition (Section 4.5) on one GPU, its parts solved one after
+    the other with one shared peel order: the largest part is the oracle's
+    omega and every part's witness is a clique of its size; each part
+    examines only its own roots.  (No part waits on another.)"""
+    from paper_1302_6256_gb300.partition import library_steps, partitioned_max_clique
+    graphs = [gg.relabel(tight_instance(5)[0], 3), gg.rmat(14, 16, planted=30, seed=16),
+              gg.chung_lu(20000, 2.3, 12.0, 800.0, planted=18, seed=15), gg.erdos_renyi(400, 0.5, planted=0, seed=19)]
+    for g in graphs:
+        ref = ref_omega(g)
+        h = load(mc, g)
+        mc.mc_core_numbers(h)
+        order = mc.mc_peel_order(h).copy()
+        whole = mc.mc_max_clique(h, order=order)[2]["roots"]
+        for parts in (2, 3):
+            res = [mc.mc_max_clique(h, order=order, part_rank=r, part_count=parts) for r in range(parts)]
+            assert max(om for om, _, _ in res) == ref, (g.name, parts)
+            for om, wit, st in res:
+                assert len(wit) == om and oracle.is_clique(g, wit)
+            # with the same heuristic bound the parts' roots make up all roots
+            if len({st["heuristic_size"] for _, _, st in res}) == 1:
+                assert sum(st["roots"] for _, _, st in res) == whole
+        peel, solve = library_steps(h)
+        om, wit, owner, sizes = partitioned_max_clique(peel, solve, 0, 1, g.n)
+        assert om == ref and oracle.is_clique(g, wit)
+        h.close()
+
+
+def test_order_option_refuses_what_is_not_a_degeneracy_order(mc):
+    g = gg.star(30)  # the centre first: 29 later neighbours, core number 1
+    h = load(mc, g)
+    for bad in (np.arange(30, dtype=np.int32), np.zeros(30, dtype=np.int32),
+                np.r_[np.arange(1, 30), 30].astype(np.int32)):
+        with pytest.raises(mc.MCError) as e:
+            mc.mc_max_clique(h, order=bad)
+        assert e.value.code == mc.MC_ERR_ARG
+    for opts in (dict(part_rank=2, part_count=2), dict(part_rank=1, part_count=0),
+                 dict(order=np.r_[np.arange(1, 30), 0].astype(np.int32), graph=True)):
+        with pytest.raises(mc.MCError):
+            mc.mc_max_clique(h, **opts)
+    # a valid order (the leaves first) and a plain solve still work afterwards
+    om, wit, _ = mc.mc_max_clique(h, order=np.r_[np.arange(1, 30), 0].astype(np.int32))
+    assert om == 2 and oracle.is_clique(g, wit)
+    assert mc.mc_max_clique(h)[0] == 2
+    h.close()
