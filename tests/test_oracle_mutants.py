@@ -19,6 +19,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE_C = os.path.join(ROOT, "oracle", "oracle.c")
 LEARNED_PY = os.path.join(ROOT, "oracle", "learned.py")
+ORDERING_PY = os.path.join(ROOT, "oracle", "ordering.py")
 
 # (name, text in the oracle, replacement, replace every occurrence)
 C_MUTANTS = [
@@ -135,6 +136,26 @@ PY_MUTANTS = [
 ]
 
 
+ORDERING_MUTANTS = [
+    ("order-ties-by-id-not-rank", "k = (len(c), -int(rank[v]))\n            for u in c:",
+     "k = (len(c), -v)\n            for u in c:", False),
+    ("order-candidates-by-id", "cand.sort(key=lambda u: (-int(core[u]), -int(deg[u]), u))", "cand.sort()", False),
+    ("order-candidates-by-degree-first", "cand.sort(key=lambda u: (-int(core[u]), -int(deg[u]), u))",
+     "cand.sort(key=lambda u: (-int(deg[u]), -int(core[u]), u))", False),
+    ("order-accept-checks-start-only", "if all(best[u] == k for u in c):", "if best[v] == k:", False),
+    ("order-members-ascending-degree", "order.extend(sorted(c, key=lambda u: (-int(deg[u]), u)))",
+     "order.extend(sorted(c, key=lambda u: (int(deg[u]), u)))", False),
+    ("order-members-by-id", "order.extend(sorted(c, key=lambda u: (-int(deg[u]), u)))", "order.extend(sorted(c))", False),
+    ("order-dead-candidates-kept", "cand = [u for u in rows[v].tolist() if alive[u]]",
+     "cand = [u for u in rows[v].tolist()]", False),
+    ("order-cliques-by-size", "        for v in sorted(cl):", "        for v in sorted(cl, key=lambda v: -len(cl[v])):", False),
+    ("gap-from-zero", "gaps[0] = abs(r[0] - pos[v])", "gaps[0] = r[0]", False),
+    ("gap-bits-log-gap", "np.log2(1.0 + gaps)", "np.log2(np.maximum(gaps, 1))", False),
+    ("gap-unsorted-row", "r = np.sort(pos[g.col_idx[g.row_ptr[v]:g.row_ptr[v + 1]]])",
+     "r = pos[g.col_idx[g.row_ptr[v]:g.row_ptr[v + 1]]]", False),
+]
+
+
 def _mutate(src, old, new, every):
     count = src.count(old)
     assert count >= 1, "mutation site not found: %r" % old
@@ -175,8 +196,8 @@ def _c_case(tmp, name, old, new, every):
     return name, _run(script)
 
 
-def _py_case(tmp, name, old, new, every):
-    src = _mutate(open(LEARNED_PY).read(), old, new, every)
+def _py_case(tmp, name, old, new, every, module="learned", tests="test_learned_oracle.py"):
+    src = _mutate(open(os.path.join(ROOT, "oracle", module + ".py")).read(), old, new, every)
     path = os.path.join(tmp, name + ".py")
     with open(path, "w") as f:
         f.write(src)
@@ -184,15 +205,19 @@ def _py_case(tmp, name, old, new, every):
         import importlib.util, sys
         sys.path.insert(0, %r)
         import oracle
-        spec = importlib.util.spec_from_file_location("oracle.learned", %r)
+        spec = importlib.util.spec_from_file_location("oracle.%s", %r)
         mod = importlib.util.module_from_spec(spec)
         spec.loader.exec_module(mod)
-        sys.modules["oracle.learned"] = mod
-        oracle.learned = mod
+        sys.modules["oracle.%s"] = mod
+        setattr(oracle, %r, mod)
         import pytest
         sys.exit(pytest.main(%s))
-    """) % (ROOT, path, PYTEST_ARGS % repr(os.path.join("tests", "test_learned_oracle.py")))
+    """) % (ROOT, module, path, module, module, PYTEST_ARGS % repr(os.path.join("tests", tests)))
     return name, _run(script)
+
+
+def _ord_case(tmp, name, old, new, every):
+    return _py_case(tmp, name, old, new, every, "ordering", "test_ordering_oracle.py")
 
 
 def test_unmutated_copies_pass(tmp_path):
@@ -201,11 +226,13 @@ def test_unmutated_copies_pass(tmp_path):
     assert rc == 0, tail
     rc, tail = _py_case(str(tmp_path), "identity_py", "import numpy as np", "import numpy as np", False)[1]
     assert rc == 0, tail
+    rc, tail = _ord_case(str(tmp_path), "identity_ord", "import numpy as np", "import numpy as np", False)[1]
+    assert rc == 0, tail
 
 
-@pytest.mark.parametrize("kind", ["c", "py"])
+@pytest.mark.parametrize("kind", ["c", "py", "ord"])
 def test_every_planted_mistake_is_caught(tmp_path, kind):
-    cases, fn = (C_MUTANTS, _c_case) if kind == "c" else (PY_MUTANTS, _py_case)
+    cases, fn = {"c": (C_MUTANTS, _c_case), "py": (PY_MUTANTS, _py_case), "ord": (ORDERING_MUTANTS, _ord_case)}[kind]
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
         results = list(ex.map(lambda m: fn(str(tmp_path), *m), cases))
     # pytest exit 1: a pin failed; a negative status: the copy crashed; 2-5
