@@ -35,6 +35,57 @@ from __future__ import annotations
 import numpy as np
 
 
+def _greedy(rows, nbs, core, deg, v, alive):
+    """Algorithm 1's greedy clique from v over the alive vertices: scan v's
+    alive neighbours by decreasing core number (ties: larger degree, then
+    smaller id) and add each one adjacent to every member so far."""
+    cand = [u for u in rows[v].tolist() if alive[u]]
+    cand.sort(key=lambda u: (-int(core[u]), -int(deg[u]), u))
+    c = [v]
+    for u in cand:
+        if all(u in nbs[x] for x in c):
+            c.append(u)
+    return c
+
+
+def greedy_clique(g, core, v, alive):
+    """The greedy clique grown from v in one round, `alive` the boolean mask
+    of the vertices not yet placed (for checking single cliques of a large
+    order one by one: rows are read only where the scan needs them)."""
+
+    class Rows(dict):
+        def __missing__(self, x):
+            r = g.col_idx[g.row_ptr[x]:g.row_ptr[x + 1]]
+            self[x] = r
+            return r
+
+    class Sets(dict):
+        def __missing__(self, x):
+            r = set(g.col_idx[g.row_ptr[x]:g.row_ptr[x + 1]].tolist())
+            self[x] = r
+            return r
+
+    return _greedy(Rows(), Sets(), core, np.diff(g.row_ptr), int(v), alive)
+
+
+def relabel(g, order):
+    """The CSR of the graph with vertex order[i] renamed i, every row sorted
+    ascending: (row_ptr, col_idx)."""
+    n = g.n
+    order = np.asarray(order, np.int64)
+    assert sorted(order.tolist()) == list(range(n)), "order must be a permutation"
+    pos = np.empty(n, np.int64)
+    pos[order] = np.arange(n)
+    rp = np.zeros(n + 1, np.int64)
+    rows = []
+    for i in range(n):
+        v = order[i]
+        rows.append(np.sort(pos[g.col_idx[g.row_ptr[v]:g.row_ptr[v + 1]]]))
+        rp[i + 1] = rp[i] + rows[-1].size
+    ci = np.concatenate(rows).astype(np.int32) if rows else np.zeros(0, np.int32)
+    return rp, ci
+
+
 def clique_order(g, core, rank=None):
     """Returns (order, group_starts, group_round): order is a permutation of
     the vertices (order[i] = the vertex placed at position i); the cliques
@@ -52,13 +103,7 @@ def clique_order(g, core, rank=None):
     while alive.any():
         cl = {}
         for v in np.nonzero(alive)[0].tolist():
-            cand = [u for u in rows[v].tolist() if alive[u]]
-            cand.sort(key=lambda u: (-int(core[u]), -int(deg[u]), u))
-            c = [v]
-            for u in cand:
-                if all(u in nbs[x] for x in c):
-                    c.append(u)
-            cl[v] = c
+            cl[v] = _greedy(rows, nbs, core, deg, v, alive)
         best = {}
         for v, c in cl.items():
             k = (len(c), -int(rank[v]))

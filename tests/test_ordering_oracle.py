@@ -79,7 +79,7 @@ def test_first_clique_is_the_deterministic_heuristic():
         groups = [set(order[starts[j]:starts[j + 1]].tolist()) for j in range(len(starts) - 1)]
         # C(v*) of the largest key over all start vertices is accepted in round 0
         assert H in groups and rnd[groups.index(H)] == 0
-        assert len(H) == max(len(c) for c in groups)
+        assert len(H) == max(len(c) for c, r in zip(groups, rnd) if r == 0)
 
 
 @pytest.mark.parametrize("seed", range(4))
@@ -117,3 +117,41 @@ def test_gap_bits_closed_forms():
     # reversing the order of a path changes nothing (gaps are symmetric)
     g = gg.path(10)
     assert OO.gap_bits(g, np.arange(10)[::-1]) == pytest.approx(OO.gap_bits(g, np.arange(10)))
+
+
+def test_greedy_clique_alone_matches_the_rounds():
+    """Each clique of the order is the greedy clique of one of its members
+    over the vertices not placed before its round."""
+    g = gg.rmat(9, 8, planted=8, seed=4)
+    K = oracle.core_numbers(g)
+    order, starts, rnd = OO.clique_order(g, K)
+    for j in range(0, len(rnd), 7):
+        first = starts[np.searchsorted(rnd, rnd[j])]
+        alive = np.zeros(g.n, bool)
+        alive[order[first:]] = True
+        grp = sorted(order[starts[j]:starts[j + 1]].tolist())
+        assert any(sorted(OO.greedy_clique(g, K, v, alive)) == grp for v in grp)
+
+
+def test_relabel_definition():
+    g = gg.rmat(8, 6, seed=2)
+    # identity: the graph itself
+    rp, ci = OO.relabel(g, np.arange(g.n))
+    assert np.array_equal(rp, g.row_ptr) and np.array_equal(ci, g.col_idx)
+    perm = np.random.default_rng(3).permutation(g.n)
+    rp, ci = OO.relabel(g, perm)
+    # degrees follow the vertices; every edge maps to an edge; rows sorted
+    assert np.array_equal(np.diff(rp), np.diff(g.row_ptr)[perm])
+    pos = np.empty(g.n, np.int64)
+    pos[perm] = np.arange(g.n)
+    for v in range(g.n):
+        row = ci[rp[pos[v]]:rp[pos[v] + 1]]
+        assert np.all(np.diff(row) > 0)
+        assert set(row.tolist()) == set(pos[g.col_idx[g.row_ptr[v]:g.row_ptr[v + 1]]].tolist())
+    # the inverse permutation gives the original back
+    h = gg.Graph(rp, ci, "relabelled")
+    rp2, ci2 = OO.relabel(h, pos)
+    assert np.array_equal(rp2, g.row_ptr) and np.array_equal(ci2, g.col_idx)
+    # gap cost is the same whether computed on the relabelled CSR with the
+    # identity or on the original with the order
+    assert OO.gap_bits(g, perm) == pytest.approx(OO.gap_bits(h, np.arange(g.n)))
