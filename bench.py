@@ -373,6 +373,77 @@ def run_batch(args):
                       "arms": out_arms}), flush=True)
 
 
+def run_sweep(args):
+    """The size sweep of the social-network recipe (the shape of the paper's
+    scaling experiment): Chung-Lu graphs with Pareto exponent 2.1, mean
+    degree 36, weight cap 10,000 and a planted clique of 80 (seed 5), n = 10^3
+    ... 10^7 (10^8 is the chung-lu-100m workload); seconds to exact omega and
+    edges/s of the default solve, device-resident CSR, CUDA events."""
+    import torch
+    import graphgen as gg
+    import paper_1302_6256_gb300 as mc
+
+    mc.load_library()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    rows = []
+    for e in range(3, 3 + args.sweep_points):
+        n = 10 ** e
+        g = gg.chung_lu(n, 2.1, 36.0, 10000.0, planted=80, seed=5)
+        h = mc.mc_load_csr(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col_idx).to(dev), 0,
+                           stream=stream)
+        steps = args.steps if n < 10 ** 6 else 1
+        ms, res = _timed(lambda: mc.mc_max_clique(h), stream, steps, 1 if n >= 10 ** 6 else args.warmup)
+        om, _, st = res[-1]
+        rows.append({"n": g.n, "m": g.m, "omega": om, "max_core": st["max_core"], "ms": ms,
+                     "edges_per_s": g.m / (ms / 1e3), "nodes": st["nodes"], "tasks": st["tasks"],
+                     "stages_ms": {k: st[k] for k in ("ms_cores", "ms_heuristic", "ms_prune", "ms_search")}})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        h.close()
+    last = rows[-1]
+    print(json.dumps({"metric": METRIC, "value": last["edges_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": last["ms"], "higher_is_better": True, "dtype": "int32",
+                      "data": "synthetic",
+                      "config": {"workload": "chung-lu sweep gamma=2.1 mean=36 cap=10000 planted=80 seed=5",
+                                 "form": "default"},
+                      "sweep": rows}), flush=True)
+
+
+def run_order(args):
+    """The clique-peeling vertex order (Section 6.2, taken in rounds) of R-MAT
+    scale 22: edges/s of the order (device-resident CSR, CUDA events), its
+    rounds and cliques, and the gap-coding cost (mean log2(1 + gap) bits per
+    adjacency entry) of the vertex ids as generated, of the degeneracy order
+    and of the clique order."""
+    import numpy as np
+    import torch
+    import paper_1302_6256_gb300 as mc
+    from graphgen import workloads as W
+
+    mc.load_library()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    g = W.rmat_s22()
+    h = mc.mc_load_csr(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col_idx).to(dev), 0, stream=stream)
+    ms, res = _timed(lambda: mc.mc_clique_order(h), stream, args.steps, args.warmup)
+    order, starts, rounds, st = res[-1]
+    sizes = np.diff(starts)
+    peel = mc.mc_peel_order(h).copy()
+    t0 = time.time()
+    bits = {"ids": mc.mc_gap_bits(h), "degeneracy": mc.mc_gap_bits(h, peel), "clique": mc.mc_gap_bits(h, order)}
+    gap_s = (time.time() - t0) / 3
+    h.close()
+    print(json.dumps({"metric": "edges/s of the clique-peeling order", "value": g.m / (ms / 1e3), "unit": "edges/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                      "higher_is_better": True, "dtype": "int32", "data": "synthetic",
+                      "config": {"workload": W.RMAT_S22, "n": g.n, "m": g.m, "l2": "inputs > L2 (537 MB CSR)"},
+                      "rounds": st["rounds"], "cliques": int(sizes.size), "largest": int(sizes.max()),
+                      "cliques_by_size": {str(k): int(v) for k, v in zip(*np.unique(np.minimum(sizes, 8),
+                                                                                   return_counts=True))},
+                      "grows": st["grows"], "tests": st["tests"], "ms_device": st["ms"],
+                      "gap_bits": bits, "gap_call_s": gap_s}), flush=True)
+
+
 def run_single(args):
     """One graph: the plain GPU B&B, the chosen form (the faster Algorithm 1
     extent) and the learned form (scores of the vertices that can beat the
@@ -429,7 +500,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="rmat-s22", choices=["rmat-s22", "er-batch", "rmat-s24", "chung-lu-20k", "chung-lu-100m"])
+    ap.add_argument("--workload", default="rmat-s22",
+                    choices=["rmat-s22", "er-batch", "rmat-s24", "chung-lu-20k", "chung-lu-100m", "chung-lu-sweep",
+                             "clique-order"])
+    ap.add_argument("--sweep-points", type=int, default=5, help="chung-lu-sweep: n = 10^3 .. 10^(2 + points)")
     ap.add_argument("--form", default="chosen", choices=["chosen", "plain", "per-graph", "learned", "all"],
                     help="chosen: the autotuned solve (on R-MAT scale 22 both arms are timed and this one is the "
                          "headline; graph replay for batches); plain: direct launches, degeneracy order, no task "
@@ -454,6 +528,10 @@ def main():
         return run_reference(args)
     if args.workload == "er-batch":
         return run_batch(args)
+    if args.workload == "chung-lu-sweep":
+        return run_sweep(args)
+    if args.workload == "clique-order":
+        return run_order(args)
     if args.workload != "rmat-s22" or args.form in ("learned", "all"):
         return run_single(args)
 

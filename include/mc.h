@@ -134,6 +134,25 @@ typedef struct {
    * graph = 1 or a batch (MC_ERR_ARG).  part_count 0 or 1: every root. */
   const int32_t *order;
   int32_t part_rank, part_count;
+  /* Block-worker layout (an autotuner coordinate): 0 = (default) roots of at
+   * most 512 candidates searched in a 512-bit-row layout at two blocks per
+   * SM, larger ones in the 1,024-bit-row layout at one block per SM; 1 =
+   * every block-class root in the 1,024-bit-row layout. */
+  int32_t layout;
+  /* 1 = neighbourhood builds look up P's members in a hash table only; 0 =
+   * (default) in a shared-memory bitmap of the root's later ranks when those
+   * fit (196,608 ranks), in the hash table otherwise (an autotuner
+   * coordinate). */
+  int32_t no_bitmap;
+  /* Work-triggered re-pruning (the paper's periodic explicit rebuild,
+   * Algorithm 2 line 9, triggered by progress instead of a clock): with
+   * repeel = R >= 2 the roots are searched in R ranges of peel positions,
+   * the densest first; before each later range, if omega has risen above the
+   * bound the pruned graph was built with, the pruned graph is rebuilt with
+   * the new bound (vertices with K(v) < omega dropped, rows shortened).
+   * One graph, degeneracy-order roots, direct launches only (MC_ERR_ARG
+   * with graph = 1, ordering != 0 or a batch).  0 or 1 = one pass. */
+  int32_t repeel;
 } mc_options;
 
 /* Per-call statistics (all times in milliseconds, CUDA events). */
@@ -162,6 +181,7 @@ typedef struct {
   double ms_learned;           /* of ms_heuristic: scoring the candidates and picking the seeds
                                   (the learned form only) */
   int64_t learned_scored;      /* vertices the learned form scored */
+  int64_t rebuilds;            /* pruned-graph rebuilds of a re-pruning solve (repeel) */
 } mc_stats;
 
 /* ------------------------------------------------------------ graphs --- */
@@ -227,8 +247,10 @@ int mc_max_clique_batch(mc_graph *g, const mc_options *opt, int32_t *omegas_out,
  * graph `repeats` times per candidate setting, one coordinate at a time,
  * starting from `base` (NULL = defaults): the work split between warp and
  * block workers (warp_max 32, 64, 128), then the task queue (no_split, or
- * split_nodes 1024, 4096, 16384), then, from the default heuristic, its
- * warm-up part alone (heuristic 3), then CUDA-graph replay (graph 0, 1).  It
+ * split_nodes 1024, 4096, 16384), then the block-worker layout (layout 0,
+ * 1) and the build's member lookup (no_bitmap 0, 1), then, from the default
+ * heuristic, its warm-up part alone (heuristic 3), then CUDA-graph replay
+ * (graph 0, 1).  It
  * writes the fastest setting to *best_out and its mean time (ms) to
  * *best_ms_out (nullable).  Every trial is a full exact solve. */
 int mc_autotune(mc_graph *g, const mc_options *base, int32_t repeats, mc_options *best_out, double *best_ms_out);
@@ -273,6 +295,55 @@ int mc_verify_clique(mc_graph *g, const int32_t *vertices, int32_t k, int32_t *i
  * and must be serialised by the caller. */
 int mc_core_numbers_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, int32_t *core_out,
                             int32_t *max_core_out, void *cuda_stream);
+
+/* ------------------------------------- clique-peeling vertex order --- */
+/* Section 6.2 orders the vertices for compression: take a large clique
+ * (with the heuristic), remove it, repeat; the vertices follow the cliques
+ * in the order they were taken, each clique's members by degree.  Here the
+ * cliques are taken in rounds.  In a round every remaining vertex v grows
+ * Algorithm 1's greedy clique C(v) over the remaining vertices (candidates
+ * by decreasing core number, then degree, then smaller id; core numbers and
+ * degrees of the whole graph); C(v) is taken iff no clique of a larger key
+ * (|C|, then the smaller tie rank of its start vertex) holds one of its
+ * vertices.  The cliques taken in a round are disjoint and include the one
+ * of largest key; they are appended by increasing start vertex, members by
+ * decreasing degree (ties: smaller id).  The first clique is the
+ * deterministic heuristic's (mc_heuristic_clique mode 1) when rank is NULL.
+ *   rank: NULL (tie rank = vertex id) or n int32, a permutation of [0, n)
+ *     (MC_ERR_ARG otherwise).  A rank that follows the graph's structure
+ *     (a path numbered end to end) takes a round per clique; a random
+ *     permutation avoids that.
+ *   order_out: n int32, order_out[i] = the vertex placed at position i.
+ *   group_starts_out: n+1 int64 capacity; clique j occupies positions
+ *     group_starts_out[j] .. group_starts_out[j+1]-1 (groups+1 entries
+ *     written, the last = n).
+ *   group_round_out: NULL or n int32 capacity: the round of clique j.
+ *   groups_out: number of cliques.  stats: NULL or filled.
+ * Outputs may be host or device memory.  Only single graphs (a batch handle
+ * gives MC_ERR_ARG).  Device memory: about 4 bytes per CSR entry plus 30
+ * bytes per vertex of workspace, kept by the handle. */
+typedef struct {
+  int32_t rounds;  /* rounds taken */
+  int32_t pad_;
+  int64_t grows;   /* greedy cliques grown (a clique is regrown only when a member was taken) */
+  int64_t tests;   /* candidate tests of the greedy filters */
+  double ms;       /* device time of the call */
+} mc_order_stats;
+int mc_clique_order(mc_graph *g, const int32_t *rank, int32_t *order_out, int64_t *group_starts_out,
+                    int32_t *group_round_out, int64_t *groups_out, mc_order_stats *stats);
+
+/* The graph relabelled by an order: new vertex i is order[i] (n int32, a
+ * permutation, MC_ERR_ARG otherwise); row_ptr_out (n+1 int64) and col_idx_out
+ * (row_ptr[n] int32) receive the new CSR with every row sorted ascending.
+ * Host or device memory.  Single graphs only. */
+int mc_relabel(mc_graph *g, const int32_t *order, int64_t *row_ptr_out, int32_t *col_idx_out);
+
+/* Gap-coding cost of an order, the locality that gap-based adjacency
+ * compression (bvgraph and its kind) exploits: relabel by the order (NULL =
+ * the graph as it is), then in every row p, sorted, code the gap from p to
+ * the first entry and between consecutive entries; *bits_out = the mean of
+ * log2(1 + gap) over all entries (0 without edges).  Lower is better. */
+int mc_gap_bits(mc_graph *g, const int32_t *order, double *bits_out);
 
 /* ------------------------------------------ learned vertex ordering --- */
 /* An extension of the method, not in the paper: a small network scores the

@@ -49,7 +49,8 @@ class Options(ctypes.Structure):
                 ("seeds", ctypes.c_int32), ("graph", ctypes.c_int32),
                 ("no_split", ctypes.c_int32), ("split_nodes", ctypes.c_int32),
                 ("mlp", ctypes.c_void_p), ("order", ctypes.c_void_p), ("part_rank", ctypes.c_int32),
-                ("part_count", ctypes.c_int32)]
+                ("part_count", ctypes.c_int32), ("layout", ctypes.c_int32), ("no_bitmap", ctypes.c_int32),
+                ("repeel", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -68,7 +69,7 @@ class Stats(ctypes.Structure):
                 ("max_core", ctypes.c_int32), ("heuristic_size", ctypes.c_int32),
                 ("omega", ctypes.c_int32), ("verified", ctypes.c_int32),
                 ("prune_row_entries", ctypes.c_int64), ("ms_learned", ctypes.c_double),
-                ("learned_scored", ctypes.c_int64)]
+                ("learned_scored", ctypes.c_int64), ("rebuilds", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -130,6 +131,11 @@ def _extend(L):
     L.mc_mlp_train_step.argtypes = [vp, vp, vp, i64, f32, f32, ctypes.POINTER(f32)]
     L.mc_autotune.argtypes = [vp, vp, i32, vp, ctypes.POINTER(ctypes.c_double)]
     L.mc_autotune.restype = ctypes.c_int
+    L.mc_clique_order.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(i64), vp]
+    L.mc_relabel.argtypes = [vp, vp, vp, vp]
+    L.mc_gap_bits.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double)]
+    for name in ("mc_clique_order", "mc_relabel", "mc_gap_bits"):
+        getattr(L, name).restype = ctypes.c_int
     for name in ("mc_features", "mc_mlp_create", "mc_mlp_get_params", "mc_mlp_set_params", "mc_mlp_forward",
                  "mc_mlp_gradient", "mc_mlp_train_step"):
         getattr(L, name).restype = ctypes.c_int
@@ -313,7 +319,8 @@ def _scores_arg(scores, n):
 
 
 def _options(n, ordering=0, no_neigh_cores=False, heuristic=0, warp_max=0, spin_limit=0, scores=None, seeds=0,
-             graph=False, no_split=False, split_nodes=0, mlp=None, order=None, part_rank=0, part_count=0):
+             graph=False, no_split=False, split_nodes=0, mlp=None, order=None, part_rank=0, part_count=0, layout=0,
+             no_bitmap=False, repeel=0):
     scores = _scores_arg(scores, n)
     o = Options()
     if order is not None:
@@ -325,6 +332,9 @@ def _options(n, ordering=0, no_neigh_cores=False, heuristic=0, warp_max=0, spin_
         o._order_ref = okeep
     o.part_rank = part_rank
     o.part_count = part_count
+    o.layout = layout
+    o.no_bitmap = 1 if no_bitmap else 0
+    o.repeel = repeel
     if mlp is not None:
         if not isinstance(mlp, MLP):
             raise TypeError("mlp must be an MLP handle")
@@ -382,6 +392,59 @@ def mc_peel_order(g: Graph, out=None):
     p, keep = _ptr(_out(out, np.int32, g.n, "out"))
     _check(L.mc_peel_order(g.handle, p), "mc_peel_order")
     return out[:g.n]
+
+
+class OrderStats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int32), ("pad_", ctypes.c_int32), ("grows", ctypes.c_int64),
+                ("tests", ctypes.c_int64), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+def mc_clique_order(g: Graph, rank=None):
+    """Clique-peeling vertex order (Section 6.2, taken in rounds).  Returns
+    (order, group_starts, group_round, stats): numpy arrays on the host;
+    clique j occupies order[group_starts[j]:group_starts[j+1]]."""
+    L = load_library()
+    n = g.n
+    order = np.zeros(max(n, 1), np.int32)
+    starts = np.zeros(n + 1, np.int64)
+    rounds = np.zeros(max(n, 1), np.int32)
+    rk = _in(rank, np.int32, "rank") if rank is not None else None
+    rp, keep = _ptr(rk)
+    groups = ctypes.c_int64(0)
+    st = OrderStats()
+    _check(L.mc_clique_order(g.handle, rp, order.ctypes.data, starts.ctypes.data, rounds.ctypes.data,
+                             ctypes.byref(groups), ctypes.byref(st)), "mc_clique_order")
+    k = groups.value
+    return order[:n], starts[:k + 1], rounds[:k], st.as_dict()
+
+
+def mc_relabel(g: Graph, order):
+    """The CSR relabelled by `order` (new vertex i = order[i]), rows sorted:
+    (row_ptr int64, col_idx int32) numpy arrays."""
+    L = load_library()
+    order = _in(order, np.int32, "order")
+    op, keep = _ptr(order)
+    n, edges = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(L.mc_graph_info(g.handle, ctypes.byref(n), ctypes.byref(edges), None), "mc_graph_info")
+    nnz = 2 * edges.value
+    rp = np.zeros(g.n + 1, np.int64)
+    ci = np.zeros(max(nnz, 1), np.int32)
+    _check(L.mc_relabel(g.handle, op, rp.ctypes.data, ci.ctypes.data), "mc_relabel")
+    return rp, ci[:nnz]
+
+
+def mc_gap_bits(g: Graph, order=None) -> float:
+    """Mean log2(1 + gap) per adjacency entry of the graph relabelled by
+    `order` (None: as loaded)."""
+    L = load_library()
+    o = _in(order, np.int32, "order") if order is not None else None
+    op, keep = _ptr(o)
+    out = ctypes.c_double(0.0)
+    _check(L.mc_gap_bits(g.handle, op, ctypes.byref(out)), "mc_gap_bits")
+    return out.value
 
 
 def mc_verify_clique(g: Graph, vertices) -> bool:
@@ -498,4 +561,5 @@ def mc_autotune(g: Graph, repeats: int = 2, **opts):
     ms = ctypes.c_double(0)
     _check(L.mc_autotune(g.handle, ctypes.byref(base), repeats, ctypes.byref(best), ctypes.byref(ms)), "mc_autotune")
     return {"warp_max": best.warp_max, "no_split": bool(best.no_split), "split_nodes": best.split_nodes,
-            "heuristic": best.heuristic, "graph": bool(best.graph)}, ms.value
+            "layout": best.layout, "no_bitmap": bool(best.no_bitmap), "heuristic": best.heuristic,
+            "graph": bool(best.graph)}, ms.value

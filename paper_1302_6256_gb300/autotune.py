@@ -25,7 +25,7 @@ def _gpu_name() -> str:
 
 # Version of the tuner's coordinate list: cached results from an older list
 # are tuned again, so a coordinate added later is never hidden by the cache.
-COORDS = "v3:warp_max,split,heuristic,layout,graph"
+COORDS = "v3:warp_max,split,layout,no_bitmap,heuristic,graph"
 
 
 def tuned(g, key: str, repeats: int = 2, cache: str = CACHE, **base):

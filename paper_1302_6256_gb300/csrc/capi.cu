@@ -265,9 +265,15 @@ static int ensure_cores(mc_graph *g, long long spin) {
   return launch_core_numbers(g, spin);
 }
 
+// Milliseconds between two recorded events; 0 when either was never
+// recorded (the failed query's error is consumed, so a later launch check
+// does not report it).
 static float elapsed(cudaEvent_t a, cudaEvent_t b) {
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, a, b);
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+    (void)cudaGetLastError();
+    ms = 0.f;
+  }
   return ms;
 }
 
@@ -296,6 +302,64 @@ static int check_options(const mc_options *opt, mc_options *o) {
       (o->part_count <= 1 && o->part_rank != 0))
     return MC_ERR_ARG;
   if (o->order && o->graph) return MC_ERR_ARG;
+  if (o->layout < 0 || o->layout > 1 || o->no_bitmap < 0 || o->no_bitmap > 1) return MC_ERR_ARG;
+  if (o->repeel < 0 || (o->repeel > 1 && (o->graph || o->ordering != 0))) return MC_ERR_ARG;
+  return MC_OK;
+}
+
+// The search with work-triggered re-pruning: the kept vertices form a suffix
+// of the peel order (K(v) >= bound); its roots are searched in o.repeel
+// ranges of peel positions, densest first, and before each later range the
+// pruned graph is rebuilt if the incumbent has risen above the bound it was
+// built with (else only the root lists are made).  Reads the incumbent and
+// the pruned size on the host between ranges.
+static int search_in_ranges(mc_graph *g, const mc_options &o, Pruned *pg, SearchCounters *sc, long long spin) {
+  const int32_t pr = o.part_count > 1 ? o.part_rank : 0, pc = std::max(o.part_count, 1);
+  int32_t *h = (int32_t *)((char *)g->h_small + 3072);
+  MC_CUDA_TRY(cudaMemcpyAsync(h, g->best, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
+  MC_TRY(launch_prune(g, 0, nullptr, g->warp_max_used, pg, spin, pr, pc));
+  MC_TRY(read_pruned_counts(g, pg));  // synchronises: *h is the bound the pruned graph was built with
+  int32_t bound = *h;
+  const int64_t n0 = pg->n;
+  MC_TRY(record_event(g, 3));
+  SearchCounters acc{};
+  g->repeel_rebuilds = 0;
+  g->repeel_roots = 0;
+  const int R = o.repeel;
+  bool searched = false;
+  for (int c = 0; c < R; c++) {
+    const int64_t hi = g->n - n0 * c / R, lo = g->n - n0 * (c + 1) / R;
+    if (hi <= lo) continue;
+    if (c > 0) {
+      MC_CUDA_TRY(cudaMemcpyAsync(h, g->best, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
+      MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    }
+    if (c > 0 && *h > bound) {
+      bound = *h;
+      MC_TRY(launch_prune(g, 0, nullptr, g->warp_max_used, pg, spin, pr, pc, lo, hi));
+      g->repeel_rebuilds++;
+    } else {
+      MC_TRY(relaunch_roots(g, g->warp_max_used, pg, pr, pc, lo, hi));
+    }
+    MC_TRY(launch_search(g, *pg, o.no_neigh_cores, o.no_split, o.split_nodes, spin, sc, o.layout, o.no_bitmap));
+    searched = true;
+    MC_TRY(read_search_counters(g, sc));
+    MC_TRY(read_pruned_counts(g, pg));
+    g->repeel_roots += pg->nroots_small + pg->nroots_block + pg->nroots_big;
+    acc.roots_colored += sc->roots_colored;
+    acc.roots_branched += sc->roots_branched;
+    acc.nodes += sc->nodes;
+    acc.donations += sc->donations;
+    acc.entries += sc->entries;
+    acc.entries_block += sc->entries_block;
+    acc.tasks += sc->tasks;
+  }
+  // nothing to search (every vertex pruned): the search-stage events still
+  // bracket an empty interval
+  if (!searched)
+    for (int i = 8; i <= 12; i++) MC_TRY(record_event(g, i));
+  acc.d_counters = sc->d_counters;
+  g->repeel_acc = acc;
   return MC_OK;
 }
 
@@ -368,11 +432,18 @@ static int enqueue_solve(mc_graph *g, const mc_options &o, Pruned *pg, SearchCou
   MC_TRY(record_event(g, 2));
   int32_t *h_heur = (int32_t *)((char *)g->h_small + 1024);
   MC_CUDA_TRY(cudaMemcpyAsync(h_heur, g->best, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
-  if (g->n > 0)
-    MC_TRY(launch_prune(g, o.ordering, d_scores, g->warp_max_used, pg, spin, o.part_count > 1 ? o.part_rank : 0,
-                        std::max(o.part_count, 1)));
-  MC_TRY(record_event(g, 3));
-  if (g->n > 0) MC_TRY(launch_search(g, *pg, o.no_neigh_cores, o.no_split, o.split_nodes, spin, sc));
+  g->repeel_ran = o.repeel > 1 && g->n > 0;
+  if (g->repeel_ran) {
+    if (g->count > 1) return MC_ERR_ARG;
+    MC_TRY(search_in_ranges(g, o, pg, sc, spin));
+  } else {
+    if (g->n > 0)
+      MC_TRY(launch_prune(g, o.ordering, d_scores, g->warp_max_used, pg, spin, o.part_count > 1 ? o.part_rank : 0,
+                          std::max(o.part_count, 1)));
+    MC_TRY(record_event(g, 3));
+    if (g->n > 0)
+      MC_TRY(launch_search(g, *pg, o.no_neigh_cores, o.no_split, o.split_nodes, spin, sc, o.layout, o.no_bitmap));
+  }
   trivial_kernel<<<std::max(1, std::min(g->count / 256 + 1, 1024)), 256, 0, g->stream>>>(
       g->count, g->gid ? g->voff : nullptr, g->n, g->best, g->wit);
   g_launches++;
@@ -413,11 +484,16 @@ static int finish_solve(mc_graph *g, Pruned *pg, SearchCounters *sc, const int32
     MC_TRY(read_pruned_counts(g, pg));
     st->pruned_n = pg->n;
     st->pruned_arcs = pg->arcs;
-    st->roots = pg->nroots_small + pg->nroots_block + pg->nroots_big;
+    st->roots = g->repeel_ran ? g->repeel_roots : pg->nroots_small + pg->nroots_block + pg->nroots_big;
     st->prune_row_entries = pg->row_entries;
   }
-  if (g->n > 0 && sc->d_counters) {
+  if (g->n > 0 && g->repeel_ran) {
+    *sc = g->repeel_acc;
+    st->rebuilds = g->repeel_rebuilds;
+  } else if (g->n > 0 && sc->d_counters) {
     MC_TRY(read_search_counters(g, sc));
+  }
+  if (g->n > 0 && sc->d_counters) {
     st->roots_colored = (int64_t)sc->roots_colored;
     st->roots_branched = (int64_t)sc->roots_branched;
     st->nodes = (int64_t)sc->nodes;
@@ -469,6 +545,9 @@ static uint64_t options_key(const mc_options &o) {
   mix((uint64_t)(uintptr_t)o.mlp);
   mix((uint64_t)o.part_rank);
   mix((uint64_t)o.part_count);
+  mix((uint64_t)o.layout);
+  mix((uint64_t)o.no_bitmap);
+  mix((uint64_t)o.repeel);
   return k;
 }
 
@@ -722,6 +801,27 @@ int mc_autotune(mc_graph *g, const mc_options *base, int32_t repeats, mc_options
   }
   bo.no_split = bs.no_split;
   bo.split_nodes = bs.nodes;
+  // the block workers' bitset layout, then the build's member lookup
+  for (int32_t lay : {1 - bo.layout}) {
+    mc_options o = bo;
+    o.layout = lay;
+    double ms;
+    MC_TRY(trial(o, &ms));
+    if (ms < best) {
+      best = ms;
+      bo.layout = lay;
+    }
+  }
+  {
+    mc_options o = bo;
+    o.no_bitmap = 1 - bo.no_bitmap;
+    double ms;
+    MC_TRY(trial(o, &ms));
+    if (ms < best) {
+      best = ms;
+      bo.no_bitmap = o.no_bitmap;
+    }
+  }
   if (bo.heuristic == 0) {
     // the warm-up part of Algorithm 1 alone, where it reaches a bound that
     // prunes as well for less work
@@ -755,6 +855,84 @@ int mc_peel_order(mc_graph *g, int32_t *order_out) {
   if (g->n > 0)
     MC_CUDA_TRY(cudaMemcpyAsync(order_out, g->order, g->n * sizeof(int32_t), cudaMemcpyDefault, g->stream));
   MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return MC_OK;
+}
+
+int mc_clique_order(mc_graph *g, const int32_t *rank, int32_t *order_out, int64_t *group_starts_out,
+                    int32_t *group_round_out, int64_t *groups_out, mc_order_stats *stats) {
+  if (!g || g->count != 1 || !groups_out || (g->n > 0 && (!order_out || !group_starts_out))) return MC_ERR_ARG;
+  *groups_out = 0;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  const int64_t n = g->n;
+  void *p;
+  MC_TRY(ws_get(g, "co.out", (size_t)(n + 1) * 16 + 64, &p));
+  int64_t *d_gstart = (int64_t *)p;
+  int32_t *d_order = (int32_t *)(d_gstart + n + 1);
+  int32_t *d_ground = d_order + n;
+  MC_TRY(record_event(g, 0));
+  int64_t groups = 0, work[2] = {0, 0};
+  int32_t rounds = 0;
+  if (n == 0) {
+    if (group_starts_out) MC_CUDA_TRY(cudaMemcpy(group_starts_out, &groups, sizeof(int64_t), cudaMemcpyDefault));
+    return MC_OK;
+  }
+  MC_TRY(clique_order(g, rank, d_order, d_gstart, d_ground, &groups, &rounds, work));
+  MC_TRY(record_event(g, 1));
+  MC_CUDA_TRY(cudaMemcpyAsync(order_out, d_order, n * 4, cudaMemcpyDefault, g->stream));
+  MC_CUDA_TRY(cudaMemcpyAsync(group_starts_out, d_gstart, (groups + 1) * 8, cudaMemcpyDefault, g->stream));
+  if (group_round_out)
+    MC_CUDA_TRY(cudaMemcpyAsync(group_round_out, d_ground, groups * 4, cudaMemcpyDefault, g->stream));
+  MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  MC_TRY(check_device_error(g));
+  *groups_out = groups;
+  if (stats) {
+    stats->rounds = rounds;
+    stats->grows = work[0];
+    stats->tests = work[1];
+    stats->ms = elapsed(g->ev[0], g->ev[1]);
+  }
+  return MC_OK;
+}
+
+int mc_relabel(mc_graph *g, const int32_t *order, int64_t *row_ptr_out, int32_t *col_idx_out) {
+  if (!g || g->count != 1 || !row_ptr_out || (g->n > 0 && !order) || (g->nnz > 0 && !col_idx_out))
+    return MC_ERR_ARG;
+  const int64_t n = g->n;
+  void *p;
+  MC_TRY(ws_get(g, "rl.nrp", (size_t)(n + 1) * 8, &p));
+  int64_t *d_nrp = (int64_t *)p;
+  MC_TRY(ws_get(g, "rl.nci", (size_t)std::max<int64_t>(g->nnz, 1) * 4, &p));
+  int32_t *d_nci = (int32_t *)p;
+  MC_TRY(relabel(g, order, d_nrp, d_nci));
+  MC_CUDA_TRY(cudaMemcpyAsync(row_ptr_out, d_nrp, (n + 1) * 8, cudaMemcpyDefault, g->stream));
+  if (g->nnz > 0) MC_CUDA_TRY(cudaMemcpyAsync(col_idx_out, d_nci, g->nnz * 4, cudaMemcpyDefault, g->stream));
+  MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return check_device_error(g);
+}
+
+int mc_gap_bits(mc_graph *g, const int32_t *order, double *bits_out) {
+  if (!g || g->count != 1 || !bits_out) return MC_ERR_ARG;
+  *bits_out = 0.0;
+  if (g->nnz == 0) return MC_OK;
+  void *p;
+  const int64_t *rp = g->row_ptr;
+  const int32_t *ci = g->col_idx;
+  if (order) {
+    MC_TRY(ws_get(g, "rl.nrp", (size_t)(g->n + 1) * 8, &p));
+    int64_t *d_nrp = (int64_t *)p;
+    MC_TRY(ws_get(g, "rl.nci", (size_t)g->nnz * 4, &p));
+    int32_t *d_nci = (int32_t *)p;
+    MC_TRY(relabel(g, order, d_nrp, d_nci));
+    rp = d_nrp;
+    ci = d_nci;
+  }
+  MC_TRY(ws_get(g, "rl.sum", 8, &p));
+  double *d_sum = (double *)p;
+  MC_TRY(gap_bits(g, rp, ci, d_sum));
+  MC_CUDA_TRY(cudaMemcpyAsync(g->h_small, d_sum, 8, cudaMemcpyDeviceToHost, g->stream));
+  MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  MC_TRY(check_device_error(g));
+  *bits_out = *(double *)g->h_small / (double)g->nnz;
   return MC_OK;
 }
 

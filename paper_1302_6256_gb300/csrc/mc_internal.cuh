@@ -108,8 +108,14 @@ struct Pruned {
 // No host synchronisation: sizes stay in pg.d_counts (see read_pruned_counts).
 // part_rank / part_count: keep only the roots whose position in the peel
 // order is part_rank modulo part_count (1: every root).
+// pos_lo / pos_hi: keep only the roots at peel positions [pos_lo, pos_hi).
 int launch_prune(mc_graph *g, int ordering, const float *scores, int32_t warp_max, Pruned *out,
-                 long long spin_limit, int32_t part_rank = 0, int32_t part_count = 1);
+                 long long spin_limit, int32_t part_rank = 0, int32_t part_count = 1, int64_t pos_lo = 0,
+                 int64_t pos_hi = INT64_MAX);
+// New root lists over an existing pruned graph (ordering 0), for the roots at
+// peel positions [pos_lo, pos_hi).
+int relaunch_roots(mc_graph *g, int32_t warp_max, Pruned *pg, int32_t part_rank, int32_t part_count, int64_t pos_lo,
+                   int64_t pos_hi);
 int read_pruned_counts(mc_graph *g, Pruned *out);
 
 // Search (InitialBranch + Branch) over all roots.
@@ -120,8 +126,10 @@ struct SearchCounters {
 int read_search_counters(mc_graph *g, SearchCounters *cnt);
 // Record event i of the graph on its stream (external when capturing).
 int record_event(mc_graph *g, int i);
+// layout 1: every block-class root in the 1,024-candidate layout; no_bitmap:
+// member lookups by hash table only.
 int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_split, int split_nodes,
-                  long long spin_limit, SearchCounters *counters);
+                  long long spin_limit, SearchCounters *counters, int layout = 0, int no_bitmap = 0);
 
 }  // namespace mc
 
@@ -146,6 +154,10 @@ struct mc_graph {
   unsigned long long *d_heur_ctr = nullptr;  // heuristic work counters of the last solve (device)
   bool heur_ran = false;                     // the last solve ran the heuristic
   bool learned_ran = false;                  // the last solve was the learned form
+  bool repeel_ran = false;                   // the last solve searched its roots in ranges
+  mc::SearchCounters repeel_acc{};           // ... and these are its counters summed over the ranges
+  int32_t repeel_rebuilds = 0;               // ... and the pruned graph was rebuilt this often
+  int64_t repeel_roots = 0;                  // ... over this many roots in all
   int32_t warp_max_used = 128;  // warp/block split of the current solve
   bool capturing = false;       // inside CUDA graph capture: no host synchronisation
   int32_t *core = nullptr, *order = nullptr, *pos = nullptr;  // n each (device)
@@ -176,6 +188,15 @@ int launch_verify_set(mc_graph *g, const int32_t *d_vs, int32_t k, int32_t *d_ok
 // it is a degeneracy order of the graph (MC_ERR_ARG otherwise).
 int use_order(mc_graph *g, const int32_t *order);
 int launch_validate(mc_graph *g, int32_t *d_bad);
+// Clique-peeling order (order.cu) into device arrays (order n, gstart n+1,
+// ground n); work_out (nullable): [0] grows, [1] candidate tests.
+int clique_order(mc_graph *g, const int32_t *rank, int32_t *d_order, int64_t *d_gstart, int32_t *d_ground,
+                 int64_t *groups_out, int32_t *rounds_out, int64_t *work_out);
+// Relabelled CSR (rows sorted) by an order (host or device), into device
+// arrays; MC_ERR_ARG if the order is not a permutation.
+int relabel(mc_graph *g, const int32_t *order, int64_t *d_nrp, int32_t *d_nci);
+// *d_total = sum over the entries of a sorted CSR of log2(1 + gap).
+int gap_bits(mc_graph *g, const int64_t *d_nrp, const int32_t *d_nci, double *d_total);
 int launch_gid(mc_graph *g);
 // Indices of the k largest scores (descending), over all vertices.
 int top_scores(mc_graph *g, const float *scores, int64_t k, int32_t *out);

@@ -146,11 +146,14 @@ __global__ void fill_kernel(const int64_t *__restrict__ d_np, const int64_t *__r
 struct RootInfo {
   const int32_t *odeg, *ogid, *best;
   int32_t warp_max;
-  const int32_t *oold, *pos;  // root partition: position of a pruned vertex in the peel order
-  int32_t part_rank, part_count;
+  const int32_t *oold, *pos;  // position of a pruned vertex in the peel order
+  int32_t part_rank, part_count;  // root partition over ranks
+  int64_t pos_lo, pos_hi;         // roots at peel positions [pos_lo, pos_hi) only
   __device__ int cls(int64_t j) const {
     if (j < 0) return -1;
-    if (part_count > 1 && pos[oold[j]] % part_count != part_rank) return -1;  // another part's root
+    const int64_t pp = pos[oold[j]];
+    if (pp < pos_lo || pp >= pos_hi) return -1;                    // outside this range of roots
+    if (part_count > 1 && pp % part_count != part_rank) return -1;  // another part's root
     int g = ogid ? ogid[j] : 0;
     int d = odeg[j];
     if (d < best[g] || d == 0) return -1;  // |P| >= omega~ is needed for a larger clique
@@ -220,7 +223,7 @@ __global__ void gather_scores_kernel(int64_t n, const int64_t *__restrict__ d_np
 }  // namespace
 
 int launch_prune(mc_graph *g, int ordering, const float *scores, int32_t warp_max, Pruned *out,
-                 long long spin_limit, int32_t part_rank, int32_t part_count) {
+                 long long spin_limit, int32_t part_rank, int32_t part_count, int64_t pos_lo, int64_t pos_hi) {
   (void)spin_limit;
   // Everything stays on the device: the pruned size, arc count and root
   // counts are written to out->d_counts and read by the later kernels, and
@@ -278,7 +281,7 @@ int launch_prune(mc_graph *g, int ordering, const float *scores, int32_t warp_ma
   // roots in processing order, split by class
   MC_TRY(ws_get(g, "pr.roots", (3 * n + 3) * sizeof(int32_t), &p));
   int32_t *roots = (int32_t *)p;
-  RootInfo ri{odeg, ogid, g->best, warp_max, oold, g->pos, part_rank, part_count};
+  RootInfo ri{odeg, ogid, g->best, warp_max, oold, g->pos, part_rank, part_count, pos_lo, pos_hi};
   int32_t *tab = nullptr;
   if (ordering == 1 || ordering == 2) {
     MC_TRY(ws_get(g, "pr.tab", (n + 1) * sizeof(int32_t), &p));
@@ -319,6 +322,22 @@ int launch_prune(mc_graph *g, int ordering, const float *scores, int32_t warp_ma
   out->roots_block = roots + n;
   out->roots_big = roots + 2 * n;
   out->odeg = odeg;
+  return MC_OK;
+}
+
+// New root lists (degeneracy order, by class) over the pruned graph that
+// `pg` already holds, for the roots at peel positions [pos_lo, pos_hi).
+int relaunch_roots(mc_graph *g, int32_t warp_max, Pruned *pg, int32_t part_rank, int32_t part_count, int64_t pos_lo,
+                   int64_t pos_hi) {
+  const int64_t n = g->n;
+  if (n == 0) return MC_OK;
+  int64_t *dsm = pg->d_counts;
+  RootInfo ri{pg->odeg, pg->ogid, g->best, warp_max, pg->oold, g->pos, part_rank, part_count, pos_lo, pos_hi};
+  for (int c = 0; c < 3; c++) {
+    int32_t *dst = pg->roots + (int64_t)c * n;
+    MC_TRY(device_scan(g, n, ClassF<PermDesc>{ri, PermDesc{dsm + 0}, c}, ClassG<PermDesc>{PermDesc{dsm + 0}, dst},
+                       dsm + 3 + c, "pr.scan"));
+  }
   return MC_OK;
 }
 

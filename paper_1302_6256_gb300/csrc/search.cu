@@ -60,6 +60,7 @@ struct SA {
   const int32_t *roots;
   const int64_t *nroots;    // device: number of roots in this class
   const int64_t *np_count;  // device: vertices of the pruned graph
+  int32_t use_bitmap;       // look members up in a bitmap of the later ranks when they fit
   int32_t *best, *lock, *wit;
   const int64_t *voff;
   int32_t *err;
@@ -1124,7 +1125,7 @@ __global__ void __launch_bounds__(kBT, (SM && PC <= kMidCap) ? 2 : 1) search_blo
     // the later ranks (u, n') fit the bitmap: member lookups by bitmap,
     // otherwise by hash table
     const int base = u + 1;
-    const bool use_bm = ((npr - base + 31) >> 5) <= kBitmapWords;
+    const bool use_bm = a.use_bitmap && ((npr - base + 31) >> 5) <= kBitmapWords;
     if (!use_bm)
       for (int i = tid; i < L::HCAP; i += kBT) hk[i] = -1;
     for (int i = tid; i < L::PCAP; i += kBT) Pidx[i] = INT_MIN;
@@ -1444,7 +1445,7 @@ __global__ void __launch_bounds__(kBT, (PC <= kMidCap) ? 2 : 1) branch_task_kern
 }  // namespace
 
 int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_split, int split_nodes,
-                  long long spin_limit, SearchCounters *cnt) {
+                  long long spin_limit, SearchCounters *cnt, int layout, int no_bitmap) {
   // Persistent kernels with fixed grids; the root counts are read on the
   // device (pg.d_counts), and sizes are bounded by K(G) >= |N+(u)|, so the
   // launches need no host synchronisation.
@@ -1459,6 +1460,7 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_spli
   MC_CUDA_TRY(cudaMemsetAsync(ctr, 0, 16 * sizeof(unsigned long long), g->stream));
   SA a{};
   a.np_count = pg.d_counts;
+  a.use_bitmap = no_bitmap ? 0 : 1;
   a.orow = pg.orow;
   a.ocol = pg.ocol;
   a.ocore = pg.ocore;
@@ -1551,28 +1553,38 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_spli
     a.roots = pg.roots_block;
     a.nroots = pg.d_counts + 4;
     a.next = next + 0;
-    if (kbound > kMidCap) {
-      MC_TRY(ws_get(g, "se.ovf", (size_t)std::max<int64_t>(g->n, 1) * 4, &p));
-      a.overflow = (int32_t *)p;
-      a.noverflow = (int64_t *)(ctr + 14);
-    }
-    MC_TRY(ws_get(g, "se.stk_m", (size_t)blocks_m * kBW * stride_m * 4, &p));
-    a.stack = (uint32_t *)p;
-    a.stack_stride = stride_m;
-    search_block_kernel<1, true, kMidCap><<<blocks_m, kBT, smem_m, g->stream>>>(a);
-    g_launches++;
-    MC_CUDA_TRY(cudaGetLastError());
-    if (kbound > kMidCap) {
-      a.roots = a.overflow;
-      a.nroots = a.noverflow;
-      a.next = next + 3;
-      a.overflow = nullptr;
-      a.noverflow = nullptr;
+    const bool wide_only = layout == 1 && kbound > kMidCap;
+    if (wide_only) {
+      // every block-class root in the 1,024-candidate layout
       a.stack = stk_b;
       a.stack_stride = stride_b;
       search_block_kernel<1, true, 1024><<<blocks_b, kBT, smem_b, g->stream>>>(a);
       g_launches++;
       MC_CUDA_TRY(cudaGetLastError());
+    } else {
+      if (kbound > kMidCap) {
+        MC_TRY(ws_get(g, "se.ovf", (size_t)std::max<int64_t>(g->n, 1) * 4, &p));
+        a.overflow = (int32_t *)p;
+        a.noverflow = (int64_t *)(ctr + 14);
+      }
+      MC_TRY(ws_get(g, "se.stk_m", (size_t)blocks_m * kBW * stride_m * 4, &p));
+      a.stack = (uint32_t *)p;
+      a.stack_stride = stride_m;
+      search_block_kernel<1, true, kMidCap><<<blocks_m, kBT, smem_m, g->stream>>>(a);
+      g_launches++;
+      MC_CUDA_TRY(cudaGetLastError());
+      if (kbound > kMidCap) {
+        a.roots = a.overflow;
+        a.nroots = a.noverflow;
+        a.next = next + 3;
+        a.overflow = nullptr;
+        a.noverflow = nullptr;
+        a.stack = stk_b;
+        a.stack_stride = stride_b;
+        search_block_kernel<1, true, 1024><<<blocks_b, kBT, smem_b, g->stream>>>(a);
+        g_launches++;
+        MC_CUDA_TRY(cudaGetLastError());
+      }
     }
   }
   MC_TRY(record_event(g, 9));

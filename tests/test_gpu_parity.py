@@ -117,7 +117,8 @@ def test_heuristic_racy_is_valid(mc, g):
 
 @pytest.mark.parametrize("opts", [dict(ordering=2), dict(no_neigh_cores=True), dict(heuristic=1),
                                   dict(heuristic=2), dict(heuristic=3), dict(warp_max=16), dict(warp_max=1),
-                                  dict(no_split=True), dict(heuristic=2, warp_max=16)],
+                                  dict(no_split=True), dict(heuristic=2, warp_max=16), dict(layout=1),
+                                  dict(no_bitmap=True), dict(layout=1, no_bitmap=True, heuristic=2)],
                          ids=lambda o: ",".join("%s=%s" % kv for kv in o.items()))
 def test_options_keep_omega(mc, opts):
     for g in medium_graphs()[:6]:
@@ -392,6 +393,7 @@ def test_autotune_returns_a_working_setting(mc):
     h = load(mc, g)
     opts, ms = mc.mc_autotune(h, repeats=1)
     assert opts["warp_max"] in (32, 64, 128) and ms > 0
+    assert opts["layout"] in (0, 1) and opts["no_bitmap"] in (False, True)
     om, wit, _ = mc.mc_max_clique(h, **opts)
     assert om == ref_omega(g) and oracle.is_clique(g, wit)
 
@@ -440,4 +442,37 @@ def test_order_option_refuses_what_is_not_a_degeneracy_order(mc):
     om, wit, _ = mc.mc_max_clique(h, order=np.r_[np.arange(1, 30), 0].astype(np.int32))
     assert om == 2 and oracle.is_clique(g, wit)
     assert mc.mc_max_clique(h)[0] == 2
+    h.close()
+
+
+@pytest.mark.parametrize("opts", [dict(repeel=4), dict(repeel=3, heuristic=2), dict(repeel=7, heuristic=2, warp_max=16),
+                                  dict(repeel=2, heuristic=3, no_split=True)],
+                         ids=lambda o: ",".join("%s=%s" % kv for kv in o.items()))
+def test_repeel_keeps_omega(mc, opts):
+    """Work-triggered re-pruning: the roots searched in ranges of peel
+    positions, the pruned graph rebuilt whenever omega rose in between; omega
+    equals the oracle's on graphs where the heuristic falls short."""
+    graphs = medium_graphs()[:7] + [gg.relabel(tight_instance(5)[0], 9)]
+    for g in graphs:
+        h = load(mc, g)
+        om, wit, st = mc.mc_max_clique(h, **opts)
+        assert om == ref_omega(g), (g.name, opts)
+        assert len(wit) == om and oracle.is_clique(g, wit) and st["verified"] == 1
+        h.close()
+
+
+def test_repeel_rebuilds_when_omega_rises(mc):
+    """With no heuristic the first range (the densest roots) finds omega, so
+    the pruned graph is rebuilt with it before the next range; the later
+    ranges then examine fewer roots than one pass without the heuristic."""
+    g = gg.rmat(14, 16, planted=30, seed=16)
+    h = load(mc, g)
+    om1, _, st1 = mc.mc_max_clique(h, heuristic=2)
+    om, wit, st = mc.mc_max_clique(h, heuristic=2, repeel=4)
+    assert om == om1 == ref_omega(g) and oracle.is_clique(g, wit)
+    assert st["rebuilds"] >= 1 and st["roots"] < st1["roots"]
+    for bad in (dict(repeel=3, graph=True), dict(repeel=3, ordering=2), dict(repeel=-1)):
+        with pytest.raises(mc.MCError) as e:
+            mc.mc_max_clique(h, **bad)
+        assert e.value.code == mc.MC_ERR_ARG
     h.close()
