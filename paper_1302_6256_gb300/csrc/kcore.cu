@@ -4,18 +4,26 @@
 //
 // One cooperative persistent launch processes all levels:
 //   scan    every live vertex with remaining degree == k joins the level-k
-//           frontier (warp-aggregated appends); vertices of larger degree are
-//           compacted into the next live list, so later scans only touch what
-//           is left; if nothing joins, k jumps to the smallest remaining degree;
-//   process each frontier vertex becomes one work item per 128-edge chunk of
-//           its row; the items appended before a grid barrier are split
+//           frontier; vertices of larger degree are compacted into the next
+//           live list, so later scans only touch what is left; if nothing
+//           joins, k jumps to the smallest remaining degree.  Each warp peels
+//           the frontier it found right after its scan: rows of at most
+//           kLocalRow edges from a warp stack in shared memory (short rows one
+//           lane each, longer ones by the whole warp), everything else as work
+//           items, one per 128-edge chunk;
+//   process after a grid barrier, the work items appended so far are split
 //           statically over all warps (rows under 32 edges one lane per
-//           item, longer chunks one warp per item, coalesced), and every neighbour whose
-//           degree is still above k is decremented; a neighbour whose degree
-//           falls to k joins the frontier and its items form the next
-//           sub-round of the same level, until a sub-round appends nothing.
-// The append order is a degeneracy order: every vertex has at most K(v)
-// neighbours appended after it.  It becomes the search's vertex ranking.
+//           item, longer chunks one warp per item, coalesced); every
+//           neighbour whose degree is still above k is decremented, and one
+//           whose degree falls to k joins the frontier: onto the warp's stack
+//           (peeled by that warp in the same phase, up to kDrainEdges edges)
+//           or as items of the next sub-round, until a sub-round appends
+//           nothing.
+// A vertex joins by claiming its core number (compare-and-swap from -1), so
+// one that a scan reads at degree k just after a decrement made it k joins
+// once.  The append order is a degeneracy order: when a vertex joins, every
+// neighbour that joins later is still counted in its remaining degree, which
+// is at most k.  It becomes the search's vertex ranking.
 #include "mc_internal.cuh"
 
 #include <algorithm>
@@ -30,6 +38,9 @@ constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
 constexpr int kChunk = 128;  // edges per work item
 constexpr int kPer = 4;      // edges per lane in flight
+constexpr int kLocal = 256;     // warp stack entries: rows a warp peels in the same phase
+constexpr int kLocalRow = 128;  // rows of at most this many edges may go onto the stack
+constexpr int kDrainEdges = 4096;  // edges a warp takes from its stack per phase (then it spills)
 
 struct KcoreCtl {
   unsigned bar_count, bar_gen;
@@ -80,30 +91,48 @@ __device__ __forceinline__ void barrier_snap(KcoreCtl *ctl, unsigned nblocks, in
 }
 
 __global__ void degree_init_kernel(int64_t n, const int64_t *__restrict__ rp, int32_t *__restrict__ deg,
-                                   int32_t *__restrict__ maxdeg) {
+                                   int32_t *__restrict__ core, int32_t *__restrict__ maxdeg) {
   int local = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     int d = (int)(rp[v + 1] - rp[v]);
     deg[v] = d;
+    core[v] = -1;  // not yet in the peel order
     local = max(local, d);
   }
   local = dev::warp_max(local);
   if ((threadIdx.x & 31) == 0) atomicMax(maxdeg, local);
 }
 
-// Append the lanes' new frontier vertices (flag nf, vertex u): core, peel
-// order and one work item per chunk of the row.  All lanes call.
+// Append the lanes' new frontier vertices (flag nf, vertex u): core and
+// peel order; then their rows' work.  With a warp stack (stk, *sn: entries
+// used, the same in every lane), vertices of 1..kLocalRow edges go onto it
+// while there is room, to be processed by this warp in the same sub-round;
+// the others become one work item per chunk of their row, processed in the
+// next sub-round.  All lanes call.
 __device__ __forceinline__ void append_frontier(bool nf, int u, int k, const int64_t *__restrict__ rp, int32_t *core,
-                                                int32_t *order, long long *wq, KcoreCtl *ctl) {
+                                                int32_t *order, long long *wq, KcoreCtl *ctl, int *stk = nullptr,
+                                                int *sn = nullptr) {
   const int lane = threadIdx.x & 31;
+  if (!__any_sync(0xffffffffu, nf)) return;
+  // claim: a vertex found by a scan and by a decrement in the same phase
+  // joins once
+  if (nf) nf = atomicCAS(core + u, -1, k) == -1;
   const unsigned m = __ballot_sync(0xffffffffu, nf);
   if (!m) return;
   const unsigned lt = (1u << lane) - 1u;
-  int nch = 0;
-  if (nf) {
-    int64_t d = rp[u + 1] - rp[u];
-    nch = (int)((d + kChunk - 1) / kChunk);
+  int64_t d = 0;
+  if (nf) d = rp[u + 1] - rp[u];
+  bool put = false;
+  if (stk) {
+    const bool loc = nf && d > 0 && d <= kLocalRow;
+    const unsigned lm = __ballot_sync(0xffffffffu, loc);
+    const int room = kLocal - *sn;
+    const int at = __popc(lm & lt);
+    put = loc && at < room;
+    if (put) stk[*sn + at] = u;
+    *sn += min(__popc(lm), room);
   }
+  const int nch = (nf && !put) ? (int)((d + kChunk - 1) / kChunk) : 0;
   int incl = nch;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -120,11 +149,111 @@ __device__ __forceinline__ void append_frontier(bool nf, int u, int k, const int
   ob = __shfl_sync(0xffffffffu, ob, 0);
   wb = __shfl_sync(0xffffffffu, wb, 0);
   if (nf) {
-    core[u] = k;
     order[ob + __popc(m & lt)] = u;
     long long at = wb + incl - nch;
     for (int c = 0; c < nch; c++) wq[at + c] = ((long long)u << 32) | (unsigned)c;
   }
+  __syncwarp();
+}
+
+// Work items (one per chunk) for lanes' vertices already in the peel order:
+// what is left on a warp stack at the end of its local budget.
+__device__ __forceinline__ void push_items(bool has, int u, const int64_t *__restrict__ rp, long long *wq,
+                                           KcoreCtl *ctl) {
+  const int lane = threadIdx.x & 31;
+  const int nch = has ? (int)((rp[u + 1] - rp[u] + kChunk - 1) / kChunk) : 0;
+  int incl = nch;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int tot = __shfl_sync(0xffffffffu, incl, 31);
+  if (!tot) return;
+  long long wb = 0;
+  if (lane == 0) wb = (long long)atomicAdd((unsigned long long *)&ctl->wtail, (unsigned long long)tot);
+  wb = __shfl_sync(0xffffffffu, wb, 0);
+  long long at = wb + incl - nch;
+  for (int c = 0; c < nch; c++) wq[at + c] = ((long long)u << 32) | (unsigned)c;
+}
+
+// Walk one row (b0, len) with the whole warp (coalesced), kPer edges per
+// lane in flight before the frontier appends.
+__device__ __forceinline__ void walk_row(int64_t b0, int len, int k, const int64_t *__restrict__ rp,
+                                         const int32_t *__restrict__ ci, int32_t *deg, int32_t *core, int32_t *order,
+                                         long long *wq, KcoreCtl *ctl, int *stk, int *sn) {
+  const int lane = threadIdx.x & 31;
+  for (int eb = 0; eb < len; eb += 32 * kPer) {
+    int u[kPer];
+    bool nf[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; q++) {
+      const int e = eb + q * 32 + lane;
+      u[q] = e < len ? ci[b0 + e] : -1;
+    }
+#pragma unroll
+    for (int q = 0; q < kPer; q++) {
+      nf[q] = false;
+      if (u[q] >= 0 && __ldcg(deg + u[q]) > k) nf[q] = (atomicSub(deg + u[q], 1) == k + 1);
+    }
+#pragma unroll
+    for (int q = 0; q < kPer; q++) append_frontier(nf[q], u[q], k, rp, core, order, wq, ctl, stk, sn);
+  }
+}
+
+// Walk rows of at most 32 edges, one lane per row (b0, len; len 0 for idle
+// lanes), decrementing every neighbour whose degree is still above k; new
+// frontier vertices are appended (to the stack when one is given).
+__device__ __forceinline__ void walk_short_rows(int64_t b0, int len, int k, const int64_t *__restrict__ rp,
+                                                const int32_t *__restrict__ ci, int32_t *deg, int32_t *core,
+                                                int32_t *order, long long *wq, KcoreCtl *ctl, int *stk, int *sn) {
+  const int maxlen = dev::warp_max(len);
+  for (int j0 = 0; j0 < maxlen; j0 += kPer) {
+    int u[kPer];
+    bool nf[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; q++) u[q] = (j0 + q < len) ? ci[b0 + j0 + q] : -1;
+#pragma unroll
+    for (int q = 0; q < kPer; q++) {
+      nf[q] = false;
+      if (u[q] >= 0 && __ldcg(deg + u[q]) > k) nf[q] = (atomicSub(deg + u[q], 1) == k + 1);
+    }
+#pragma unroll
+    for (int q = 0; q < kPer; q++) append_frontier(nf[q], u[q], k, rp, core, order, wq, ctl, stk, sn);
+  }
+}
+
+// The warp's own cascade: rows it put on its stack, up to 32 at a time
+// (short rows one lane each, longer ones by the whole warp; their new
+// frontier vertices go back on the stack) until kDrainEdges edges are
+// walked; what is left becomes work items of the next sub-round.
+__device__ __forceinline__ void drain_stack(int k, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                            int32_t *deg, int32_t *core, int32_t *order, long long *wq, KcoreCtl *ctl,
+                                            int *stk, int *sn) {
+  const int lane = threadIdx.x & 31;
+  for (int budget = kDrainEdges; *sn > 0 && budget > 0;) {
+    const int take = min(*sn, 32);
+    *sn -= take;
+    const int u = lane < take ? stk[*sn + lane] : -1;
+    __syncwarp();
+    const int64_t b0 = u >= 0 ? rp[u] : 0;
+    const int len = u >= 0 ? (int)(rp[u + 1] - b0) : 0;
+    budget -= dev::warp_sum(len);
+    walk_short_rows(b0, len <= 32 ? len : 0, k, rp, ci, deg, core, order, wq, ctl, stk, sn);
+    unsigned lm = __ballot_sync(0xffffffffu, len > 32);
+    while (lm) {
+      const int src = __ffs(lm) - 1;
+      lm &= lm - 1;
+      walk_row(__shfl_sync(0xffffffffu, b0, src), __shfl_sync(0xffffffffu, len, src), k, rp, ci, deg, core, order, wq,
+               ctl, stk, sn);
+    }
+  }
+  for (int i0 = 0; i0 < *sn; i0 += 32) {
+    const bool has = i0 + lane < *sn;
+    push_items(has, has ? stk[i0 + lane] : 0, rp, wq, ctl);
+  }
+  *sn = 0;
+  __syncwarp();
 }
 
 __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, const int64_t *__restrict__ rp,
@@ -133,6 +262,7 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
                                                                  int32_t *live1, long long *wq, KcoreCtl *ctl,
                                                                  int32_t *err, long long spin_limit) {
   __shared__ int bmin;
+  __shared__ int s_stk[kWarps][kLocal];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gwarp = (int64_t)blockIdx.x * kWarps + wib;
   const int64_t nwarps = (int64_t)gridDim.x * kWarps;
@@ -142,9 +272,10 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
 
   int k = 0;
   unsigned level = 0;
-  long long otail_now = 0, wtail_now = 0, wstart = 0;
+  long long otail_now = 0, otail_prev = 0, wtail_now = 0, wstart = 0;
   int64_t live_count = n;  // level 0 scans every vertex (identity list)
   int32_t *lin = live0, *lout = live1;
+  int *stk = s_stk[wib];
 
   for (;;) {
     // ---------------- scan: frontier of level k, compaction of the rest ----
@@ -154,7 +285,7 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
       ctl->live_n[(level + 1) & 1] = 0;
     }
     __syncthreads();
-    int lmin = INT_MAX;
+    int lmin = INT_MAX, sn0 = 0;
     int *lout_n = &ctl->live_n[level & 1];
     for (int64_t base = gwarp * 32; base < live_count; base += nwarps * 32) {
       int64_t i = base + lane;
@@ -172,8 +303,13 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
         ob = __shfl_sync(0xffffffffu, ob, 0);
         if (keep) lout[ob + __popc(km & lt)] = v;
       }
-      append_frontier(d == k, v, k, rp, core, order, wq, ctl);
+      append_frontier(d == k, v, k, rp, core, order, wq, ctl, stk, &sn0);
     }
+    // the frontier a warp found (up to its stack) is peeled at once by that
+    // warp, while others may still be scanning: a vertex they read at degree
+    // k after a decrement here is claimed once; one kept at k + 1 and then
+    // peeled here is dropped by the next scan, its degree being <= k
+    drain_stack(k, rp, ci, deg, core, order, wq, ctl, stk, &sn0);
     lmin = -dev::warp_max(-lmin);
     if (lane == 0 && lmin != INT_MAX) atomicMin(&bmin, lmin);
     __syncthreads();
@@ -185,8 +321,9 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
     { int32_t *t = lin; lin = lout; lout = t; }
 
     if (otail_now >= n) break;
-    if (wtail_now == wstart) {
-      // nothing at level k (no frontier, or only isolated vertices)
+    if (otail_now == otail_prev) {
+      // nothing at level k: no decrement happened, so the smallest kept
+      // degree is exact
       int mk = *(volatile int *)&ctl->minrem[level % 3];
       level++;
       if (mk == INT_MAX) break;  // unreachable while vertices remain
@@ -202,6 +339,7 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
     // the whole warp.
     long long s0 = wstart, e0 = wtail_now;
     while (s0 < e0) {
+      int sn = 0;
       // pass A: items of fewer than 32 edges, 32 per warp, one lane each
       for (long long gb = s0 + gwarp * 32; gb < e0; gb += nwarps * 32) {
         const long long t = gb + lane;
@@ -214,47 +352,18 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
           b0 = rp[v] + (int64_t)c * kChunk;
           len = (int)(min(rp[v + 1], b0 + kChunk) - b0);
         }
-        const bool small = valid && len < 32;
-        const int maxlen = dev::warp_max(small ? len : 0);
-        for (int j0 = 0; j0 < maxlen; j0 += kPer) {
-          int u[kPer];
-          bool nf[kPer];
-#pragma unroll
-          for (int q = 0; q < kPer; q++) u[q] = (small && j0 + q < len) ? ci[b0 + j0 + q] : -1;
-#pragma unroll
-          for (int q = 0; q < kPer; q++) {
-            nf[q] = false;
-            if (u[q] >= 0 && __ldcg(deg + u[q]) > k) nf[q] = (atomicSub(deg + u[q], 1) == k + 1);
-          }
-#pragma unroll
-          for (int q = 0; q < kPer; q++) append_frontier(nf[q], u[q], k, rp, core, order, wq, ctl);
-        }
+        walk_short_rows(b0, (valid && len < 32) ? len : 0, k, rp, ci, deg, core, order, wq, ctl, stk, &sn);
       }
-      // pass B: longer chunks, one warp each (coalesced row reads); each
-      // lane keeps kPer edges in flight before the frontier appends
+      // pass B: longer chunks, one warp each (coalesced row reads)
       for (long long t = s0 + gwarp; t < e0; t += nwarps) {
         const long long item = __ldcg(wq + t);
         const int v = (int)(item >> 32), c = (int)(item & 0xffffffff);
         const int64_t b0 = rp[v] + (int64_t)c * kChunk;
         const int len = (int)(min(rp[v + 1], b0 + kChunk) - b0);
         if (len < 32) continue;
-        for (int eb = 0; eb < len; eb += 32 * kPer) {
-          int u[kPer];
-          bool nf[kPer];
-#pragma unroll
-          for (int q = 0; q < kPer; q++) {
-            const int e = eb + q * 32 + lane;
-            u[q] = e < len ? ci[b0 + e] : -1;
-          }
-#pragma unroll
-          for (int q = 0; q < kPer; q++) {
-            nf[q] = false;
-            if (u[q] >= 0 && __ldcg(deg + u[q]) > k) nf[q] = (atomicSub(deg + u[q], 1) == k + 1);
-          }
-#pragma unroll
-          for (int q = 0; q < kPer; q++) append_frontier(nf[q], u[q], k, rp, core, order, wq, ctl);
-        }
+        walk_row(b0, len, k, rp, ci, deg, core, order, wq, ctl, stk, &sn);
       }
+      drain_stack(k, rp, ci, deg, core, order, wq, ctl, stk, &sn);
       long long e1 = 0;
       barrier_snap(ctl, nblocks, err, spin_limit, &otail_now, &e1, nullptr, nullptr);
       if (*(volatile int32_t *)err) return;
@@ -263,6 +372,7 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
       wtail_now = e1;
     }
     wstart = wtail_now;
+    otail_prev = otail_now;
     level++;
     if (otail_now >= n) break;
     k++;
@@ -448,7 +558,7 @@ int launch_core_numbers(mc_graph *g, long long spin_limit) {
   MC_CUDA_TRY(cudaMemsetAsync(wq, 0xff, wcap * sizeof(long long), g->stream));
 
   int ib = (int)std::min<int64_t>((n + 255) / 256, (int64_t)g->sm_count * 8);
-  degree_init_kernel<<<ib, 256, 0, g->stream>>>(n, g->row_ptr, deg, maxdeg);
+  degree_init_kernel<<<ib, 256, 0, g->stream>>>(n, g->row_ptr, deg, g->core, maxdeg);
   g_launches++;
   MC_CUDA_TRY(cudaGetLastError());
 
@@ -600,7 +710,7 @@ extern "C" int mc_core_numbers_noalloc(int64_t n, const int64_t *row_ptr, const 
   if (h_bad) return MC_ERR_INVALID_GRAPH;
 
   const int ib = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
-  degree_init_kernel<<<ib, 256, 0, s>>>(n, row_ptr, deg, maxdeg);
+  degree_init_kernel<<<ib, 256, 0, s>>>(n, row_ptr, deg, core_out, maxdeg);
   g_launches++;
   MC_CUDA_TRY(cudaGetLastError());
   int per_sm = 0;

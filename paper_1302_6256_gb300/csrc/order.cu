@@ -33,7 +33,8 @@
 // every new row (bitonic networks: a warp in registers up to 32 entries, a
 // warp in shared memory up to 1,024, a block in shared memory up to 16,384,
 // a block over a global scratch row beyond), and sums log2(1 + gap) over the
-// entries, the first gap of row p taken from p itself.
+// entries, the first gap of row p taken from p itself: 1 + gap rounded once
+// to single precision, log2f (within 1 ulp), summed in double.
 #include <algorithm>
 #include <climits>
 
@@ -49,6 +50,9 @@ constexpr int kOT = 256;         // threads per block of the warp-per-vertex ker
 constexpr int kWarpSortMax = 1024;
 constexpr int kBlockSortMax = 16384;
 constexpr int kBigT = 1024;      // threads of the block sorter
+constexpr int kBG = 512;         // threads of the block grower
+constexpr int kBGW = kBG / 32;
+constexpr int64_t kBlockGrowMin = 4096;  // neighbours above which a block grows the clique
 
 struct OA {
   int64_t n;
@@ -59,13 +63,16 @@ struct OA {
   int32_t *csize;  // stored clique size; 0: grow; negative: accepted this round
   int32_t *arena;
   unsigned long long *bestkey;
-  int64_t *ctl;  // [0] placed, [1] groups, [2] grows, [3] candidate tests, [4] rounds, [5] scan total
+  int64_t *ctl;  // [0] placed, [1] groups, [2] grows, [3] candidate tests, [4] rounds, [5] scan total,
+                 // [6] block grower's list length (unsigned)
   int64_t *goff;
   int32_t *order;
   int64_t *gstart;
   int32_t *ground;
   int32_t round;
   int32_t *err;
+  int32_t *big;     // vertices for the block grower this round
+  unsigned *nbig;
 };
 
 struct CKey {
@@ -100,31 +107,182 @@ __device__ __forceinline__ unsigned long long key_of(const OA &a, int v, int siz
   return ((unsigned long long)(unsigned)size << 32) | (unsigned)(0x7fffffff - r);
 }
 
-// grow: a warp per alive vertex whose stored clique is missing or stale
-__global__ void __launch_bounds__(kOT) grow_kernel(OA a) {
+// Windowed merge step of a greedy filter (all 32 lanes): lane candidate x
+// (INT_MAX past the end; `last` = the last valid lane) against w's row from
+// pos, which only moves forward; true iff x is in the row.
+__device__ __forceinline__ bool merge_hit(const OA &a, int x, int last, int64_t &pos, int64_t r1) {
+  const int xmin = __shfl_sync(FULL, x, 0), xmax = __shfl_sync(FULL, x, last);
+  int64_t p = pos;
+  while (p < r1) {
+    const int64_t e = min(p + 31, r1 - 1);
+    if (a.ci[e] >= xmin) break;
+    p = e + 1;
+  }
+  bool hit = false;
+  while (p < r1) {
+    const int y = (p + (threadIdx.x & 31) < r1) ? a.ci[p + (threadIdx.x & 31)] : INT_MAX;
+    int l = -1;  // largest window index with y <= x
+#pragma unroll
+    for (int st = 32; st >= 1; st >>= 1) {
+      const int t = l + st;
+      const int yt = __shfl_sync(FULL, y, t & 31);
+      if (t < 32 && yt <= x) l = t;
+    }
+    const int yl = __shfl_sync(FULL, y, l & 31);
+    if (l >= 0 && yl == x) hit = true;
+    const int ymax = __shfl_sync(FULL, y, 31);
+    if (ymax >= xmax) break;
+    p += 32;
+  }
+  pos = p;
+  return hit;
+}
+
+// Greedy growth of C(v) by one warp (all lanes): v's alive neighbours to the
+// front of its arena range (row order: ascending id), then pick the first
+// candidate by (core, degree, id) and keep the candidates adjacent to it
+// (binary search per candidate when the candidates are few against w's row,
+// else a merge), until none is left.  Member j (from 1) goes to rp[v+1] - j
+// after its filter: with cnt candidates left, cnt + j <= deg(v), so it lies
+// past them.  Returns |C(v)|.
+__device__ __forceinline__ int warp_grow(const OA &a, int v, unsigned long long &tests) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const CKey none{INT_MIN, INT_MIN, INT_MAX};
+  const int64_t e0 = a.rp[v], e1 = a.rp[v + 1];
+  int32_t *cand = a.arena + e0;
+  int cnt = 0;
+  CKey bk = none;
+  for (int64_t eb = e0; eb < e1; eb += 32) {
+    const int64_t e = eb + lane;
+    int u = -1;
+    bool ok = false;
+    if (e < e1) {
+      u = a.ci[e];
+      ok = a.alive[u] != 0;
+    }
+    const unsigned m = __ballot_sync(FULL, ok);
+    if (ok) {
+      cand[cnt + __popc(m & lt)] = u;
+      const CKey k = ckey(a, u);
+      if (ahead(k, bk)) bk = k;
+    }
+    cnt += __popc(m);
+  }
+  __syncwarp();
+  bk = warp_first(bk);
+  int j = 0;
+  while (cnt > 0) {
+    const int w = bk.id;
+    const int64_t r0 = a.rp[w], r1 = a.rp[w + 1];
+    const bool merge = (int64_t)cnt * 16 >= (r1 - r0);
+    tests += (unsigned long long)cnt;
+    int out = 0;
+    CKey nb = none;
+    int64_t pos = r0;
+    for (int base = 0; base < cnt; base += 32) {
+      const int i = base + lane;
+      const int x = (i < cnt) ? cand[i] : INT_MAX;
+      bool keep;
+      if (!merge) keep = i < cnt && x != w && in_row(a.rp, a.ci, w, x);
+      else keep = merge_hit(a, x, min(31, cnt - 1 - base), pos, r1) && i < cnt && x != w;
+      const unsigned m = __ballot_sync(FULL, keep);
+      __syncwarp();
+      if (keep) {
+        cand[out + __popc(m & lt)] = x;
+        const CKey k = ckey(a, x);
+        if (ahead(k, nb)) nb = k;
+      }
+      out += __popc(m);
+      __syncwarp();
+    }
+    cnt = out;
+    j++;
+    if (lane == 0) a.arena[e1 - j] = w;
+    __syncwarp();
+    bk = warp_first(nb);
+  }
+  return 1 + j;
+}
+
+// Lane test: v's stored clique is missing or holds a placed member.
+__device__ __forceinline__ bool needs_grow(const OA &a, int v) {
+  const int s = a.csize[v];
+  if (s <= 0) return true;
+  const int64_t e1 = a.rp[v + 1];
+  for (int i = 0; i < s - 1; i++)
+    if (!a.alive[a.arena[e1 - 1 - i]]) return true;
+  return false;
+}
+
+// grow: warps take 32 vertices at a time (coalesced flags), find the alive
+// ones that need a clique, and grow them one after the other; vertices of
+// more than kBlockGrowMin neighbours go to the block kernel's list instead
+__global__ void __launch_bounds__(kOT) grow_kernel(OA a) {
+  const int lane = threadIdx.x & 31;
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long grows = 0, tests = 0;
-  for (int64_t vv = gw; vv < a.n; vv += nw) {
-    const int v = (int)vv;
-    if (!a.alive[v]) continue;
-    const int64_t e0 = a.rp[v], e1 = a.rp[v + 1];
-    if (lane == 0) a.bestkey[v] = 0ull;
-    const int s = a.csize[v];
-    if (s > 0) {
-      bool dead = false;
-      for (int i = lane; i < s - 1; i += 32) dead |= !a.alive[a.arena[e1 - 1 - i]];
-      if (!__any_sync(FULL, dead)) continue;
+  for (int64_t base = gw * 32; base < a.n; base += nw * 32) {
+    const int64_t vv = base + lane;
+    bool need = false;
+    if (vv < a.n && a.alive[vv]) {
+      a.bestkey[vv] = 0ull;
+      need = needs_grow(a, (int)vv);
     }
-    // alive neighbours to the front of the range (row order: ascending id)
-    int32_t *cand = a.arena + e0;
+    unsigned m = __ballot_sync(FULL, need);
+    while (m) {
+      const int v = (int)base + __ffs(m) - 1;
+      m &= m - 1;
+      if (a.rp[v + 1] - a.rp[v] > kBlockGrowMin) {
+        if (lane == 0) a.big[atomicAdd(a.nbig, 1u)] = v;
+        continue;
+      }
+      const int size = warp_grow(a, v, tests);
+      if (lane == 0) {
+        a.csize[v] = size;
+        grows++;
+      }
+    }
+  }
+  if (lane == 0 && grows) atomicAdd((unsigned long long *)(a.ctl + 2), grows);
+  if (lane == 0 && tests) atomicAdd((unsigned long long *)(a.ctl + 3), tests);
+}
+
+// First candidate over the block (contains two __syncthreads).
+__device__ __forceinline__ CKey block_first(CKey x, CKey *sk) {
+  x = warp_first(x);
+  if ((threadIdx.x & 31) == 0) sk[threadIdx.x >> 5] = x;
+  __syncthreads();
+  CKey r = sk[0];
+#pragma unroll
+  for (int i = 1; i < kBGW; i++)
+    if (ahead(sk[i], r)) r = sk[i];
+  __syncthreads();
+  return r;
+}
+
+// The same greedy growth by a whole block, for vertices of many neighbours:
+// the candidates are split into one slice per warp, each warp merges its
+// slice against w's row from the slice's first candidate on and writes what
+// it keeps to a scratch row, and the kept runs are packed back in order.
+__global__ void __launch_bounds__(kBG) grow_big_kernel(OA a, int32_t *scratch, int64_t scratch_stride) {
+  __shared__ CKey sk[kBGW];
+  __shared__ int scnt[kBGW];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const CKey none{INT_MIN, INT_MIN, INT_MAX};
+  const unsigned nbig = *a.nbig;
+  int32_t *B = scratch + blockIdx.x * scratch_stride;
+  unsigned long long grows = 0, tests = 0;
+  for (unsigned b = blockIdx.x; b < nbig; b += gridDim.x) {
+    const int v = a.big[b];
+    const int64_t e0 = a.rp[v], e1 = a.rp[v + 1];
+    int32_t *A = a.arena + e0;
     int cnt = 0;
     CKey bk = none;
-    for (int64_t eb = e0; eb < e1; eb += 32) {
-      const int64_t e = eb + lane;
+    for (int64_t tb = e0; tb < e1; tb += kBG) {
+      const int64_t e = tb + threadIdx.x;
       int u = -1;
       bool ok = false;
       if (e < e1) {
@@ -132,82 +290,79 @@ __global__ void __launch_bounds__(kOT) grow_kernel(OA a) {
         ok = a.alive[u] != 0;
       }
       const unsigned m = __ballot_sync(FULL, ok);
+      if (lane == 0) scnt[wid] = __popc(m);
+      __syncthreads();
+      int before = 0, tot = 0;
+#pragma unroll
+      for (int i = 0; i < kBGW; i++) {
+        const int c = scnt[i];
+        before += i < wid ? c : 0;
+        tot += c;
+      }
       if (ok) {
-        cand[cnt + __popc(m & lt)] = u;
+        A[cnt + before + __popc(m & lt)] = u;
         const CKey k = ckey(a, u);
         if (ahead(k, bk)) bk = k;
       }
-      cnt += __popc(m);
+      cnt += tot;
+      __syncthreads();
     }
-    __syncwarp();
-    bk = warp_first(bk);
-    int j = 0;  // members besides v
+    bk = block_first(bk, sk);
+    int j = 0;
     while (cnt > 0) {
       const int w = bk.id;
       const int64_t r0 = a.rp[w], r1 = a.rp[w + 1];
-      const bool merge = (int64_t)cnt * 16 >= (r1 - r0);
-      tests += (unsigned long long)cnt;
+      if (threadIdx.x == 0) tests += (unsigned long long)cnt;
+      const int s0 = (int)((int64_t)cnt * wid / kBGW), s1 = (int)((int64_t)cnt * (wid + 1) / kBGW);
       int out = 0;
       CKey nb = none;
-      int64_t pos = r0;
-      for (int base = 0; base < cnt; base += 32) {
-        const int i = base + lane;
-        const int x = (i < cnt) ? cand[i] : INT_MAX;
-        bool keep = false;
-        if (!merge) {
-          keep = i < cnt && x != w && in_row(a.rp, a.ci, w, x);
-        } else {
-          // both lists ascending: walk w's row in windows of 32
-          const int last = min(31, cnt - 1 - base);
-          const int xmin = __shfl_sync(FULL, x, 0), xmax = __shfl_sync(FULL, x, last);
-          while (pos < r1) {
-            const int64_t e = min(pos + 31, r1 - 1);
-            if (a.ci[e] >= xmin) break;
-            pos = e + 1;
-          }
-          int64_t wp = pos;
-          while (wp < r1) {
-            const int y = (wp + lane < r1) ? a.ci[wp + lane] : INT_MAX;
-            int l = -1;  // largest window index with y <= x
-#pragma unroll
-            for (int st = 32; st >= 1; st >>= 1) {
-              const int t = l + st;
-              const int yt = __shfl_sync(FULL, y, t & 31);
-              if (t < 32 && yt <= x) l = t;
-            }
-            const int yl = __shfl_sync(FULL, y, l & 31);
-            if (l >= 0 && yl == x) keep = true;
-            const int ymax = __shfl_sync(FULL, y, 31);
-            if (ymax >= xmax) break;
-            wp += 32;
-          }
-          pos = wp;
-          keep = keep && i < cnt && x != w;
+      if (s0 < s1) {
+        // the row from its first entry >= A[s0]
+        const int x0 = A[s0];
+        int64_t lo = r0, hi = r1;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi) >> 1;
+          if (a.ci[mid] < x0) lo = mid + 1; else hi = mid;
         }
-        const unsigned m = __ballot_sync(FULL, keep);
-        __syncwarp();
-        if (keep) {
-          cand[out + __popc(m & lt)] = x;
-          const CKey k = ckey(a, x);
-          if (ahead(k, nb)) nb = k;
+        int64_t pos = lo;
+        for (int base = s0; base < s1; base += 32) {
+          const int i = base + lane;
+          const int x = i < s1 ? A[i] : INT_MAX;
+          const bool keep = merge_hit(a, x, min(31, s1 - 1 - base), pos, r1) && i < s1 && x != w;
+          const unsigned m = __ballot_sync(FULL, keep);
+          if (keep) {
+            B[s0 + out + __popc(m & lt)] = x;
+            const CKey k = ckey(a, x);
+            if (ahead(k, nb)) nb = k;
+          }
+          out += __popc(m);
         }
-        out += __popc(m);
-        __syncwarp();
       }
-      cnt = out;
+      if (lane == 0) scnt[wid] = out;
+      __syncthreads();
+      int before = 0, tot = 0;
+#pragma unroll
+      for (int i = 0; i < kBGW; i++) {
+        const int c = scnt[i];
+        before += i < wid ? c : 0;
+        tot += c;
+      }
+      for (int i = lane; i < out; i += 32) A[before + i] = B[s0 + i];
+      cnt = tot;
       j++;
-      // cnt + j <= deg(v): the member slot is past the surviving candidates
-      if (lane == 0) a.arena[e1 - j] = w;
-      __syncwarp();
-      bk = warp_first(nb);
+      bk = block_first(nb, sk);
+      // cnt + j <= deg(v): the member slot lies past the packed candidates
+      if (threadIdx.x == 0) a.arena[e1 - j] = w;
+      __syncthreads();
     }
-    if (lane == 0) {
+    if (threadIdx.x == 0) {
       a.csize[v] = 1 + j;
       grows++;
     }
+    __syncthreads();
   }
-  if (lane == 0 && grows) atomicAdd((unsigned long long *)(a.ctl + 2), grows);
-  if (lane == 0 && tests) atomicAdd((unsigned long long *)(a.ctl + 3), tests);
+  if (threadIdx.x == 0 && grows) atomicAdd((unsigned long long *)(a.ctl + 2), grows);
+  if (threadIdx.x == 0 && tests) atomicAdd((unsigned long long *)(a.ctl + 3), tests);
 }
 
 // scatter: every member takes the largest key of the cliques holding it
@@ -251,42 +406,49 @@ struct AccG {
   }
 };
 
-// place: a warp per accepted clique writes its members ranked by degree
+// place: warps take 32 vertices at a time and write each accepted clique's
+// members ranked by degree (whole warp per clique)
 __global__ void __launch_bounds__(kOT) place_kernel(OA a) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t placed = a.ctl[0], groups = a.ctl[1];
-  for (int64_t vv = gw; vv < a.n; vv += nw) {
-    const int v = (int)vv;
-    const int s = -a.csize[v];
-    if (s <= 0) continue;
-    const int64_t packed = a.goff[v];
-    const int64_t gi = groups + (packed >> 32), pos = placed + (packed & 0xffffffffLL);
-    const int64_t e1 = a.rp[v + 1];
-    // accepted cliques are disjoint sets of unplaced vertices, so they fit;
-    // anything else is a broken invariant: report it, write nothing
-    if (pos + s > a.n || gi >= a.n) {
-      if (lane == 0) atomicExch(a.err, kDevCheck);
-      continue;
-    }
-    for (int i = lane; i < s; i += 32) {
-      const int x = i == 0 ? v : a.arena[e1 - i];
-      const int64_t dx = a.rp[x + 1] - a.rp[x];
-      int r = 0;
-      for (int t = 0; t < s; t++) {
-        const int y = t == 0 ? v : a.arena[e1 - t];
-        const int64_t dy = a.rp[y + 1] - a.rp[y];
-        r += (dy > dx || (dy == dx && y < x)) ? 1 : 0;
+  for (int64_t base = gw * 32; base < a.n; base += nw * 32) {
+    const int64_t vv = base + lane;
+    const int sl = vv < a.n ? -a.csize[vv] : 0;
+    unsigned m = __ballot_sync(FULL, sl > 0);
+    while (m) {
+      const int src = __ffs(m) - 1;
+      m &= m - 1;
+      const int v = (int)base + src;
+      const int s = __shfl_sync(FULL, sl, src);
+      const int64_t packed = a.goff[v];
+      const int64_t gi = groups + (packed >> 32), pos = placed + (packed & 0xffffffffLL);
+      const int64_t e1 = a.rp[v + 1];
+      // accepted cliques are disjoint sets of unplaced vertices, so they fit;
+      // anything else is a broken invariant: report it, write nothing
+      if (pos + s > a.n || gi >= a.n) {
+        if (lane == 0) atomicExch(a.err, kDevCheck);
+        continue;
       }
-      a.order[pos + r] = x;
-    }
-    __syncwarp();
-    for (int i = lane; i < s; i += 32) a.alive[i == 0 ? v : a.arena[e1 - i]] = 0;
-    if (lane == 0) {
-      a.gstart[gi] = pos;
-      a.ground[gi] = a.round;
-      a.csize[v] = 0;
+      for (int i = lane; i < s; i += 32) {
+        const int x = i == 0 ? v : a.arena[e1 - i];
+        const int64_t dx = a.rp[x + 1] - a.rp[x];
+        int r = 0;
+        for (int t = 0; t < s; t++) {
+          const int y = t == 0 ? v : a.arena[e1 - t];
+          const int64_t dy = a.rp[y + 1] - a.rp[y];
+          r += (dy > dx || (dy == dx && y < x)) ? 1 : 0;
+        }
+        a.order[pos + r] = x;
+      }
+      __syncwarp();
+      for (int i = lane; i < s; i += 32) a.alive[i == 0 ? v : a.arena[e1 - i]] = 0;
+      if (lane == 0) {
+        a.gstart[gi] = pos;
+        a.ground[gi] = a.round;
+        a.csize[v] = 0;
+      }
     }
   }
 }
@@ -296,6 +458,7 @@ __global__ void advance_kernel(int64_t *ctl) {
   ctl[0] += t & 0xffffffffLL;
   ctl[1] += t >> 32;
   ctl[4] += 1;
+  *(unsigned *)(ctl + 6) = 0u;  // the block grower's list, empty for the next round
 }
 
 // a caller's tie rank must be a permutation of [0, n): seen[] starts at 0
@@ -466,7 +629,9 @@ __global__ void __launch_bounds__(kBigT) block_sort_kernel(const int64_t *nrp, i
   }
 }
 
-// sum over the entries of the relabelled graph of log2(1 + gap)
+// sum over the entries of the relabelled graph of log2(1 + gap): each term
+// in single precision (one rounding of 1 + gap, log2f within 1 ulp, so a
+// relative error below 2^-22), the sum in double
 __global__ void __launch_bounds__(kOT) gap_kernel(int64_t n, const int64_t *nrp, const int32_t *nci, double *total) {
   __shared__ double red[kOT / 32];
   const int lane = threadIdx.x & 31;
@@ -479,7 +644,7 @@ __global__ void __launch_bounds__(kOT) gap_kernel(int64_t n, const int64_t *nrp,
       const int64_t x = nci[e];
       const int64_t prev = e == e0 ? p : (int64_t)nci[e - 1];
       const int64_t gap = e == e0 ? (x > p ? x - p : p - x) : x - prev;
-      s += log2(1.0 + (double)gap);
+      s += (double)log2f((float)(gap + 1));
     }
   }
 #pragma unroll
@@ -546,12 +711,27 @@ int clique_order(mc_graph *g, const int32_t *rank, int32_t *d_order, int64_t *d_
   }
   MC_CUDA_TRY(cudaMemsetAsync(a.alive, 1, (size_t)n, g->stream));
   MC_CUDA_TRY(cudaMemsetAsync(a.csize, 0, (size_t)n * 4, g->stream));
-  const int gw = grid_of(g, n * 32, kOT, 8), gt = grid_of(g, n, 256, 8);
+  a.nbig = (unsigned *)(a.ctl + 6);
+  int32_t *scratch = nullptr;
+  const int big_blocks = 2 * g->sm_count;
+  const int64_t stride = std::max<int64_t>(g->max_degree, 1);
+  const bool any_big = g->max_degree > kBlockGrowMin;
+  if (any_big) {
+    MC_TRY(ws_get(g, "co.big", (size_t)n * 4, &p));
+    a.big = (int32_t *)p;
+    MC_TRY(ws_get(g, "co.bscratch", (size_t)big_blocks * stride * 4, &p));
+    scratch = (int32_t *)p;
+  }
+  const int gw = grid_of(g, (n + 31) / 32, kOT / 32, 8), gt = grid_of(g, n, 256, 8);
   int64_t *h = (int64_t *)((char *)g->h_small + 2560);
   int64_t placed = 0;
   for (int32_t r = 0;; r++) {
     a.round = r;
     grow_kernel<<<gw, kOT, 0, g->stream>>>(a);
+    if (any_big) {
+      grow_big_kernel<<<big_blocks, kBG, 0, g->stream>>>(a, scratch, stride);
+      g_launches++;
+    }
     scatter_kernel<<<gt, 256, 0, g->stream>>>(a);
     accept_kernel<<<gt, 256, 0, g->stream>>>(a);
     g_launches += 3;

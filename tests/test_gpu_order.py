@@ -3,10 +3,12 @@ cost (CUDA path through the C ABI) with oracle/ordering.py.
 
 The order is integer work with one defined answer (tie ranks make every key
 distinct), so order, clique boundaries and rounds must match bit for bit;
-the relabelled CSR too.  The gap cost is a float sum in another order: its
-relative difference must stay below 1e-12 (each log2 term is correctly
-rounded to within an ulp or two and the sum has fewer than 2^27 terms of
-the same sign, so 1e-12 leaves three orders of magnitude to spare).
+the relabelled CSR too.  The gap cost is a sum of positive terms that the
+kernel takes in single precision (1 + gap rounded once, relative error
+2^-24; log2f within 1 ulp, 2^-23 relative; together below 2^-22 = 2.4e-7 of
+each term, and so of the sum) and adds in double: the relative difference
+from the oracle's float64 must stay below 2.4e-7 plus the double sums' own
+rounding, so the tests allow 3e-7.
 """
 import numpy as np
 import pytest
@@ -16,6 +18,7 @@ import oracle
 from oracle import ordering as OO
 
 pytestmark = pytest.mark.gpu
+GAP_RTOL = 3e-7
 
 torch = pytest.importorskip("torch")
 
@@ -112,8 +115,9 @@ def test_relabel_and_gap_bits(mc, g):
         wrp, wci = OO.relabel(g, order)
         assert np.array_equal(rp, wrp) and np.array_equal(ci, wci)
         got, want = mc.mc_gap_bits(h, order), OO.gap_bits(g, order)
-        assert abs(got - want) <= 1e-12 * max(want, 1.0)
-    assert abs(mc.mc_gap_bits(h) - OO.gap_bits(g, np.arange(g.n))) <= 1e-12 * max(OO.gap_bits(g, np.arange(g.n)), 1)
+        assert abs(got - want) <= GAP_RTOL * want
+    ident = OO.gap_bits(g, np.arange(g.n))
+    assert abs(mc.mc_gap_bits(h) - ident) <= GAP_RTOL * ident
     for bad in (np.zeros(g.n, np.int32), np.full(g.n, g.n, np.int32)):
         with pytest.raises(mc.MCError) as e:
             mc.mc_relabel(h, bad)
