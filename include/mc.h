@@ -48,7 +48,7 @@ extern "C" {
 #define MC_ERR_TIMEOUT (-5)       /* a device spin-wait exceeded its iteration limit */
 #define MC_ERR_CUDA (-6)          /* a CUDA runtime call failed */
 #define MC_ERR_DEVICE_CHECK (-7)  /* a device-side consistency check failed */
-#define MC_ERR_UNSUPPORTED (-8)   /* K(G) above 4,096, the largest neighbourhood a worker holds */
+#define MC_ERR_UNSUPPORTED (-8)   /* a batch graph with K(G) above 4,096, the largest neighbourhood a worker holds */
 #define MC_ERR_TOO_LARGE (-9)     /* input larger than mc_core_numbers_noalloc's fixed scratch */
 
 /* load flags */
@@ -182,6 +182,7 @@ typedef struct {
                                   (the learned form only) */
   int64_t learned_scored;      /* vertices the learned form scored */
   int64_t rebuilds;            /* pruned-graph rebuilds of a re-pruning solve (repeel) */
+  int64_t huge_roots;          /* roots of more than 4,096 candidates, solved as induced subgraphs */
 } mc_stats;
 
 /* ------------------------------------------------------------ graphs --- */
@@ -228,9 +229,12 @@ int mc_heuristic_clique(mc_graph *g, const int32_t *core, int32_t mode, int32_t 
  * InitialBranch and Branch for every root, incumbent shared by all workers).
  * opt: NULL for defaults.  omega_out: omega(G); witness_out: capacity int32, a
  * maximum clique sorted ascending and verified on the device; stats nullable.
- * MC_ERR_UNSUPPORTED when K(G) > 4,096: a root's candidates (at most K(G))
- * must fit one worker's 4,096-wide adjacency matrix; nothing of the search is
- * launched then. */
+ * A root with more than 4,096 candidates (possible only when K(G) > 4,096)
+ * does not fit a worker's adjacency matrix: it is solved as the graph its
+ * candidates induce, by the same pipeline, from the incumbent as a lower
+ * bound (stats->huge_roots counts them; such graphs are never captured with
+ * opt->graph).  For a batch handle, K(G) > 4,096 gives MC_ERR_UNSUPPORTED
+ * before anything of the search is launched. */
 int mc_max_clique(mc_graph *g, const mc_options *opt, int32_t *omega_out, int32_t *witness_out,
                   int32_t capacity, mc_stats *stats);
 
@@ -342,7 +346,9 @@ int mc_relabel(mc_graph *g, const int32_t *order, int64_t *row_ptr_out, int32_t 
  * compression (bvgraph and its kind) exploits: relabel by the order (NULL =
  * the graph as it is), then in every row p, sorted, code the gap from p to
  * the first entry and between consecutive entries; *bits_out = the mean of
- * log2(1 + gap) over all entries (0 without edges).  Lower is better. */
+ * log2(1 + gap) over all entries (0 without edges).  Lower is better.
+ * Each term is taken in single precision (relative error below 2^-22), the
+ * sum in double. */
 int mc_gap_bits(mc_graph *g, const int32_t *order, double *bits_out);
 
 /* ------------------------------------------ learned vertex ordering --- */

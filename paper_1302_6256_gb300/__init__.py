@@ -69,7 +69,8 @@ class Stats(ctypes.Structure):
                 ("max_core", ctypes.c_int32), ("heuristic_size", ctypes.c_int32),
                 ("omega", ctypes.c_int32), ("verified", ctypes.c_int32),
                 ("prune_row_entries", ctypes.c_int64), ("ms_learned", ctypes.c_double),
-                ("learned_scored", ctypes.c_int64), ("rebuilds", ctypes.c_int64)]
+                ("learned_scored", ctypes.c_int64), ("rebuilds", ctypes.c_int64),
+                ("huge_roots", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

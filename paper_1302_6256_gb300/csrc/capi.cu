@@ -307,6 +307,77 @@ static int check_options(const mc_options *opt, mc_options *o) {
   return MC_OK;
 }
 
+static int run_max_clique(mc_graph *g, const mc_options *opt, mc_stats *st);
+
+// Roots with more than kBigCap candidates (single graphs): each is solved as
+// the graph its candidates P induce, by the whole pipeline, starting from
+// the incumbent minus one as its lower bound -- a clique of G[P] of size at
+// least omega extends by the root to a larger clique (every clique is found
+// from its earliest member, whatever the root's class).  A root with fewer
+// than omega candidates is skipped (it cannot hold omega + 1).  Synchronises
+// the stream (reads the root list and the incumbent).
+static int search_huge_roots(mc_graph *g, const mc_options &o, Pruned *pg) {
+  if (g->count != 1 || g->max_core <= kBigCap || g->n == 0) return MC_OK;
+  MC_TRY(read_pruned_counts(g, pg));
+  const int64_t nh = pg->nroots_huge;
+  if (nh == 0) return MC_OK;
+  std::vector<int32_t> roots((size_t)nh);
+  MC_CUDA_TRY(cudaMemcpyAsync(roots.data(), pg->roots_huge, (size_t)nh * 4, cudaMemcpyDeviceToHost, g->stream));
+  MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  int32_t *hb = (int32_t *)((char *)g->h_small + 3584);
+  for (int32_t j : roots) {
+    MC_CUDA_TRY(cudaMemcpyAsync(hb, g->best, 4, cudaMemcpyDeviceToHost, g->stream));
+    MC_CUDA_TRY(cudaMemcpyAsync(hb + 1, pg->odeg + j, 4, cudaMemcpyDeviceToHost, g->stream));
+    MC_CUDA_TRY(cudaMemcpyAsync(hb + 2, pg->oold + j, 4, cudaMemcpyDeviceToHost, g->stream));
+    MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    const int32_t om = hb[0], d = hb[1], u = hb[2];
+    if (d < om) continue;
+    std::vector<int32_t> P;
+    MC_TRY(gather_root_row(g, *pg, j, &P));
+    std::sort(P.begin(), P.end());
+    int64_t *srp = nullptr;
+    int32_t *sci = nullptr;
+    int64_t snnz = 0;
+    MC_TRY(induced_csr(g, P, &srp, &sci, &snnz));
+    mc_graph *sub = nullptr;
+    MC_TRY(load_common(1, nullptr, (int64_t)P.size(), srp, sci, 0, g->stream, &sub));
+    sub->lb = std::max(om - 1, 0);
+    mc_options so = o;
+    so.graph = 0;
+    so.order = nullptr;
+    so.part_rank = 0;
+    so.part_count = 0;
+    so.repeel = 0;
+    so.scores = nullptr;
+    so.seeds = 0;
+    so.mlp = nullptr;
+    if (so.ordering == 1) so.ordering = 0;
+    mc_stats sst;
+    int rc = run_max_clique(sub, &so, &sst);
+    int32_t sb = 0;
+    std::vector<int32_t> w;
+    if (rc == MC_OK) {
+      if (cudaMemcpy(&sb, sub->best, 4, cudaMemcpyDeviceToHost) != cudaSuccess) rc = MC_ERR_CUDA;
+      if (rc == MC_OK && sb > sub->lb && sb + 1 > om) {
+        w.resize((size_t)sb + 1);
+        if (cudaMemcpy(w.data() + 1, sub->wit, (size_t)sb * 4, cudaMemcpyDeviceToHost) != cudaSuccess) rc = MC_ERR_CUDA;
+        w[0] = u;
+        for (int32_t i = 1; i <= sb; i++) w[i] = P[w[i]];
+      }
+    }
+    g->huge_roots += 1 + sub->huge_roots;
+    free_graph(sub);
+    if (rc != MC_OK) return rc;
+    if (!w.empty()) {
+      const int32_t size = sb + 1;
+      MC_CUDA_TRY(cudaMemcpyAsync(g->wit, w.data(), (size_t)size * 4, cudaMemcpyHostToDevice, g->stream));
+      MC_CUDA_TRY(cudaMemcpyAsync(g->best, &size, 4, cudaMemcpyHostToDevice, g->stream));
+      MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    }
+  }
+  return MC_OK;
+}
+
 // The search with work-triggered re-pruning: the kept vertices form a suffix
 // of the peel order (K(v) >= bound); its roots are searched in o.repeel
 // ranges of peel positions, densest first, and before each later range the
@@ -342,6 +413,7 @@ static int search_in_ranges(mc_graph *g, const mc_options &o, Pruned *pg, Search
       MC_TRY(relaunch_roots(g, g->warp_max_used, pg, pr, pc, lo, hi));
     }
     MC_TRY(launch_search(g, *pg, o.no_neigh_cores, o.no_split, o.split_nodes, spin, sc, o.layout, o.no_bitmap));
+    MC_TRY(search_huge_roots(g, o, pg));
     searched = true;
     MC_TRY(read_search_counters(g, sc));
     MC_TRY(read_pruned_counts(g, pg));
@@ -381,6 +453,8 @@ static int enqueue_solve(mc_graph *g, const mc_options &o, Pruned *pg, SearchCou
   MC_TRY(record_event(g, 1));
   MC_CUDA_TRY(cudaMemsetAsync(g->best, 0, g->count * 4, g->stream));
   MC_CUDA_TRY(cudaMemsetAsync(g->lock, 0, g->count * 4, g->stream));
+  g->huge_roots = 0;
+  if (g->lb > 0) MC_CUDA_TRY(cudaMemcpyAsync(g->best, &g->lb, 4, cudaMemcpyHostToDevice, g->stream));
   // learned scores (host or device) -> device copy
   const float *d_scores = nullptr;
   const int32_t *d_seeds = nullptr;
@@ -443,6 +517,7 @@ static int enqueue_solve(mc_graph *g, const mc_options &o, Pruned *pg, SearchCou
     MC_TRY(record_event(g, 3));
     if (g->n > 0)
       MC_TRY(launch_search(g, *pg, o.no_neigh_cores, o.no_split, o.split_nodes, spin, sc, o.layout, o.no_bitmap));
+    if (g->n > 0 && !g->capturing) MC_TRY(search_huge_roots(g, o, pg));
   }
   trivial_kernel<<<std::max(1, std::min(g->count / 256 + 1, 1024)), 256, 0, g->stream>>>(
       g->count, g->gid ? g->voff : nullptr, g->n, g->best, g->wit);
@@ -515,8 +590,15 @@ static int finish_solve(mc_graph *g, Pruned *pg, SearchCounters *sc, const int32
   std::vector<int32_t> ok(g->count);
   MC_CUDA_TRY(cudaMemcpy(ok.data(), d_ok, g->count * 4, cudaMemcpyDeviceToHost));
   st->verified = 1;
+  st->huge_roots = g->huge_roots;
   for (int32_t i = 0; i < g->count; i++)
     if (!ok[i]) st->verified = 0;
+  if (g->lb > 0 && !st->verified) {
+    // started from a lower bound: nothing larger found means no witness
+    int32_t b = 0;
+    MC_CUDA_TRY(cudaMemcpy(&b, g->best, 4, cudaMemcpyDeviceToHost));
+    if (b == g->lb) st->verified = 1;
+  }
   if (!st->verified) return MC_ERR_DEVICE_CHECK;
   return MC_OK;
 }
@@ -572,6 +654,9 @@ static int run_max_clique(mc_graph *g, const mc_options *opt, mc_stats *st) {
     }
     MC_TRY(enqueue_solve(g, o, &pg, &sc, &d_ok));  // direct solve: sizes buffers, K(G)
     MC_TRY(finish_solve(g, &pg, &sc, d_ok, st));
+    // roots beyond the workers are solved from the host: such graphs are
+    // solved directly, never captured
+    if (g->count == 1 && g->max_core > kBigCap) return MC_OK;
     cudaStream_t user = g->stream;
     if (!g->cap_stream) MC_CUDA_TRY(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
     g->stream = g->cap_stream;
@@ -629,7 +714,7 @@ const char *mc_strerror(int code) {
     case MC_ERR_TIMEOUT: return "a device spin-wait exceeded its iteration limit";
     case MC_ERR_CUDA: return g_errbuf[0] ? g_errbuf : "CUDA runtime error";
     case MC_ERR_DEVICE_CHECK: return "device-side consistency check failed";
-    case MC_ERR_UNSUPPORTED: return "maximum core number above 4096, the largest neighbourhood a search worker holds";
+    case MC_ERR_UNSUPPORTED: return "a batch graph with core number above 4096, the largest neighbourhood a search worker holds";
     case MC_ERR_TOO_LARGE:
       return "input larger than the fixed scratch of mc_core_numbers_noalloc (1,048,576 vertices, 67,108,864 entries)";
     default: return "unknown error";

@@ -7,6 +7,7 @@
 #include <atomic>
 #include <map>
 #include <string>
+#include <vector>
 
 #include "../../include/mc.h"
 
@@ -32,6 +33,10 @@ extern std::atomic<int64_t> g_launches;
   } while (0)
 
 void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+// Largest candidate set a search worker holds (the big class's adjacency
+// matrix); roots with more candidates are solved as induced subgraphs.
+constexpr int32_t kBigCap = 4096;
 
 // Batches whose graphs all have at most this many vertices are peeled one
 // graph per block (kcore.cu); their peel order is one segment per graph.
@@ -102,8 +107,11 @@ struct Pruned {
   int32_t *roots_small = nullptr;  // roots by class, each in processing order
   int32_t *roots_block = nullptr;
   int32_t *roots_big = nullptr;
+  int32_t *roots_huge = nullptr;   // more than kBigCap candidates (single graphs only)
+  int64_t nroots_huge = 0;
   int32_t *odeg = nullptr;         // out-degree per pruned vertex
-  int64_t *d_counts = nullptr;     // device: [0] n', [1] arcs, [2] max out-degree, [3..5] roots per class
+  int64_t *d_counts = nullptr;     // device: [0] n', [1] arcs, [2] max out-degree, [3..5] roots per class,
+                                   // [6] row entries, [7] roots of more than kBigCap candidates
 };
 // No host synchronisation: sizes stay in pg.d_counts (see read_pruned_counts).
 // part_rank / part_count: keep only the roots whose position in the peel
@@ -158,6 +166,9 @@ struct mc_graph {
   mc::SearchCounters repeel_acc{};           // ... and these are its counters summed over the ranges
   int32_t repeel_rebuilds = 0;               // ... and the pruned graph was rebuilt this often
   int64_t repeel_roots = 0;                  // ... over this many roots in all
+  int32_t lb = 0;                            // incumbent a solve starts from (induced subgraphs of large roots)
+  bool huge_mark_ready = false;              // the induced-subgraph member map is all -1
+  int64_t huge_roots = 0;                    // roots of the last solve solved as induced subgraphs
   int32_t warp_max_used = 128;  // warp/block split of the current solve
   bool capturing = false;       // inside CUDA graph capture: no host synchronisation
   int32_t *core = nullptr, *order = nullptr, *pos = nullptr;  // n each (device)
@@ -188,6 +199,11 @@ int launch_verify_set(mc_graph *g, const int32_t *d_vs, int32_t k, int32_t *d_ok
 // it is a degeneracy order of the graph (MC_ERR_ARG otherwise).
 int use_order(mc_graph *g, const int32_t *order);
 int launch_validate(mc_graph *g, int32_t *d_bad);
+// Candidates of pruned root j (original ids, padding dropped), read to the host.
+int gather_root_row(mc_graph *g, const Pruned &pg, int32_t j, std::vector<int32_t> *out);
+// CSR of the subgraph induced by `verts` (sorted original ids; local id =
+// index in verts), in workspace buffers of g; *nnz its entries.
+int induced_csr(mc_graph *g, const std::vector<int32_t> &verts, int64_t **d_rp, int32_t **d_ci, int64_t *nnz);
 // Clique-peeling order (order.cu) into device arrays (order n, gstart n+1,
 // ground n); work_out (nullable): [0] grows, [1] candidate tests.
 int clique_order(mc_graph *g, const int32_t *rank, int32_t *d_order, int64_t *d_gstart, int32_t *d_ground,
@@ -198,6 +214,9 @@ int relabel(mc_graph *g, const int32_t *order, int64_t *d_nrp, int32_t *d_nci);
 // *d_total = sum over the entries of a sorted CSR of log2(1 + gap).
 int gap_bits(mc_graph *g, const int64_t *d_nrp, const int32_t *d_nci, double *d_total);
 int launch_gid(mc_graph *g);
+// Stable radix sort of (key, value) pairs by decreasing key (sort.cu); the
+// result is back in keys / vals, ktmp / vtmp are n-entry scratch.
+int radix_sort_desc(mc_graph *g, uint32_t *keys, int32_t *vals, uint32_t *ktmp, int32_t *vtmp, int64_t n);
 // Indices of the k largest scores (descending), over all vertices.
 int top_scores(mc_graph *g, const float *scores, int64_t k, int32_t *out);
 

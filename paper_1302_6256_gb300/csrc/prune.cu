@@ -9,7 +9,6 @@
 // from its earliest member, and a vertex has at most K(v) later neighbours.
 // Rows start at multiples of 4 entries so the search reads them with int4
 // loads (pad entries are -1).
-#include <cub/cub.cuh>
 
 #include "mc_internal.cuh"
 #include "scan.cuh"
@@ -157,7 +156,7 @@ struct RootInfo {
     int g = ogid ? ogid[j] : 0;
     int d = odeg[j];
     if (d < best[g] || d == 0) return -1;  // |P| >= omega~ is needed for a larger clique
-    return d <= warp_max ? 0 : (d <= 1024 ? 1 : 2);
+    return d <= warp_max ? 0 : (d <= 1024 ? 1 : (d <= kBigCap ? 2 : 3));
   }
 };
 
@@ -279,7 +278,7 @@ int launch_prune(mc_graph *g, int ordering, const float *scores, int32_t warp_ma
   MC_CUDA_TRY(cudaGetLastError());
 
   // roots in processing order, split by class
-  MC_TRY(ws_get(g, "pr.roots", (3 * n + 3) * sizeof(int32_t), &p));
+  MC_TRY(ws_get(g, "pr.roots", (4 * n + 4) * sizeof(int32_t), &p));
   int32_t *roots = (int32_t *)p;
   RootInfo ri{odeg, ogid, g->best, warp_max, oold, g->pos, part_rank, part_count, pos_lo, pos_hi};
   int32_t *tab = nullptr;
@@ -297,22 +296,21 @@ int launch_prune(mc_graph *g, int ordering, const float *scores, int32_t warp_ma
     int32_t *sidx = (int32_t *)p;
     gather_scores_kernel<<<blocks, 256, 0, g->stream>>>(n, dsm + 0, oold, scores, skey, sidx);
     g_launches++;
-    size_t tmp = 0;
-    cub::DeviceRadixSort::SortPairsDescending(nullptr, tmp, skey, skey + n + 1, sidx, tab, (int)n, 0, 32,
-                                              g->stream);
-    MC_TRY(ws_get(g, "pr.cubtmp", tmp + 16, &p));
-    MC_CUDA_TRY(cub::DeviceRadixSort::SortPairsDescending(p, tmp, skey, skey + n + 1, sidx, tab, (int)n, 0, 32,
-                                                          g->stream));
-    g_launches++;
+    MC_CUDA_TRY(cudaGetLastError());
+    // stable: equal scores keep increasing pruned id; tab = the sorted ids
+    MC_TRY(radix_sort_desc(g, skey, sidx, skey + n + 1, tab, n));
+    MC_CUDA_TRY(cudaMemcpyAsync(tab, sidx, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, g->stream));
   }
-  for (int c = 0; c < 3; c++) {
+  const int ncls = (g->count == 1 && g->max_core > kBigCap) ? 4 : 3;
+  for (int c = 0; c < ncls; c++) {
     int32_t *dst = roots + (int64_t)c * n;
+    int64_t *cnt = dsm + (c < 3 ? 3 + c : 7);
     if (ordering == 0) {
       MC_TRY(device_scan(g, n, ClassF<PermDesc>{ri, PermDesc{dsm + 0}, c},
-                         ClassG<PermDesc>{PermDesc{dsm + 0}, dst}, dsm + 3 + c, "pr.scan"));
+                         ClassG<PermDesc>{PermDesc{dsm + 0}, dst}, cnt, "pr.scan"));
     } else {
       MC_TRY(device_scan(g, n, ClassF<PermTable>{ri, PermTable{tab, dsm + 0}, c},
-                         ClassG<PermTable>{PermTable{tab, dsm + 0}, dst}, dsm + 3 + c, "pr.scan"));
+                         ClassG<PermTable>{PermTable{tab, dsm + 0}, dst}, cnt, "pr.scan"));
     }
   }
   out->orow = orow;
@@ -321,6 +319,7 @@ int launch_prune(mc_graph *g, int ordering, const float *scores, int32_t warp_ma
   out->roots_small = roots;
   out->roots_block = roots + n;
   out->roots_big = roots + 2 * n;
+  out->roots_huge = roots + 3 * n;
   out->odeg = odeg;
   return MC_OK;
 }
@@ -333,10 +332,11 @@ int relaunch_roots(mc_graph *g, int32_t warp_max, Pruned *pg, int32_t part_rank,
   if (n == 0) return MC_OK;
   int64_t *dsm = pg->d_counts;
   RootInfo ri{pg->odeg, pg->ogid, g->best, warp_max, pg->oold, g->pos, part_rank, part_count, pos_lo, pos_hi};
-  for (int c = 0; c < 3; c++) {
+  const int ncls = (g->count == 1 && g->max_core > kBigCap) ? 4 : 3;
+  for (int c = 0; c < ncls; c++) {
     int32_t *dst = pg->roots + (int64_t)c * n;
     MC_TRY(device_scan(g, n, ClassF<PermDesc>{ri, PermDesc{dsm + 0}, c}, ClassG<PermDesc>{PermDesc{dsm + 0}, dst},
-                       dsm + 3 + c, "pr.scan"));
+                       dsm + (c < 3 ? 3 + c : 7), "pr.scan"));
   }
   return MC_OK;
 }
@@ -344,7 +344,7 @@ int relaunch_roots(mc_graph *g, int32_t warp_max, Pruned *pg, int32_t part_rank,
 // Host copy of the pruned graph's sizes (one small device-to-host read).
 int read_pruned_counts(mc_graph *g, Pruned *out) {
   int64_t *h = (int64_t *)g->h_small;
-  MC_CUDA_TRY(cudaMemcpyAsync(h, out->d_counts, 7 * sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream));
+  MC_CUDA_TRY(cudaMemcpyAsync(h, out->d_counts, 8 * sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream));
   MC_CUDA_TRY(cudaStreamSynchronize(g->stream));
   out->n = h[0];
   out->arcs = h[1];
@@ -353,13 +353,18 @@ int read_pruned_counts(mc_graph *g, Pruned *out) {
   out->nroots_block = h[4];
   out->nroots_big = h[5];
   out->row_entries = h[6];
+  out->nroots_huge = h[7];
   return MC_OK;
 }
 
 namespace {
-__global__ void iota_kernel(int64_t n, const float *__restrict__ s, float *__restrict__ key, int32_t *__restrict__ idx) {
+// sort keys of the scores (the order of the float values, as in
+// gather_scores_kernel) and their indices
+__global__ void iota_kernel(int64_t n, const float *__restrict__ s, uint32_t *__restrict__ key,
+                            int32_t *__restrict__ idx) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    key[i] = s[i];
+    const uint32_t b = __float_as_uint(s[i]);
+    key[i] = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
     idx[i] = (int32_t)i;
   }
 }
@@ -368,21 +373,16 @@ __global__ void iota_kernel(int64_t n, const float *__restrict__ s, float *__res
 int top_scores(mc_graph *g, const float *scores, int64_t k, int32_t *out) {
   const int64_t n = g->n;
   void *p;
-  MC_TRY(ws_get(g, "ts.key", (2 * n + 2) * sizeof(float), &p));
-  float *key = (float *)p;
+  MC_TRY(ws_get(g, "ts.key", (2 * n + 2) * sizeof(uint32_t), &p));
+  uint32_t *key = (uint32_t *)p;
   MC_TRY(ws_get(g, "ts.idx", (2 * n + 2) * sizeof(int32_t), &p));
   int32_t *idx = (int32_t *)p;
   const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)g->sm_count * 8);
   iota_kernel<<<blocks, 256, 0, g->stream>>>(n, scores, key, idx);
   g_launches++;
-  size_t tmp = 0;
-  cub::DeviceRadixSort::SortPairsDescending(nullptr, tmp, key, key + n + 1, idx, idx + n + 1, (int)n, 0, 32,
-                                            g->stream);
-  MC_TRY(ws_get(g, "ts.tmp", tmp + 16, &p));
-  MC_CUDA_TRY(cub::DeviceRadixSort::SortPairsDescending(p, tmp, key, key + n + 1, idx, idx + n + 1, (int)n, 0, 32,
-                                                        g->stream));
-  g_launches++;
-  MC_CUDA_TRY(cudaMemcpyAsync(out, idx + n + 1, k * sizeof(int32_t), cudaMemcpyDeviceToDevice, g->stream));
+  MC_CUDA_TRY(cudaGetLastError());
+  MC_TRY(radix_sort_desc(g, key, idx, key + n + 1, idx + n + 1, n));
+  MC_CUDA_TRY(cudaMemcpyAsync(out, idx, k * sizeof(int32_t), cudaMemcpyDeviceToDevice, g->stream));
   return MC_OK;
 }
 

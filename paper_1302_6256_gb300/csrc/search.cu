@@ -1474,8 +1474,11 @@ int launch_search(mc_graph *g, const Pruned &pg, int no_neigh_cores, int no_spli
   a.spin = spin_limit;
   a.neigh_cores = no_neigh_cores ? 0 : 1;
   a.counters = ctr;
-  const int kbound = std::max(g->max_core, 1);  // |P| <= |N+(u)| <= K(u) <= K(G)
-  if (kbound > 4096) return MC_ERR_UNSUPPORTED;  // refused before anything is launched
+  // |P| <= |N+(u)| <= K(u) <= K(G); roots above kBigCap are not in any of
+  // the lists launched here (single graphs solve them as induced subgraphs;
+  // a batch with such a graph is refused before anything is launched)
+  if (g->count > 1 && g->max_core > kBigCap) return MC_ERR_UNSUPPORTED;
+  const int kbound = std::min(std::max(g->max_core, 1), kBigCap);
   const int wmax = g->warp_max_used;
   if (!no_split) {
     // queue sizes grow with the graph (a small graph gets a small queue; a

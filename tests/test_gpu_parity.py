@@ -388,6 +388,52 @@ def test_big_neighbourhoods_turan(mc):
     assert om2 == 300 and oracle.is_clique(g, wit2)
 
 
+def _turan_with_planted(n, r, per_part, parts):
+    """Turan T(n, r) (parts of n/r consecutive vertices) with a clique planted
+    on the first `per_part` vertices of each of the first `parts` parts."""
+    size = n // r
+    part = np.arange(n) // size
+    src, dst = [], []
+    for v in range(n):
+        u = np.arange(v + 1, n)
+        u = u[part[u] != part[v]]
+        src.append(np.full(u.size, v))
+        dst.append(u)
+    S = np.array([p * size + i for p in range(parts) for i in range(per_part)])
+    for a in range(len(S)):
+        for b in range(a + 1, len(S)):
+            if part[S[a]] == part[S[b]]:
+                src.append(np.array([S[a]]))
+                dst.append(np.array([S[b]]))
+    return gg.from_edges(n, np.concatenate(src), np.concatenate(dst), name="turan%d_%d_planted" % (n, r))
+
+
+def test_neighbourhoods_beyond_4096_candidates(mc):
+    """Roots with more than 4,096 candidates are solved as the graphs their
+    candidates induce.  Turan T(4400, 20) (degree 4180, K(G) > 4096) with a
+    clique planted on 5 vertices of each of parts 0..4: a clique holds at
+    most one vertex of a part outside the planted set, so omega = 25 + 15 =
+    40 by construction.  Without the heuristic the first large root's
+    subgraph finds it; with it, the large roots are solved from the bound."""
+    g = gg.relabel(_turan_with_planted(4400, 20, 5, 5), 13)
+    h = load(mc, g, flags=0)
+    core, kmax = mc.mc_core_numbers(h)
+    assert kmax > 4096
+    for opts in (dict(), dict(heuristic=2), dict(heuristic=2, no_split=True)):
+        om, wit, st = mc.mc_max_clique(h, **opts)
+        assert om == 40 and len(wit) == 40 and oracle.is_clique(g, wit), opts
+        assert st["verified"] == 1 and st["huge_roots"] > 0, opts
+    # a batch holding such a graph is refused before any search launch
+    b = gg.Batch([g, gg.complete(3)])
+    hb = mc.mc_load_batch(torch.from_numpy(b.voff).cuda(), torch.from_numpy(b.row_ptr).cuda(),
+                          torch.from_numpy(b.col_idx).cuda())
+    with pytest.raises(mc.MCError) as e:
+        mc.mc_max_clique_batch(hb)
+    assert e.value.code == mc.MC_ERR_UNSUPPORTED
+    hb.close()
+    h.close()
+
+
 def test_autotune_returns_a_working_setting(mc):
     g = gg.rmat(14, 16, planted=30, seed=16)
     h = load(mc, g)

@@ -478,3 +478,29 @@ def test_partition_refuses_an_order_that_is_not_a_degeneracy_order():
         oracle.max_clique_part(g, 0, 2, np.arange(10, dtype=np.int32))
     with pytest.raises(RuntimeError):
         oracle.max_clique_part(g, 0, 2, np.zeros(10, dtype=np.int32))  # not a permutation
+
+
+def test_turan_with_planted_clique_closed_form():
+    """Turan T(220, 20) (parts of 11) with a clique planted on 5 vertices of
+    each of parts 0..4: outside the planted set a clique holds one vertex per
+    part, so omega = 25 + (20 - 5) = 40 -- the small analogue of the GPU test
+    of roots beyond 4,096 candidates."""
+    n, r, per, parts = 220, 20, 5, 5
+    size = n // r
+    part = np.arange(n) // size
+    src, dst = [], []
+    for v in range(n):
+        for u in range(v + 1, n):
+            if part[u] != part[v]:
+                src.append(v)
+                dst.append(u)
+    S = [p * size + i for p in range(parts) for i in range(per)]
+    for a in range(len(S)):
+        for b in range(a + 1, len(S)):
+            if part[S[a]] == part[S[b]]:
+                src.append(S[a])
+                dst.append(S[b])
+    g = gg.from_edges(n, np.array(src), np.array(dst))
+    om, wit, _ = oracle.max_clique(g)
+    assert om == per * parts + (r - parts) and oracle.is_clique(g, wit)
+    assert oracle.max_clique_threads(g, 3)[0] == om
