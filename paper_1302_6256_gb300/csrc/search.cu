@@ -781,11 +781,19 @@ __device__ __forceinline__ void load_P(const SA &a, int u, int om, int *Pidx, in
 // memory system instead of one.
 template <class Lookup>
 __device__ __forceinline__ void build_rows(const SA &a, const int *Pidx, int p, const Lookup &find, uint32_t *A, int Ws,
-                                           int wid, int nw, unsigned long long *count) {
+                                           int wid, int nw, unsigned long long *count, int *dyn = nullptr) {
   const int lane = threadIdx.x & 31;
   const int grp = lane >> 3, gl = lane & 7;
   unsigned long long scanned = 0;
-  for (int i0 = wid * 4; i0 < p; i0 += nw * 4) {
+  // groups of 4 rows: statically wid, wid + nw, ...; or, with a shared
+  // counter (dyn, zero before the call), taken by each warp as it frees up,
+  // so rows of uneven length do not leave warps waiting at the next barrier
+  int i0 = wid * 4;
+  if (dyn) {
+    if (lane == 0) i0 = atomicAdd(dyn, 4);
+    i0 = __shfl_sync(FULL, i0, 0);
+  }
+  for (; i0 < p;) {
     const int i = i0 + grp;
     int64_t e0 = 0, e1 = 0;
     if (i < p) {
@@ -815,6 +823,12 @@ __device__ __forceinline__ void build_rows(const SA &a, const int *Pidx, int p, 
           if (b >= 0) atomicOr(A + (int64_t)i * Ws + (b >> 5), 1u << (b & 31));
         }
       }
+    }
+    if (dyn) {
+      if (lane == 0) i0 = atomicAdd(dyn, 4);
+      i0 = __shfl_sync(FULL, i0, 0);
+    } else {
+      i0 += nw * 4;
     }
   }
   // row entries scanned (Fact 3's work), one atomic per warp
@@ -1112,6 +1126,7 @@ __global__ void __launch_bounds__(kBT, (SM && PC <= kMidCap) ? 2 : 1) search_blo
       ctl[0] = atomicAdd(a.next, 1);
       ctl[2] = 0;
       ctl[5] = *(volatile int32_t *)a.err;
+      ctl[6] = 0;  // the row builder's group counter
     }
     __syncthreads();
     const int idx = ctl[0];
@@ -1182,9 +1197,9 @@ __global__ void __launch_bounds__(kBT, (SM && PC <= kMidCap) ? 2 : 1) search_blo
     if (!SM) __threadfence();
     __syncthreads();
     if (use_bm)
-      build_rows(a, Pidx, p, BitmapLookup{bm, pre, base, p}, A, Ws, wid, kBW, a.counters + 5);
+      build_rows(a, Pidx, p, BitmapLookup{bm, pre, base, p}, A, Ws, wid, kBW, a.counters + 5, &ctl[6]);
     else
-      build_rows(a, Pidx, p, HashLookup{hk, hv, hmask}, A, Ws, wid, kBW, a.counters + 5);
+      build_rows(a, Pidx, p, HashLookup{hk, hv, hmask}, A, Ws, wid, kBW, a.counters + 5, &ctl[6]);
     if (!SM) __threadfence();
     __syncthreads();
     if (use_bm)
