@@ -1157,14 +1157,16 @@ __global__ void __launch_bounds__(kBT, (SM && PC <= kMidCap) ? 2 : 1) search_blo
       break;
     }
     if (p < om || p == 0) continue;
-    int np2 = 32;
-    while (np2 < p) np2 <<= 1;
-    bitonic_desc<true>(Pidx, np2, tid, kBT);
     const int wwin = (int)((npr - base + 31) >> 5);
     if (use_bm) {
+      // P in any order: its bits, the prefix counts, and then every member
+      // moves to its index in decreasing-rank order, which the counts give
+      // (the hash table's space, unused on this path, holds the list)
+      int *tmp = hk;
       for (int i = tid; i < p; i += kBT) {
-        const int r = Pidx[i] - base;
-        atomicOr(&bm[r >> 5], 1u << (r & 31));
+        const int y = Pidx[i];
+        atomicOr(&bm[(y - base) >> 5], 1u << ((y - base) & 31));
+        tmp[i] = y;
       }
       __syncthreads();
       // pre[w] = members in words [0, w): each thread counts a contiguous
@@ -1189,7 +1191,13 @@ __global__ void __launch_bounds__(kBT, (SM && PC <= kMidCap) ? 2 : 1) search_blo
         pre[w] = (uint16_t)run;
         run += __popc(bm[w]);
       }
+      __syncthreads();
+      const BitmapLookup at{bm, pre, base, p};
+      for (int i = tid; i < p; i += kBT) Pidx[at(tmp[i])] = tmp[i];
     } else {
+      int np2 = 32;
+      while (np2 < p) np2 <<= 1;
+      bitonic_desc<true>(Pidx, np2, tid, kBT);
       for (int i = tid; i < p; i += kBT) hash_insert(hk, hv, hmask, Pidx[i], i);
     }
     const int W = (p + 31) >> 5, Ws = W | 1;
