@@ -144,4 +144,10 @@ def test_argument_errors_before_any_cuda_call():
     dummy = ctypes.c_int64(0)
     p = ctypes.addressof(dummy)
     assert L.mc_core_numbers_noalloc((1 << 20) + 1, p, p, p, None, None) == mc.MC_ERR_TOO_LARGE
-    assert L.mc_strerror(mc.MC_ERR_UNSUPPORTED).decode().startswith("maximum core number above 4096")
+    assert L.mc_strerror(mc.MC_ERR_UNSUPPORTED).decode().startswith("a batch graph with core number above 4096")
+    # the clique-peeling order, relabelling and gap cost refuse a null handle
+    groups = ctypes.c_int64(5)
+    assert L.mc_clique_order(None, None, None, None, None, ctypes.byref(groups), None) == mc.MC_ERR_ARG
+    assert L.mc_relabel(None, None, None, None) == mc.MC_ERR_ARG
+    bits = ctypes.c_double(1.0)
+    assert L.mc_gap_bits(None, None, ctypes.byref(bits)) == mc.MC_ERR_ARG
