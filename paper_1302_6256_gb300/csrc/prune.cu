@@ -76,30 +76,79 @@ struct KeepG {
   }
 };
 
-// out-degree in the oriented pruned graph (warp per vertex)
-__global__ void outdeg_kernel(const int64_t *__restrict__ d_np, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                              const int32_t *__restrict__ oold, const int32_t *__restrict__ nid,
-                              int32_t *__restrict__ odeg, int32_t *__restrict__ maxout,
-                              unsigned long long *__restrict__ scanned) {
+// Rows of the kept vertices in chunks of kRowChunk entries, so that a hub's
+// row (163,305 entries at R-MAT scale 22) is split over many warps instead
+// of holding one warp while the rest of the grid idles.
+constexpr int kRowChunk = 1024;
+
+struct ChunkF {  // chunks of kept row j
+  const int64_t *rp, *np;
+  const int32_t *oold;
+  __device__ int64_t operator()(int64_t j) const {
+    if (j >= *np) return 0;
+    const int v = oold[j];
+    return (rp[v + 1] - rp[v] + kRowChunk - 1) / kRowChunk;
+  }
+};
+struct ChunkG {
+  int64_t *coff;
+  __device__ void operator()(int64_t j, int64_t excl, int64_t) const { coff[j] = excl; }
+};
+struct CntF {  // kept entries of chunk c
+  const int32_t *ccnt;
+  __device__ int64_t operator()(int64_t c) const { return ccnt[c]; }
+};
+struct PosG {
+  int64_t *cpos;
+  __device__ void operator()(int64_t c, int64_t excl, int64_t) const { cpos[c] = excl; }
+};
+
+// row j of chunk c: the last j with coff[j] <= c (coff[np] = the chunk count)
+__device__ __forceinline__ int64_t chunk_row(const int64_t *coff, int64_t np, int64_t c) {
+  int64_t lo = 0, hi = np;  // coff[lo] <= c < coff[hi]
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (coff[mid] <= c) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// kept entries (later neighbours) per chunk, summed into the row's
+// out-degree; one warp per chunk
+__global__ void outdeg_chunk_kernel(const int64_t *__restrict__ d_np, const int64_t *__restrict__ coff,
+                                    const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                    const int32_t *__restrict__ oold, const int32_t *__restrict__ nid,
+                                    int32_t *__restrict__ ccnt, int32_t *__restrict__ odeg,
+                                    unsigned long long *__restrict__ scanned) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t np = *d_np;
-  int lmax = 0;
+  const int64_t np = *d_np, nch = coff[np];
   unsigned long long rows = 0;
-  for (int64_t j = w0; j < np; j += nw) {
-    int v = oold[j];
-    int c = 0;
-    for (int64_t e = rp[v] + lane; e < rp[v + 1]; e += 32) c += (nid[ci[e]] > (int32_t)j) ? 1 : 0;
-    c = dev::warp_sum(c);
-    if (lane == 0) odeg[j] = c;
-    lmax = max(lmax, c);
-    rows += (unsigned long long)(rp[v + 1] - rp[v]);
+  for (int64_t c = w0; c < nch; c += nw) {
+    const int64_t j = chunk_row(coff, np, c);
+    const int v = oold[j];
+    const int64_t e0 = rp[v] + (c - coff[j]) * kRowChunk, e1 = min(rp[v + 1], e0 + kRowChunk);
+    int k = 0;
+    for (int64_t e = e0 + lane; e < e1; e += 32) k += (nid[ci[e]] > (int32_t)j) ? 1 : 0;
+    k = dev::warp_sum(k);
+    if (lane == 0) {
+      ccnt[c] = k;
+      if (k) atomicAdd(odeg + j, k);
+    }
+    rows += (unsigned long long)(e1 - e0);
   }
-  if (lane == 0) {
-    atomicMax(maxout, lmax);
-    if (rows) atomicAdd(scanned, rows);
-  }
+  if (lane == 0 && rows) atomicAdd(scanned, rows);
+}
+
+__global__ void maxout_kernel(const int64_t *__restrict__ d_np, const int32_t *__restrict__ odeg,
+                              int32_t *__restrict__ maxout) {
+  int m = 0;
+  const int64_t np = *d_np;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < np; j += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, odeg[j]);
+  m = dev::warp_max(m);
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(maxout, m);
 }
 
 struct PadF {
@@ -112,34 +161,38 @@ struct RowG {
   __device__ void operator()(int64_t j, int64_t excl, int64_t) const { orow[j] = excl; }
 };
 
-__global__ void fill_kernel(const int64_t *__restrict__ d_np, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                            const int32_t *__restrict__ oold, const int32_t *__restrict__ nid,
-                            const int64_t *__restrict__ orow, const int32_t *__restrict__ odeg,
-                            int32_t *__restrict__ ocol, int64_t total) {
+// the oriented rows, one warp per chunk: a chunk's kept entries go after
+// those of the row's earlier chunks (row order kept), and the row's last
+// chunk writes its padding
+__global__ void fill_chunk_kernel(const int64_t *__restrict__ d_np, const int64_t *__restrict__ coff,
+                                  const int64_t *__restrict__ cpos, const int64_t *__restrict__ rp,
+                                  const int32_t *__restrict__ ci, const int32_t *__restrict__ oold,
+                                  const int32_t *__restrict__ nid, const int64_t *__restrict__ orow,
+                                  const int32_t *__restrict__ odeg, int32_t *__restrict__ ocol) {
   const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const unsigned lt = (1u << lane) - 1u;
-  const int64_t np = *d_np;
-  for (int64_t j = w0; j < np; j += nw) {
-    int v = oold[j];
-    int64_t out = orow[j];
-    int64_t e1 = rp[v + 1];
-    int put = 0;
-    for (int64_t eb = rp[v]; eb < e1; eb += 32) {
-      int64_t e = eb + lane;
-      int y = (e < e1) ? nid[ci[e]] : -1;
-      bool k = y > (int32_t)j;
-      unsigned m = __ballot_sync(0xffffffffu, k);
-      if (k) ocol[out + put + __popc(m & lt)] = y;
-      put += __popc(m);
+  const int64_t np = *d_np, nch = coff[np];
+  for (int64_t c = w0; c < nch; c += nw) {
+    const int64_t j = chunk_row(coff, np, c);
+    const int v = oold[j];
+    const int64_t e0 = rp[v] + (c - coff[j]) * kRowChunk, e1 = min(rp[v + 1], e0 + kRowChunk);
+    int64_t out = orow[j] + (cpos[c] - cpos[coff[j]]);
+    for (int64_t eb = e0; eb < e1; eb += 32) {
+      const int64_t e = eb + lane;
+      const int y = (e < e1) ? nid[ci[e]] : -1;
+      const bool k = y > (int32_t)j;
+      const unsigned m = __ballot_sync(0xffffffffu, k);
+      if (k) ocol[out + __popc(m & lt)] = y;
+      out += __popc(m);
     }
-    int padded = (odeg[j] + 3) & ~3;
-    for (int t = put + lane; t < padded; t += 32) ocol[out + t] = -1;
+    if (c == coff[j + 1] - 1) {
+      const int padded = (odeg[j] + 3) & ~3;
+      for (int t = odeg[j] + lane; t < padded; t += 32) ocol[orow[j] + t] = -1;
+    }
   }
-  (void)total;
 }
-
 
 // root flags and classes
 struct RootInfo {
@@ -260,10 +313,26 @@ int launch_prune(mc_graph *g, int ordering, const float *scores, int32_t warp_ma
   int32_t *odeg = (int32_t *)p;
   int32_t *maxout = (int32_t *)(dsm + 2);
   const int blocks = (int)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)g->sm_count * 16);
-  outdeg_kernel<<<blocks, 256, 0, g->stream>>>(dsm + 0, g->row_ptr, g->col_idx, oold, nid, odeg, maxout,
-                                               (unsigned long long *)(dsm + 6));
-  g_launches++;
+  // chunks of the kept rows: offsets per row (coff[n'] = their count), kept
+  // entries per chunk, out-degrees as sums of those
+  const int64_t ncap = n + g->nnz / kRowChunk + 2;  // at least the chunk count
+  MC_TRY(ws_get(g, "pr.coff", (n + 1) * sizeof(int64_t), &p));
+  int64_t *coff = (int64_t *)p;
+  MC_TRY(ws_get(g, "pr.ccnt", ncap * sizeof(int32_t), &p));
+  int32_t *ccnt = (int32_t *)p;
+  MC_TRY(ws_get(g, "pr.cpos", ncap * sizeof(int64_t), &p));
+  int64_t *cpos = (int64_t *)p;
+  MC_CUDA_TRY(cudaMemsetAsync(odeg, 0, (n + 1) * sizeof(int32_t), g->stream));
+  MC_CUDA_TRY(cudaMemsetAsync(ccnt, 0, ncap * sizeof(int32_t), g->stream));
+  MC_TRY(device_scan(g, n + 1, ChunkF{g->row_ptr, dsm + 0, oold}, ChunkG{coff}, nullptr, "pr.scan"));
+  const int cblocks = (int)std::min<int64_t>((ncap * 32 + 255) / 256, (int64_t)g->sm_count * 16);
+  outdeg_chunk_kernel<<<cblocks, 256, 0, g->stream>>>(dsm + 0, coff, g->row_ptr, g->col_idx, oold, nid, ccnt, odeg,
+                                                      (unsigned long long *)(dsm + 6));
+  maxout_kernel<<<(int)std::min<int64_t>((n + 255) / 256, (int64_t)g->sm_count * 4), 256, 0, g->stream>>>(dsm + 0,
+                                                                                                     odeg, maxout);
+  g_launches += 2;
   MC_CUDA_TRY(cudaGetLastError());
+  MC_TRY(device_scan(g, ncap, CntF{ccnt}, PosG{cpos}, nullptr, "pr.scan"));
   MC_TRY(ws_get(g, "pr.orow", (n + 1) * sizeof(int64_t), &p));
   int64_t *orow = (int64_t *)p;
   // n + 1 entries: rows past n' (and the end offset orow[n]) get the total,
@@ -273,7 +342,8 @@ int launch_prune(mc_graph *g, int ordering, const float *scores, int32_t warp_ma
   const size_t arcs_cap = (size_t)(g->nnz / 2 + 4 * n + 4);
   MC_TRY(ws_get(g, "pr.ocol", arcs_cap * sizeof(int32_t), &p));
   int32_t *ocol = (int32_t *)p;
-  fill_kernel<<<blocks, 256, 0, g->stream>>>(dsm + 0, g->row_ptr, g->col_idx, oold, nid, orow, odeg, ocol, 0);
+  fill_chunk_kernel<<<cblocks, 256, 0, g->stream>>>(dsm + 0, coff, cpos, g->row_ptr, g->col_idx, oold, nid, orow,
+                                                    odeg, ocol);
   g_launches++;
   MC_CUDA_TRY(cudaGetLastError());
 
