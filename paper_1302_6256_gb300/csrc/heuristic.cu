@@ -27,7 +27,8 @@
 //
 // Launches: a warm-up launch grows the first 256 start vertices (the seeds
 // and the largest core numbers, whose candidate sets are whole neighbourhoods
-// before any clique is known) with one block each; the main launch runs 32
+// before any clique is known) with one 512-thread block each, two blocks per
+// SM so that all 256 run in one wave; the main launch runs 32
 // warps per SM with candidate buffers sharing 2 GiB; start vertices with more
 // candidates than a buffer holds go to a last launch with full-degree
 // buffers.  Every growth, by a block or a warp, yields the same clique.
@@ -265,7 +266,7 @@ __device__ __forceinline__ bool pick_vertex(const HA &a, int64_t i, int *v) {
   return true;
 }
 
-constexpr int kWT = 1024;      // threads of a warm-up block
+constexpr int kWT = 512;       // threads of a warm-up block (two per SM: all 256 starts in one wave)
 constexpr int kWW = kWT / 32;  // its warps
 
 // The greedy clique of grow() (same arguments, same result), grown by a whole
@@ -429,7 +430,7 @@ __device__ int grow_block(const HA &a, int v, int thr, int stop_at, int32_t *cur
 
 // Warm-up launch: one block per start vertex (the first positions of the
 // visiting order), so the maximum is high before the warp-per-vertex launch.
-__global__ void __launch_bounds__(kWT) heuristic_warm_kernel(HA a) {
+__global__ void __launch_bounds__(kWT, 2) heuristic_warm_kernel(HA a) {
   __shared__ int64_t s_i;
   __shared__ int s_x;
   int32_t *cur = a.cand + (int64_t)blockIdx.x * 2 * a.cand_stride;
@@ -572,7 +573,7 @@ int launch_heuristic(mc_graph *g, int mode, long long spin_limit, const int32_t 
   warps_b = (warps_b + 7) / 8 * 8;
   // warm-up blocks hold two full-degree candidate buffers each
   const int64_t warm_blocks =
-      std::max<int64_t>(1, std::min<int64_t>({(int64_t)g->sm_count, kWarm, budget / (2 * full)}));
+      std::max<int64_t>(1, std::min<int64_t>({(int64_t)g->sm_count * 2, kWarm, budget / (2 * full)}));
   const int64_t cand_entries =
       std::max({warps_s * cap_s, warm_blocks * 2 * full, two || mode == 1 ? warps_b * full : (int64_t)0});
   MC_TRY(ws_get(g, "he.cand", (size_t)cand_entries * 4, &p));
