@@ -90,9 +90,13 @@ struct ChunkF {  // chunks of kept row j
     return (rp[v + 1] - rp[v] + kRowChunk - 1) / kRowChunk;
   }
 };
-struct ChunkG {
+struct ChunkG {  // row offsets in chunk space, and each chunk's row
   int64_t *coff;
-  __device__ void operator()(int64_t j, int64_t excl, int64_t) const { coff[j] = excl; }
+  int32_t *crow;
+  __device__ void operator()(int64_t j, int64_t excl, int64_t val) const {
+    coff[j] = excl;
+    for (int64_t c = excl; c < excl + val; c++) crow[c] = (int32_t)j;
+  }
 };
 struct CntF {  // kept entries of chunk c
   const int32_t *ccnt;
@@ -103,20 +107,10 @@ struct PosG {
   __device__ void operator()(int64_t c, int64_t excl, int64_t) const { cpos[c] = excl; }
 };
 
-// row j of chunk c: the last j with coff[j] <= c (coff[np] = the chunk count)
-__device__ __forceinline__ int64_t chunk_row(const int64_t *coff, int64_t np, int64_t c) {
-  int64_t lo = 0, hi = np;  // coff[lo] <= c < coff[hi]
-  while (hi - lo > 1) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (coff[mid] <= c) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-
 // kept entries (later neighbours) per chunk, summed into the row's
 // out-degree; one warp per chunk
 __global__ void outdeg_chunk_kernel(const int64_t *__restrict__ d_np, const int64_t *__restrict__ coff,
-                                    const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                    const int32_t *__restrict__ crow, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                     const int32_t *__restrict__ oold, const int32_t *__restrict__ nid,
                                     int32_t *__restrict__ ccnt, int32_t *__restrict__ odeg,
                                     unsigned long long *__restrict__ scanned) {
@@ -126,7 +120,7 @@ __global__ void outdeg_chunk_kernel(const int64_t *__restrict__ d_np, const int6
   const int64_t np = *d_np, nch = coff[np];
   unsigned long long rows = 0;
   for (int64_t c = w0; c < nch; c += nw) {
-    const int64_t j = chunk_row(coff, np, c);
+    const int64_t j = crow[c];
     const int v = oold[j];
     const int64_t e0 = rp[v] + (c - coff[j]) * kRowChunk, e1 = min(rp[v + 1], e0 + kRowChunk);
     int k = 0;
@@ -165,7 +159,8 @@ struct RowG {
 // those of the row's earlier chunks (row order kept), and the row's last
 // chunk writes its padding
 __global__ void fill_chunk_kernel(const int64_t *__restrict__ d_np, const int64_t *__restrict__ coff,
-                                  const int64_t *__restrict__ cpos, const int64_t *__restrict__ rp,
+                                  const int32_t *__restrict__ crow, const int64_t *__restrict__ cpos,
+                                  const int64_t *__restrict__ rp,
                                   const int32_t *__restrict__ ci, const int32_t *__restrict__ oold,
                                   const int32_t *__restrict__ nid, const int64_t *__restrict__ orow,
                                   const int32_t *__restrict__ odeg, int32_t *__restrict__ ocol) {
@@ -175,7 +170,7 @@ __global__ void fill_chunk_kernel(const int64_t *__restrict__ d_np, const int64_
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t np = *d_np, nch = coff[np];
   for (int64_t c = w0; c < nch; c += nw) {
-    const int64_t j = chunk_row(coff, np, c);
+    const int64_t j = crow[c];
     const int v = oold[j];
     const int64_t e0 = rp[v] + (c - coff[j]) * kRowChunk, e1 = min(rp[v + 1], e0 + kRowChunk);
     int64_t out = orow[j] + (cpos[c] - cpos[coff[j]]);
@@ -320,13 +315,15 @@ int launch_prune(mc_graph *g, int ordering, const float *scores, int32_t warp_ma
   int64_t *coff = (int64_t *)p;
   MC_TRY(ws_get(g, "pr.ccnt", ncap * sizeof(int32_t), &p));
   int32_t *ccnt = (int32_t *)p;
+  MC_TRY(ws_get(g, "pr.crow", ncap * sizeof(int32_t), &p));
+  int32_t *crow = (int32_t *)p;
   MC_TRY(ws_get(g, "pr.cpos", ncap * sizeof(int64_t), &p));
   int64_t *cpos = (int64_t *)p;
   MC_CUDA_TRY(cudaMemsetAsync(odeg, 0, (n + 1) * sizeof(int32_t), g->stream));
   MC_CUDA_TRY(cudaMemsetAsync(ccnt, 0, ncap * sizeof(int32_t), g->stream));
-  MC_TRY(device_scan(g, n + 1, ChunkF{g->row_ptr, dsm + 0, oold}, ChunkG{coff}, nullptr, "pr.scan"));
+  MC_TRY(device_scan(g, n + 1, ChunkF{g->row_ptr, dsm + 0, oold}, ChunkG{coff, crow}, nullptr, "pr.scan"));
   const int cblocks = (int)std::min<int64_t>((ncap * 32 + 255) / 256, (int64_t)g->sm_count * 16);
-  outdeg_chunk_kernel<<<cblocks, 256, 0, g->stream>>>(dsm + 0, coff, g->row_ptr, g->col_idx, oold, nid, ccnt, odeg,
+  outdeg_chunk_kernel<<<cblocks, 256, 0, g->stream>>>(dsm + 0, coff, crow, g->row_ptr, g->col_idx, oold, nid, ccnt, odeg,
                                                       (unsigned long long *)(dsm + 6));
   maxout_kernel<<<(int)std::min<int64_t>((n + 255) / 256, (int64_t)g->sm_count * 4), 256, 0, g->stream>>>(dsm + 0,
                                                                                                      odeg, maxout);
@@ -342,8 +339,8 @@ int launch_prune(mc_graph *g, int ordering, const float *scores, int32_t warp_ma
   const size_t arcs_cap = (size_t)(g->nnz / 2 + 4 * n + 4);
   MC_TRY(ws_get(g, "pr.ocol", arcs_cap * sizeof(int32_t), &p));
   int32_t *ocol = (int32_t *)p;
-  fill_chunk_kernel<<<cblocks, 256, 0, g->stream>>>(dsm + 0, coff, cpos, g->row_ptr, g->col_idx, oold, nid, orow,
-                                                    odeg, ocol);
+  fill_chunk_kernel<<<cblocks, 256, 0, g->stream>>>(dsm + 0, coff, crow, cpos, g->row_ptr, g->col_idx, oold, nid,
+                                                    orow, odeg, ocol);
   g_launches++;
   MC_CUDA_TRY(cudaGetLastError());
 
