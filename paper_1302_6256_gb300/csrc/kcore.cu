@@ -19,9 +19,10 @@
 //           (peeled by that warp in the same phase, up to kDrainEdges edges)
 //           or as items of the next sub-round, until a sub-round appends
 //           nothing.
-// A vertex joins by claiming its core number (compare-and-swap from -1), so
-// one that a scan reads at degree k just after a decrement made it k joins
-// once.  The append order is a degeneracy order: when a vertex joins, every
+// In the scan phase a vertex joins by claiming its core number
+// (compare-and-swap from -1), so one that a scan reads at degree k just after
+// a decrement made it k joins once; in the sub-rounds only the decrement that
+// takes a degree from k + 1 to k finds a vertex, and a plain store does.  The append order is a degeneracy order: when a vertex joins, every
 // neighbour that joins later is still counted in its remaining degree, which
 // is at most k.  It becomes the search's vertex ranking.
 #include "mc_internal.cuh"
@@ -109,14 +110,20 @@ __global__ void degree_init_kernel(int64_t n, const int64_t *__restrict__ rp, in
 // while there is room, to be processed by this warp in the same sub-round;
 // the others become one work item per chunk of their row, processed in the
 // next sub-round.  All lanes call.
+template <bool CLAIM>
 __device__ __forceinline__ void append_frontier(bool nf, int u, int k, const int64_t *__restrict__ rp, int32_t *core,
                                                 int32_t *order, long long *wq, KcoreCtl *ctl, int *stk = nullptr,
                                                 int *sn = nullptr) {
   const int lane = threadIdx.x & 31;
   if (!__any_sync(0xffffffffu, nf)) return;
   // claim: a vertex found by a scan and by a decrement in the same phase
-  // joins once
-  if (nf) nf = atomicCAS(core + u, -1, k) == -1;
+  // joins once; after the scan only decrements find vertices, each exactly
+  // once (the one that takes its degree from k + 1 to k), so a store does
+  if (CLAIM) {
+    if (nf) nf = atomicCAS(core + u, -1, k) == -1;
+  } else if (nf) {
+    core[u] = k;
+  }
   const unsigned m = __ballot_sync(0xffffffffu, nf);
   if (!m) return;
   const unsigned lt = (1u << lane) - 1u;
@@ -179,6 +186,7 @@ __device__ __forceinline__ void push_items(bool has, int u, const int64_t *__res
 
 // Walk one row (b0, len) with the whole warp (coalesced), kPer edges per
 // lane in flight before the frontier appends.
+template <bool CLAIM>
 __device__ __forceinline__ void walk_row(int64_t b0, int len, int k, const int64_t *__restrict__ rp,
                                          const int32_t *__restrict__ ci, int32_t *deg, int32_t *core, int32_t *order,
                                          long long *wq, KcoreCtl *ctl, int *stk, int *sn) {
@@ -197,13 +205,14 @@ __device__ __forceinline__ void walk_row(int64_t b0, int len, int k, const int64
       if (u[q] >= 0 && __ldcg(deg + u[q]) > k) nf[q] = (atomicSub(deg + u[q], 1) == k + 1);
     }
 #pragma unroll
-    for (int q = 0; q < kPer; q++) append_frontier(nf[q], u[q], k, rp, core, order, wq, ctl, stk, sn);
+    for (int q = 0; q < kPer; q++) append_frontier<CLAIM>(nf[q], u[q], k, rp, core, order, wq, ctl, stk, sn);
   }
 }
 
 // Walk rows of at most 32 edges, one lane per row (b0, len; len 0 for idle
 // lanes), decrementing every neighbour whose degree is still above k; new
 // frontier vertices are appended (to the stack when one is given).
+template <bool CLAIM>
 __device__ __forceinline__ void walk_short_rows(int64_t b0, int len, int k, const int64_t *__restrict__ rp,
                                                 const int32_t *__restrict__ ci, int32_t *deg, int32_t *core,
                                                 int32_t *order, long long *wq, KcoreCtl *ctl, int *stk, int *sn) {
@@ -219,7 +228,7 @@ __device__ __forceinline__ void walk_short_rows(int64_t b0, int len, int k, cons
       if (u[q] >= 0 && __ldcg(deg + u[q]) > k) nf[q] = (atomicSub(deg + u[q], 1) == k + 1);
     }
 #pragma unroll
-    for (int q = 0; q < kPer; q++) append_frontier(nf[q], u[q], k, rp, core, order, wq, ctl, stk, sn);
+    for (int q = 0; q < kPer; q++) append_frontier<CLAIM>(nf[q], u[q], k, rp, core, order, wq, ctl, stk, sn);
   }
 }
 
@@ -227,6 +236,7 @@ __device__ __forceinline__ void walk_short_rows(int64_t b0, int len, int k, cons
 // (short rows one lane each, longer ones by the whole warp; their new
 // frontier vertices go back on the stack) until kDrainEdges edges are
 // walked; what is left becomes work items of the next sub-round.
+template <bool CLAIM>
 __device__ __forceinline__ void drain_stack(int k, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                             int32_t *deg, int32_t *core, int32_t *order, long long *wq, KcoreCtl *ctl,
                                             int *stk, int *sn) {
@@ -239,12 +249,12 @@ __device__ __forceinline__ void drain_stack(int k, const int64_t *__restrict__ r
     const int64_t b0 = u >= 0 ? rp[u] : 0;
     const int len = u >= 0 ? (int)(rp[u + 1] - b0) : 0;
     budget -= dev::warp_sum(len);
-    walk_short_rows(b0, len <= 32 ? len : 0, k, rp, ci, deg, core, order, wq, ctl, stk, sn);
+    walk_short_rows<CLAIM>(b0, len <= 32 ? len : 0, k, rp, ci, deg, core, order, wq, ctl, stk, sn);
     unsigned lm = __ballot_sync(0xffffffffu, len > 32);
     while (lm) {
       const int src = __ffs(lm) - 1;
       lm &= lm - 1;
-      walk_row(__shfl_sync(0xffffffffu, b0, src), __shfl_sync(0xffffffffu, len, src), k, rp, ci, deg, core, order, wq,
+      walk_row<CLAIM>(__shfl_sync(0xffffffffu, b0, src), __shfl_sync(0xffffffffu, len, src), k, rp, ci, deg, core, order, wq,
                ctl, stk, sn);
     }
   }
@@ -303,13 +313,13 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
         ob = __shfl_sync(0xffffffffu, ob, 0);
         if (keep) lout[ob + __popc(km & lt)] = v;
       }
-      append_frontier(d == k, v, k, rp, core, order, wq, ctl, stk, &sn0);
+      append_frontier<true>(d == k, v, k, rp, core, order, wq, ctl, stk, &sn0);
     }
     // the frontier a warp found (up to its stack) is peeled at once by that
     // warp, while others may still be scanning: a vertex they read at degree
     // k after a decrement here is claimed once; one kept at k + 1 and then
     // peeled here is dropped by the next scan, its degree being <= k
-    drain_stack(k, rp, ci, deg, core, order, wq, ctl, stk, &sn0);
+    drain_stack<true>(k, rp, ci, deg, core, order, wq, ctl, stk, &sn0);
     lmin = -dev::warp_max(-lmin);
     if (lane == 0 && lmin != INT_MAX) atomicMin(&bmin, lmin);
     __syncthreads();
@@ -352,7 +362,7 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
           b0 = rp[v] + (int64_t)c * kChunk;
           len = (int)(min(rp[v + 1], b0 + kChunk) - b0);
         }
-        walk_short_rows(b0, (valid && len < 32) ? len : 0, k, rp, ci, deg, core, order, wq, ctl, stk, &sn);
+        walk_short_rows<false>(b0, (valid && len < 32) ? len : 0, k, rp, ci, deg, core, order, wq, ctl, stk, &sn);
       }
       // pass B: longer chunks, one warp each (coalesced row reads)
       for (long long t = s0 + gwarp; t < e0; t += nwarps) {
@@ -361,9 +371,9 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
         const int64_t b0 = rp[v] + (int64_t)c * kChunk;
         const int len = (int)(min(rp[v + 1], b0 + kChunk) - b0);
         if (len < 32) continue;
-        walk_row(b0, len, k, rp, ci, deg, core, order, wq, ctl, stk, &sn);
+        walk_row<false>(b0, len, k, rp, ci, deg, core, order, wq, ctl, stk, &sn);
       }
-      drain_stack(k, rp, ci, deg, core, order, wq, ctl, stk, &sn);
+      drain_stack<false>(k, rp, ci, deg, core, order, wq, ctl, stk, &sn);
       long long e1 = 0;
       barrier_snap(ctl, nblocks, err, spin_limit, &otail_now, &e1, nullptr, nullptr);
       if (*(volatile int32_t *)err) return;

@@ -12,7 +12,10 @@
 //           and the candidates are filtered to that member's neighbours.  A
 //           stored clique stays valid while all its members are alive (the
 //           vertices that died were rejected candidates, whose removal
-//           changes no decision of the greedy scan).
+//           changes no decision of the greedy scan).  Warps check 32
+//           vertices at a time and grow the stale ones one after the other;
+//           vertices of more than 4,096 neighbours are grown by a whole
+//           block, one candidate slice per warp.
 //   scatter key(v) = |C(v)| << 32 | (2^31 - 1 - rank(v)); every member u of
 //           C(v) takes the largest key of the cliques holding it (atomicMax).
 //   accept  C(v) is accepted iff it holds the largest key at every member;

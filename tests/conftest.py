@@ -10,4 +10,4 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built CUDA library")
-    config.addinivalue_line("markers", "slow: long-running full-size test (also needs MC_FULL_SIZE=1 where it says so)")
+    config.addinivalue_line("markers", "slow: long-running full-size test (MC_SKIP_FULL_SIZE=1 skips the largest)")
