@@ -56,6 +56,7 @@ constexpr int kBigT = 1024;      // threads of the block sorter
 constexpr int kBG = 512;         // threads of the block grower
 constexpr int kBGW = kBG / 32;
 constexpr int64_t kBlockGrowMin = 4096;  // neighbours above which a block grows the clique
+constexpr int kTake = 4;                 // listed vertices a warp takes at a time
 
 struct OA {
   int64_t n;
@@ -67,7 +68,7 @@ struct OA {
   int32_t *arena;
   unsigned long long *bestkey;
   int64_t *ctl;  // [0] placed, [1] groups, [2] grows, [3] candidate tests, [4] rounds, [5] scan total,
-                 // [6] block grower's list length (unsigned)
+                 // [6] the block grower's list length and next entry, [7] the warps' (two unsigned each)
   int64_t *goff;
   int32_t *order;
   int64_t *gstart;
@@ -76,6 +77,8 @@ struct OA {
   int32_t *err;
   int32_t *big;     // vertices for the block grower this round
   unsigned *nbig;
+  int32_t *stale;   // vertices for the warps this round
+  unsigned *nstale, *take, *take_big;
 };
 
 struct CKey {
@@ -218,29 +221,48 @@ __device__ __forceinline__ bool needs_grow(const OA &a, int v) {
   return false;
 }
 
-// grow: warps take 32 vertices at a time (coalesced flags), find the alive
-// ones that need a clique, and grow them one after the other; vertices of
-// more than kBlockGrowMin neighbours go to the block kernel's list instead
-__global__ void __launch_bounds__(kOT) grow_kernel(OA a) {
+// check: a thread per vertex resets the alive vertices' keys and lists the
+// ones that need a clique (warp-aggregated appends): vertices of more than
+// kBlockGrowMin neighbours for the block grower, the rest for the warps
+__global__ void check_kernel(OA a) {
   const int lane = threadIdx.x & 31;
-  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  unsigned long long grows = 0, tests = 0;
-  for (int64_t base = gw * 32; base < a.n; base += nw * 32) {
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < a.n; base += stride) {
     const int64_t vv = base + lane;
-    bool need = false;
+    bool need = false, big = false;
     if (vv < a.n && a.alive[vv]) {
       a.bestkey[vv] = 0ull;
       need = needs_grow(a, (int)vv);
+      big = need && a.rp[vv + 1] - a.rp[vv] > kBlockGrowMin;
     }
-    unsigned m = __ballot_sync(FULL, need);
-    while (m) {
-      const int v = (int)base + __ffs(m) - 1;
-      m &= m - 1;
-      if (a.rp[v + 1] - a.rp[v] > kBlockGrowMin) {
-        if (lane == 0) a.big[atomicAdd(a.nbig, 1u)] = v;
-        continue;
-      }
+    const unsigned ms = __ballot_sync(FULL, need && !big), mb = __ballot_sync(FULL, big);
+    unsigned at_s = 0, at_b = 0;
+    if (lane == 0) {
+      if (ms) at_s = atomicAdd(a.nstale, (unsigned)__popc(ms));
+      if (mb) at_b = atomicAdd(a.nbig, (unsigned)__popc(mb));
+    }
+    at_s = __shfl_sync(FULL, at_s, 0);
+    at_b = __shfl_sync(FULL, at_b, 0);
+    if (need && !big) a.stale[at_s + __popc(ms & lt)] = (int32_t)vv;
+    if (big) a.big[at_b + __popc(mb & lt)] = (int32_t)vv;
+  }
+}
+
+// grow: each warp takes the next kTake listed vertices as it frees up, so a
+// few long growths (the dense core's, every round) do not hold back the rest
+__global__ void __launch_bounds__(kOT) grow_kernel(OA a) {
+  const int lane = threadIdx.x & 31;
+  const unsigned total = *a.nstale;
+  unsigned long long grows = 0, tests = 0;
+  for (;;) {
+    unsigned idx = 0;
+    if (lane == 0) idx = atomicAdd(a.take, (unsigned)kTake);
+    idx = __shfl_sync(FULL, idx, 0);
+    if (idx >= total) break;
+    const unsigned end = min(total, idx + (unsigned)kTake);
+    for (unsigned t = idx; t < end; t++) {
+      const int v = a.stale[t];
       const int size = warp_grow(a, v, tests);
       if (lane == 0) {
         a.csize[v] = size;
@@ -275,10 +297,17 @@ __global__ void __launch_bounds__(kBG) grow_big_kernel(OA a, int32_t *scratch, i
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   const CKey none{INT_MIN, INT_MIN, INT_MAX};
+  __shared__ unsigned s_b;
   const unsigned nbig = *a.nbig;
   int32_t *B = scratch + blockIdx.x * scratch_stride;
   unsigned long long grows = 0, tests = 0;
-  for (unsigned b = blockIdx.x; b < nbig; b += gridDim.x) {
+  for (;;) {
+    // the next listed vertex, taken as the block frees up
+    if (threadIdx.x == 0) s_b = atomicAdd(a.take_big, 1u);
+    __syncthreads();
+    const unsigned b = s_b;
+    __syncthreads();
+    if (b >= nbig) break;
     const int v = a.big[b];
     const int64_t e0 = a.rp[v], e1 = a.rp[v + 1];
     int32_t *A = a.arena + e0;
@@ -461,7 +490,10 @@ __global__ void advance_kernel(int64_t *ctl) {
   ctl[0] += t & 0xffffffffLL;
   ctl[1] += t >> 32;
   ctl[4] += 1;
-  *(unsigned *)(ctl + 6) = 0u;  // the block grower's list, empty for the next round
+  ((unsigned *)(ctl + 6))[0] = 0u;  // the growers' lists, empty for the next round
+  ((unsigned *)(ctl + 6))[1] = 0u;
+  ((unsigned *)(ctl + 7))[0] = 0u;
+  ((unsigned *)(ctl + 7))[1] = 0u;
 }
 
 // a caller's tie rank must be a permutation of [0, n): seen[] starts at 0
@@ -715,6 +747,11 @@ int clique_order(mc_graph *g, const int32_t *rank, int32_t *d_order, int64_t *d_
   MC_CUDA_TRY(cudaMemsetAsync(a.alive, 1, (size_t)n, g->stream));
   MC_CUDA_TRY(cudaMemsetAsync(a.csize, 0, (size_t)n * 4, g->stream));
   a.nbig = (unsigned *)(a.ctl + 6);
+  a.take_big = a.nbig + 1;
+  a.nstale = (unsigned *)(a.ctl + 7);
+  a.take = a.nstale + 1;
+  MC_TRY(ws_get(g, "co.stale", (size_t)n * 4, &p));
+  a.stale = (int32_t *)p;
   int32_t *scratch = nullptr;
   const int big_blocks = 2 * g->sm_count;
   const int64_t stride = std::max<int64_t>(g->max_degree, 1);
@@ -730,7 +767,9 @@ int clique_order(mc_graph *g, const int32_t *rank, int32_t *d_order, int64_t *d_
   int64_t placed = 0;
   for (int32_t r = 0;; r++) {
     a.round = r;
+    check_kernel<<<gt, 256, 0, g->stream>>>(a);
     grow_kernel<<<gw, kOT, 0, g->stream>>>(a);
+    g_launches++;
     if (any_big) {
       grow_big_kernel<<<big_blocks, kBG, 0, g->stream>>>(a, scratch, stride);
       g_launches++;
