@@ -761,13 +761,29 @@ __device__ __forceinline__ void load_P(const SA &a, int u, int om, int *Pidx, in
   const int64_t e0 = a.orow[u], e1 = a.orow[u + 1];
   const int4 *row = reinterpret_cast<const int4 *>(a.ocol + e0);
   const int64_t nq = (e1 - e0) >> 2;
-  for (int64_t q = t; q < nq; q += nthr) {
-    int4 y = __ldg(row + q);
-    int ys[4] = {y.x, y.y, y.z, y.w};
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  // whole warps step together (t - lane is the warp's first index), so the
+  // members a warp finds take one shared atomic per ballot
+  for (int64_t q0 = t - lane; q0 < nq; q0 += nthr) {
+    const int64_t q = q0 + lane;
+    int ys[4] = {-1, -1, -1, -1};
+    if (q < nq) {
+      const int4 y = __ldg(row + q);
+      ys[0] = y.x;
+      ys[1] = y.y;
+      ys[2] = y.z;
+      ys[3] = y.w;
+    }
 #pragma unroll
     for (int j = 0; j < 4; j++) {
-      if (ys[j] >= 0 && __ldg(a.ocore + ys[j]) >= om) {
-        int p = atomicAdd(cnt, 1);
+      const bool keep = ys[j] >= 0 && __ldg(a.ocore + ys[j]) >= om;
+      const unsigned m = __ballot_sync(FULL, keep);
+      int base = 0;
+      if (lane == 0 && m) base = atomicAdd(cnt, __popc(m));
+      base = __shfl_sync(FULL, base, 0);
+      if (keep) {
+        const int p = base + __popc(m & lt);
         if (p < cap) Pidx[p] = ys[j];
       }
     }
@@ -837,6 +853,22 @@ __device__ __forceinline__ void build_rows(const SA &a, const int *Pidx, int p, 
   if (lane == 0 && scanned) atomicAdd(count, scanned);
 }
 
+// 32 x 32 bit transpose across a warp: lane r holds row r (bit c = column
+// c); returns row c of the transpose for lane c (bit r = row r's bit c).
+// Five exchange stages swap ever smaller off-diagonal blocks: in the stage
+// of width j, the lane with bit j clear trades its upper j-bit halves for its
+// partner's lower ones.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x) {
+  const int lane = threadIdx.x & 31;
+  uint32_t m = 0x0000ffffu;
+#pragma unroll
+  for (int j = 16; j != 0; j >>= 1, m ^= (m << j)) {
+    const uint32_t y = __shfl_xor_sync(FULL, x, j);
+    x = (lane & j) ? (((y >> j) & m) | (x & ~m)) : ((x & m) | ((y & m) << j));
+  }
+  return x;
+}
+
 // Complete the adjacency matrix from its lower triangle.  build_rows sets
 // bit (i, b) for every edge of G[P] with b < i (a later neighbour has a
 // higher rank, hence a smaller index in P); the 32 x 32 tiles on and below
@@ -855,12 +887,7 @@ __device__ void symmetrize(uint32_t *A, int Ws, int W, int p, int wid, int nw) {
     const int J = t - I * (I + 1) / 2;
     const int r = 32 * I + lane;
     const uint32_t x = (r < p) ? rw<SM>(A, (int64_t)r * Ws + J) : 0u;
-    uint32_t col = 0;
-#pragma unroll
-    for (int c = 0; c < 32; c++) {
-      const uint32_t m = __ballot_sync(FULL, (x >> c) & 1u);
-      if (lane == c) col = m;
-    }
+    const uint32_t col = transpose32(x);
     const int rt = 32 * J + lane;
     if (rt < p) {
       const int64_t at = (int64_t)rt * Ws + I;
