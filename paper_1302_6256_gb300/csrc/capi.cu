@@ -137,19 +137,8 @@ __global__ void trivial_kernel(int32_t count, const int64_t *voff, int64_t n, in
 static void free_graph(mc_graph *g) {
   if (!g) return;
   if (g->stream) cudaStreamSynchronize(g->stream);
-  if (!g->borrowed) {
-    cudaFree(g->row_ptr);
-    cudaFree(g->col_idx);
-  }
-  cudaFree(g->voff);
-  cudaFree(g->gid);
-  cudaFree(g->core);
-  cudaFree(g->order);
-  cudaFree(g->pos);
-  cudaFree(g->best);
-  cudaFree(g->lock);
-  cudaFree(g->wit);
-  cudaFree(g->err);
+  // the graph's own arrays are named workspace buffers too (the CSR copy,
+  // per-vertex arrays, incumbents): all go back to the pool below
   if (g->graph_exec) cudaGraphExecDestroy(g->graph_exec);
   if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
   for (auto &kv : g->ws)
@@ -198,14 +187,21 @@ static int load_common(int32_t count, const int64_t *voff_in, int64_t n, const i
   }
   if (nnz < 0 || (nnz > 0 && !col_idx)) return fail(MC_ERR_ARG);
   g->nnz = nnz;
+  // device arrays come from the per-device pool (as named workspace
+  // buffers), so a handle loaded after another one was freed reuses its
+  // memory instead of allocating
+  void *wp = nullptr;
+  auto take = [&](const char *name, size_t bytes) -> void * {
+    return ws_get(g, name, bytes, &wp) == MC_OK ? wp : nullptr;
+  };
   if (flags & MC_BORROW) {
     if ((n > 0 && !is_device_ptr(row_ptr)) || (nnz > 0 && !is_device_ptr(col_idx))) return fail(MC_ERR_ARG);
     g->row_ptr = const_cast<int64_t *>(row_ptr);
     g->col_idx = const_cast<int32_t *>(col_idx);
     g->borrowed = true;
   } else {
-    if (cudaMalloc(&g->row_ptr, (n + 1) * sizeof(int64_t)) != cudaSuccess) return fail(MC_ERR_OOM);
-    if (cudaMalloc(&g->col_idx, std::max<int64_t>(nnz, 4) * sizeof(int32_t)) != cudaSuccess)
+    if (!(g->row_ptr = (int64_t *)take("g.row_ptr", (n + 1) * sizeof(int64_t)))) return fail(MC_ERR_OOM);
+    if (!(g->col_idx = (int32_t *)take("g.col_idx", std::max<int64_t>(nnz, 4) * sizeof(int32_t))))
       return fail(MC_ERR_OOM);
     if (n > 0) {
       if ((rc = copy_in(g->row_ptr, row_ptr, (n + 1) * sizeof(int64_t), g->stream)) != MC_OK) return fail(rc);
@@ -215,10 +211,10 @@ static int load_common(int32_t count, const int64_t *voff_in, int64_t n, const i
     }
   }
   const size_t nv = (size_t)std::max<int64_t>(n, 1);
-  if (cudaMalloc(&g->core, nv * 4) != cudaSuccess || cudaMalloc(&g->order, nv * 4) != cudaSuccess ||
-      cudaMalloc(&g->pos, nv * 4) != cudaSuccess || cudaMalloc(&g->wit, (nv + 1) * 4) != cudaSuccess ||
-      cudaMalloc(&g->best, count * 4) != cudaSuccess || cudaMalloc(&g->lock, count * 4) != cudaSuccess ||
-      cudaMalloc(&g->err, 64) != cudaSuccess || cudaMalloc(&g->voff, (count + 1) * 8) != cudaSuccess)
+  if (!(g->core = (int32_t *)take("g.core", nv * 4)) || !(g->order = (int32_t *)take("g.order", nv * 4)) ||
+      !(g->pos = (int32_t *)take("g.pos", nv * 4)) || !(g->wit = (int32_t *)take("g.wit", (nv + 1) * 4)) ||
+      !(g->best = (int32_t *)take("g.best", count * 4)) || !(g->lock = (int32_t *)take("g.lock", count * 4)) ||
+      !(g->err = (int32_t *)take("g.err", 64)) || !(g->voff = (int64_t *)take("g.voff", (count + 1) * 8)))
     return fail(MC_ERR_OOM);
   cudaMemsetAsync(g->err, 0, 64, g->stream);
   cudaMemsetAsync(g->lock, 0, count * 4, g->stream);
@@ -241,7 +237,7 @@ static int load_common(int32_t count, const int64_t *voff_in, int64_t n, const i
   if (cudaMemcpyAsync(g->voff, g->h_voff, (count + 1) * 8, cudaMemcpyHostToDevice, g->stream) != cudaSuccess)
     return fail(MC_ERR_CUDA);
   if (count > 1) {
-    if (cudaMalloc(&g->gid, nv * 4) != cudaSuccess) return fail(MC_ERR_OOM);
+    if (!(g->gid = (int32_t *)take("g.gid", nv * 4))) return fail(MC_ERR_OOM);
     if ((rc = launch_gid(g)) != MC_OK) return fail(rc);
   }
   if (flags & MC_VALIDATE) {
