@@ -42,6 +42,7 @@ constexpr int kPer = 4;      // edges per lane in flight
 constexpr int kLocal = 256;     // warp stack entries: rows a warp peels in the same phase
 constexpr int kLocalRow = 128;  // rows of at most this many edges may go onto the stack
 constexpr int kDrainEdges = 4096;  // edges a warp takes from its stack per phase (then it spills)
+constexpr int64_t kScanLocalLive = (int64_t)1 << 21;  // live vertices up to which the scan peels locally
 
 struct KcoreCtl {
   unsigned bar_count, bar_gen;
@@ -297,6 +298,7 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
     __syncthreads();
     int lmin = INT_MAX, sn0 = 0;
     int *lout_n = &ctl->live_n[level & 1];
+    const bool scan_local = live_count <= kScanLocalLive;  // the same in every block
     for (int64_t base = gwarp * 32; base < live_count; base += nwarps * 32) {
       int64_t i = base + lane;
       int v = -1, d = INT_MIN;
@@ -313,13 +315,19 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
         ob = __shfl_sync(0xffffffffu, ob, 0);
         if (keep) lout[ob + __popc(km & lt)] = v;
       }
-      append_frontier<true>(d == k, v, k, rp, core, order, wq, ctl, stk, &sn0);
+      if (scan_local)
+        append_frontier<true>(d == k, v, k, rp, core, order, wq, ctl, stk, &sn0);
+      else
+        append_frontier<false>(d == k, v, k, rp, core, order, wq, ctl);
     }
     // the frontier a warp found (up to its stack) is peeled at once by that
     // warp, while others may still be scanning: a vertex they read at degree
     // k after a decrement here is claimed once; one kept at k + 1 and then
-    // peeled here is dropped by the next scan, its degree being <= k
-    drain_stack<true>(k, rp, ci, deg, core, order, wq, ctl, stk, &sn0);
+    // peeled here is dropped by the next scan, its degree being <= k.  Above
+    // kScanLocalLive live vertices the frontier is large enough to keep every
+    // warp busy in the sub-rounds: the scan only lists it (no decrement runs
+    // during the scan, so each vertex joins once without a claim)
+    if (scan_local) drain_stack<true>(k, rp, ci, deg, core, order, wq, ctl, stk, &sn0);
     lmin = -dev::warp_max(-lmin);
     if (lane == 0 && lmin != INT_MAX) atomicMin(&bmin, lmin);
     __syncthreads();
