@@ -63,6 +63,36 @@ def test_clique_order_bit_exact(mc, g):
     h.close()
 
 
+def _hub_graph(n=5200, seed=11):
+    """A hub adjacent to every other vertex (degree n - 1 > 4,096, so its
+    clique is grown by the block grower) over a sparse random graph with a
+    planted clique of 12."""
+    rng = np.random.default_rng(seed)
+    src = [np.zeros(n - 1, np.int64)]
+    dst = [np.arange(1, n)]
+    m = 3 * n
+    a, b = rng.integers(1, n, m), rng.integers(1, n, m)
+    keep = a != b
+    src.append(a[keep])
+    dst.append(b[keep])
+    S = rng.choice(np.arange(1, n), 12, replace=False)
+    for i in range(12):
+        for j in range(i + 1, 12):
+            src.append(np.array([S[i]]))
+            dst.append(np.array([S[j]]))
+    return gg.from_edges(n, np.concatenate(src), np.concatenate(dst), name="hub%d" % n)
+
+
+def test_clique_order_hub_beyond_4096_bit_exact(mc):
+    g = _hub_graph()
+    assert int(np.diff(g.row_ptr).max()) > 4096
+    want = OO.clique_order(g, oracle.core_numbers(g))
+    h = load(mc, g)
+    order, starts, rounds, _ = mc.mc_clique_order(h)
+    assert np.array_equal(order, want[0]) and np.array_equal(starts, want[1]) and np.array_equal(rounds, want[2])
+    h.close()
+
+
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_clique_order_with_rank_bit_exact(mc, seed):
     g = [gg.path(64), gg.rmat(10, 8, planted=10, seed=9), gg.chung_lu(3000, 2.4, 8.0, 200.0, planted=9, seed=4)][seed]
