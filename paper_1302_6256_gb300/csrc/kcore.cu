@@ -40,8 +40,8 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kChunk = 128;  // edges per work item
 constexpr int kPer = 4;      // edges per lane in flight
 constexpr int kLocal = 256;     // warp stack entries: rows a warp peels in the same phase
-constexpr int kLocalRow = 128;  // rows of at most this many edges may go onto the stack
-constexpr int kDrainEdges = 4096;  // edges a warp takes from its stack per phase (then it spills)
+constexpr int kLocalRow = 512;  // rows of at most this many edges may go onto the stack
+constexpr int kDrainEdges = 8192;  // edges a warp takes from its stack per phase (then it spills)
 constexpr int64_t kScanLocalLive = (int64_t)1 << 21;  // live vertices up to which the scan peels locally
 
 struct KcoreCtl {
