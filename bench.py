@@ -235,20 +235,28 @@ def host_info():
     return {"nproc": os.cpu_count(), "cpu_model": model}
 
 
-def oracle_sample(seconds_min: float = 10.0, max_runs: int = 5):
-    """The CPU oracle as it stands on the bounded sample (same generator)."""
+def oracle_threads() -> int:
+    """The host cores the CPU baseline uses: all of them (at most 64)."""
+    return max(1, min(64, os.cpu_count() or 1))
+
+
+def oracle_sample(seconds_min: float = 10.0, max_runs: int = 50):
+    """The CPU oracle as it stands (its search with one worker per host core
+    sharing the incumbent, Section 4.5) on the bounded sample (same
+    generator)."""
     import oracle
     import graphgen as gg
     g = gg.rmat(SAMPLE_SCALE, 16, 0.57, 0.19, 0.19, planted=40, seed=2)
+    th = oracle_threads()
     runs, tot = 0, 0.0
     while runs < max_runs and (tot < seconds_min or runs == 0):
         t = time.perf_counter()
-        om, wit, st = oracle.max_clique(g)
+        om, wit, st = oracle.max_clique_threads(g, th)
         tot += time.perf_counter() - t
         runs += 1
-    return {"value": g.m * runs / tot, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
-            "sample": "oracle (single thread) on R-MAT scale %d ef 16 (0.57,0.19,0.19) planted 40 seed 2 "
-                      "(n=%d, m=%d, omega=%d), %d run(s), %.1f s" % (SAMPLE_SCALE, g.n, g.m, om, runs, tot)}
+    return {"value": g.m * runs / tot, "unit": UNIT, "cores": th, "kind": "oracle", "host": host_info(),
+            "sample": "oracle (%d threads) on R-MAT scale %d ef 16 (0.57,0.19,0.19) planted 40 seed 2 "
+                      "(n=%d, m=%d, omega=%d), %d run(s), %.1f s" % (th, SAMPLE_SCALE, g.n, g.m, om, runs, tot)}
 
 
 def run_reference(args):
@@ -259,23 +267,24 @@ def run_reference(args):
     import graphgen as gg
     from graphgen import workloads as W
     g = gg.rmat(SAMPLE_SCALE, 16, 0.57, 0.19, 0.19, planted=40, seed=2)
+    th = oracle_threads()
     for _ in range(args.warmup):
-        oracle.max_clique(g)
+        oracle.max_clique_threads(g, th)
     t = time.perf_counter()
     for _ in range(args.steps):
-        om, _, _ = oracle.max_clique(g)
+        om, _, _ = oracle.max_clique_threads(g, th)
     dt = time.perf_counter() - t
     value = g.m * args.steps / dt
-    sample = ("oracle (single thread, as it stands) on R-MAT scale %d ef 16 (0.57,0.19,0.19) planted 40 seed 2 "
-              "(n=%d, m=%d, omega=%d), one solve per step" % (SAMPLE_SCALE, g.n, g.m, om))
+    sample = ("oracle (as it stands, %d threads sharing the incumbent) on R-MAT scale %d ef 16 (0.57,0.19,0.19) "
+              "planted 40 seed 2 (n=%d, m=%d, omega=%d), one solve per step" % (th, SAMPLE_SCALE, g.n, g.m, om))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": W.RMAT_S22,
                    "sample": "each step: the oracle on R-MAT scale %d from the same generator (n=%d, m=%d); "
-                             "the scale-22 solve takes the oracle 6,161 s" % (SAMPLE_SCALE, g.n, g.m)},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "the scale-22 solve takes the single-thread oracle 6,161 s" % (SAMPLE_SCALE, g.n, g.m)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": th, "kind": "oracle", "sample": sample,
                          "host": host_info()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)

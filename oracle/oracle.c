@@ -712,6 +712,11 @@ static void th_branch(th_worker *w, int32_t csize, int32_t *idx, int32_t *colors
   free(pidx); free(pcol); free(scr);
 }
 
+static int cmp_knkey_id(const void *x, const void *y) {
+  const knkey *a = (const knkey *)x, *b = (const knkey *)y;
+  return (a->id > b->id) - (a->id < b->id);
+}
+
 /* the search rooted at u (new id): cliques whose lowest-ranked member is u */
 static void th_root(th_worker *w, int32_t u, int32_t *kn, uint8_t *in, int32_t *idx, int32_t *col, int32_t *scr,
                     knkey *ord, int32_t *nat, int32_t *ncol) {
@@ -752,11 +757,13 @@ static void th_root(th_worker *w, int32_t u, int32_t *kn, uint8_t *in, int32_t *
   for (int32_t j = 0; j < cnt; j++) idx[j] = ord[j].i;
   int32_t L = th_color_list(w, idx, cnt, col, scr);
   if (1 + L <= th_best(w)) return;
-  /* Branch({u}, kept) with the kept vertices in natural (rank) order */
-  for (int32_t a = 0; a < np; a++) in[a] = 0;
-  for (int32_t j = 0; j < cnt; j++) { in[idx[j]] = 1; kn[idx[j]] = col[j]; }
+  /* Branch({u}, kept) with the kept vertices in natural order: increasing
+   * original vertex id, as in orc_max_clique (the recolouring order of
+   * Branch is free; ascending rank, the peel order, colours worst) */
+  for (int32_t j = 0; j < cnt; j++) { ord[j].i = idx[j]; ord[j].kn = col[j]; ord[j].id = sh->orig[w->P[idx[j]]]; }
+  qsort(ord, (size_t)cnt, sizeof(knkey), cmp_knkey_id);
   int32_t c = 0;
-  for (int32_t a = 0; a < np; a++) if (in[a]) { nat[c] = a; ncol[c] = kn[a]; c++; }
+  for (int32_t j = 0; j < cnt; j++) { nat[c] = ord[j].i; ncol[c] = ord[j].kn; c++; }
   w->C[0] = u;
   th_branch(w, 1, nat, ncol, c);
 }
