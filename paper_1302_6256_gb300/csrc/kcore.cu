@@ -6,25 +6,29 @@
 //   scan    every live vertex with remaining degree == k joins the level-k
 //           frontier; vertices of larger degree are compacted into the next
 //           live list, so later scans only touch what is left; if nothing
-//           joins, k jumps to the smallest remaining degree.  Each warp peels
-//           the frontier it found right after its scan: rows of at most
-//           kLocalRow edges from a warp stack in shared memory (short rows one
-//           lane each, longer ones by the whole warp), everything else as work
-//           items, one per 128-edge chunk;
+//           joins, k jumps to the smallest remaining degree.  A warp reads
+//           kScanSlices slices of 32 live entries at once (one atomic for
+//           their place in the next list).  Up to kScanLocalLive live
+//           vertices, each block peels the frontier its warps found right
+//           after its scan, from lists in shared memory that all its warps
+//           share: rows of at most 32 edges one lane each, rows of up to
+//           kLocalRow edges one warp each, the cascade they start as further
+//           generations of the same lists, up to kBlockDrainEdges edges;
+//           everything else becomes work items, one per 128-edge chunk;
 //   process after a grid barrier, the work items appended so far are split
 //           statically over all warps (rows under 32 edges one lane per
 //           item, longer chunks one warp per item, coalesced); every
 //           neighbour whose degree is still above k is decremented, and one
-//           whose degree falls to k joins the frontier: onto the warp's stack
-//           (peeled by that warp in the same phase, up to kDrainEdges edges)
-//           or as items of the next sub-round, until a sub-round appends
-//           nothing.
+//           whose degree falls to k joins the frontier: onto its block's
+//           lists (walked by that block in the same phase) or as items of the
+//           next sub-round, until a sub-round appends nothing.
 // In the scan phase a vertex joins by claiming its core number
 // (compare-and-swap from -1), so one that a scan reads at degree k just after
 // a decrement made it k joins once; in the sub-rounds only the decrement that
-// takes a degree from k + 1 to k finds a vertex, and a plain store does.  The append order is a degeneracy order: when a vertex joins, every
-// neighbour that joins later is still counted in its remaining degree, which
-// is at most k.  It becomes the search's vertex ranking.
+// takes a degree from k + 1 to k finds a vertex, and a plain store does.  The
+// append order is a degeneracy order: when a vertex joins, every neighbour
+// that joins later is still counted in its remaining degree, which is at most
+// k.  It becomes the search's vertex ranking.
 #include "mc_internal.cuh"
 
 #include <algorithm>
@@ -39,10 +43,13 @@ constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
 constexpr int kChunk = 128;  // edges per work item
 constexpr int kPer = 4;      // edges per lane in flight
-constexpr int kLocal = 256;     // warp stack entries: rows a warp peels in the same phase
-constexpr int kLocalRow = 512;  // rows of at most this many edges may go onto the stack
-constexpr int kDrainEdges = 8192;  // edges a warp takes from its stack per phase (then it spills)
+constexpr int kLocalRow = 512;  // rows of at most this many edges may go onto the block lists
+constexpr int kPoolShort = 4096;  // block list of rows of 1..32 edges (one lane per row)
+constexpr int kPoolLong = 2048;   // block list of rows of 33..kLocalRow edges (one warp per row)
+constexpr long long kBlockDrainEdges = 65536;  // edges a block walks from its lists per phase (then it spills)
 constexpr int64_t kScanLocalLive = (int64_t)1 << 21;  // live vertices up to which the scan peels locally
+constexpr int kScanSlices = 4;  // slices of 32 live entries a warp's scan reads at once
+constexpr int64_t kNoCheckMaxN = (int64_t)1 << 23;  // degree arrays up to 32 MB stay in L2: sub-rounds decrement unread
 
 struct KcoreCtl {
   unsigned bar_count, bar_gen;
@@ -105,16 +112,30 @@ __global__ void degree_init_kernel(int64_t n, const int64_t *__restrict__ rp, in
   if ((threadIdx.x & 31) == 0) atomicMax(maxdeg, local);
 }
 
+// The rows a block peels within one phase: two generations of two lists
+// (rows of 1..32 edges, walked one lane per row; rows of 33..kLocalRow
+// edges, walked by one warp each).  The new frontier found while one
+// generation is walked goes to the other, so the block's 32 warps share its
+// cascade.  A counter may run past its list's capacity: the entries beyond
+// it were not stored (those rows became work items instead).
+struct BlockPool {
+  int s[2][kPoolShort];
+  int l[2][kPoolLong];
+  int ns[2], nl[2];
+  long long edges;  // edges walked from the lists in this phase
+  int fscan[kWarps][32 * kScanSlices];  // a warp's scanned frontier, compacted
+};
+
 // Append the lanes' new frontier vertices (flag nf, vertex u): core and
-// peel order; then their rows' work.  With a warp stack (stk, *sn: entries
-// used, the same in every lane), vertices of 1..kLocalRow edges go onto it
-// while there is room, to be processed by this warp in the same sub-round;
-// the others become one work item per chunk of their row, processed in the
-// next sub-round.  All lanes call.
+// peel order; then their rows' work.  With a block pool (bp, generation
+// gen), rows of 1..kLocalRow edges go onto its lists while there is room,
+// to be walked by this block in the same phase; the others become one work
+// item per chunk of their row, walked in the next sub-round.  All lanes
+// call.
 template <bool CLAIM>
 __device__ __forceinline__ void append_frontier(bool nf, int u, int k, const int64_t *__restrict__ rp, int32_t *core,
-                                                int32_t *order, long long *wq, KcoreCtl *ctl, int *stk = nullptr,
-                                                int *sn = nullptr) {
+                                                int32_t *order, long long *wq, KcoreCtl *ctl,
+                                                BlockPool *bp = nullptr, int gen = 0) {
   const int lane = threadIdx.x & 31;
   if (!__any_sync(0xffffffffu, nf)) return;
   // claim: a vertex found by a scan and by a decrement in the same phase
@@ -131,14 +152,31 @@ __device__ __forceinline__ void append_frontier(bool nf, int u, int k, const int
   int64_t d = 0;
   if (nf) d = rp[u + 1] - rp[u];
   bool put = false;
-  if (stk) {
-    const bool loc = nf && d > 0 && d <= kLocalRow;
-    const unsigned lm = __ballot_sync(0xffffffffu, loc);
-    const int room = kLocal - *sn;
-    const int at = __popc(lm & lt);
-    put = loc && at < room;
-    if (put) stk[*sn + at] = u;
-    *sn += min(__popc(lm), room);
+  if (bp) {
+    const bool sh = nf && d > 0 && d <= 32;
+    const bool lg = nf && d > 32 && d <= kLocalRow;
+    const unsigned ms = __ballot_sync(0xffffffffu, sh), ml = __ballot_sync(0xffffffffu, lg);
+    int bs = 0, bl = 0;
+    if (lane == 0) {
+      if (ms) bs = atomicAdd(&bp->ns[gen], __popc(ms));
+      if (ml) bl = atomicAdd(&bp->nl[gen], __popc(ml));
+    }
+    bs = __shfl_sync(0xffffffffu, bs, 0);
+    bl = __shfl_sync(0xffffffffu, bl, 0);
+    if (sh) {
+      const int at = bs + __popc(ms & lt);
+      if (at < kPoolShort) {
+        bp->s[gen][at] = u;
+        put = true;
+      }
+    }
+    if (lg) {
+      const int at = bl + __popc(ml & lt);
+      if (at < kPoolLong) {
+        bp->l[gen][at] = u;
+        put = true;
+      }
+    }
   }
   const int nch = (nf && !put) ? (int)((d + kChunk - 1) / kChunk) : 0;
   int incl = nch;
@@ -165,7 +203,7 @@ __device__ __forceinline__ void append_frontier(bool nf, int u, int k, const int
 }
 
 // Work items (one per chunk) for lanes' vertices already in the peel order:
-// what is left on a warp stack at the end of its local budget.
+// what is left on a block's lists at the end of its budget.
 __device__ __forceinline__ void push_items(bool has, int u, const int64_t *__restrict__ rp, long long *wq,
                                            KcoreCtl *ctl) {
   const int lane = threadIdx.x & 31;
@@ -185,12 +223,24 @@ __device__ __forceinline__ void push_items(bool has, int u, const int64_t *__res
   for (int c = 0; c < nch; c++) wq[at + c] = ((long long)u << 32) | (unsigned)c;
 }
 
+// One decrement of neighbour u at level k; true when it takes u's degree
+// from k + 1 to k.  With chk the degree is read first and only a degree
+// above k is decremented: while a scan may still read the degrees, a vertex
+// at exactly k must stay at k for it.  Without chk (sub-rounds, where every
+// vertex at k or below is already peeled and its degree no longer read) the
+// read is skipped and a peeled neighbour's degree just goes lower.
+__device__ __forceinline__ bool decrement(int32_t *deg, int u, int k, bool chk) {
+  if (u < 0) return false;
+  if (chk && __ldcg(deg + u) <= k) return false;
+  return atomicSub(deg + u, 1) == k + 1;
+}
+
 // Walk one row (b0, len) with the whole warp (coalesced), kPer edges per
 // lane in flight before the frontier appends.
 template <bool CLAIM>
-__device__ __forceinline__ void walk_row(int64_t b0, int len, int k, const int64_t *__restrict__ rp,
+__device__ __forceinline__ void walk_row(int64_t b0, int len, int k, bool chk, const int64_t *__restrict__ rp,
                                          const int32_t *__restrict__ ci, int32_t *deg, int32_t *core, int32_t *order,
-                                         long long *wq, KcoreCtl *ctl, int *stk, int *sn) {
+                                         long long *wq, KcoreCtl *ctl, BlockPool *bp, int gen) {
   const int lane = threadIdx.x & 31;
   for (int eb = 0; eb < len; eb += 32 * kPer) {
     int u[kPer];
@@ -201,22 +251,20 @@ __device__ __forceinline__ void walk_row(int64_t b0, int len, int k, const int64
       u[q] = e < len ? ci[b0 + e] : -1;
     }
 #pragma unroll
-    for (int q = 0; q < kPer; q++) {
-      nf[q] = false;
-      if (u[q] >= 0 && __ldcg(deg + u[q]) > k) nf[q] = (atomicSub(deg + u[q], 1) == k + 1);
-    }
+    for (int q = 0; q < kPer; q++) nf[q] = decrement(deg, u[q], k, chk);
 #pragma unroll
-    for (int q = 0; q < kPer; q++) append_frontier<CLAIM>(nf[q], u[q], k, rp, core, order, wq, ctl, stk, sn);
+    for (int q = 0; q < kPer; q++) append_frontier<CLAIM>(nf[q], u[q], k, rp, core, order, wq, ctl, bp, gen);
   }
 }
 
 // Walk rows of at most 32 edges, one lane per row (b0, len; len 0 for idle
 // lanes), decrementing every neighbour whose degree is still above k; new
-// frontier vertices are appended (to the stack when one is given).
+// frontier vertices are appended (to the block's lists when given).
 template <bool CLAIM>
-__device__ __forceinline__ void walk_short_rows(int64_t b0, int len, int k, const int64_t *__restrict__ rp,
+__device__ __forceinline__ void walk_short_rows(int64_t b0, int len, int k, bool chk, const int64_t *__restrict__ rp,
                                                 const int32_t *__restrict__ ci, int32_t *deg, int32_t *core,
-                                                int32_t *order, long long *wq, KcoreCtl *ctl, int *stk, int *sn) {
+                                                int32_t *order, long long *wq, KcoreCtl *ctl, BlockPool *bp,
+                                                int gen) {
   const int maxlen = dev::warp_max(len);
   for (int j0 = 0; j0 < maxlen; j0 += kPer) {
     int u[kPer];
@@ -224,69 +272,99 @@ __device__ __forceinline__ void walk_short_rows(int64_t b0, int len, int k, cons
 #pragma unroll
     for (int q = 0; q < kPer; q++) u[q] = (j0 + q < len) ? ci[b0 + j0 + q] : -1;
 #pragma unroll
-    for (int q = 0; q < kPer; q++) {
-      nf[q] = false;
-      if (u[q] >= 0 && __ldcg(deg + u[q]) > k) nf[q] = (atomicSub(deg + u[q], 1) == k + 1);
-    }
+    for (int q = 0; q < kPer; q++) nf[q] = decrement(deg, u[q], k, chk);
 #pragma unroll
-    for (int q = 0; q < kPer; q++) append_frontier<CLAIM>(nf[q], u[q], k, rp, core, order, wq, ctl, stk, sn);
+    for (int q = 0; q < kPer; q++) append_frontier<CLAIM>(nf[q], u[q], k, rp, core, order, wq, ctl, bp, gen);
   }
 }
 
-// The warp's own cascade: rows it put on its stack, up to 32 at a time
-// (short rows one lane each, longer ones by the whole warp; their new
-// frontier vertices go back on the stack) until kDrainEdges edges are
-// walked; what is left becomes work items of the next sub-round.
+// The block's own cascade: the rows on its lists of generation gen, walked
+// by all its warps (short rows 32 to a warp, one lane each; long rows one
+// warp each), the new frontier going to the other generation, until the
+// lists are empty or kBlockDrainEdges edges were walked; what is left
+// becomes work items of the next sub-round.  Every thread of the block
+// calls; the lists are empty on return.
 template <bool CLAIM>
-__device__ __forceinline__ void drain_stack(int k, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                                            int32_t *deg, int32_t *core, int32_t *order, long long *wq, KcoreCtl *ctl,
-                                            int *stk, int *sn) {
-  const int lane = threadIdx.x & 31;
-  for (int budget = kDrainEdges; *sn > 0 && budget > 0;) {
-    const int take = min(*sn, 32);
-    *sn -= take;
-    const int u = lane < take ? stk[*sn + lane] : -1;
-    __syncwarp();
-    const int64_t b0 = u >= 0 ? rp[u] : 0;
-    const int len = u >= 0 ? (int)(rp[u + 1] - b0) : 0;
-    budget -= dev::warp_sum(len);
-    walk_short_rows<CLAIM>(b0, len <= 32 ? len : 0, k, rp, ci, deg, core, order, wq, ctl, stk, sn);
-    unsigned lm = __ballot_sync(0xffffffffu, len > 32);
-    while (lm) {
-      const int src = __ffs(lm) - 1;
-      lm &= lm - 1;
-      walk_row<CLAIM>(__shfl_sync(0xffffffffu, b0, src), __shfl_sync(0xffffffffu, len, src), k, rp, ci, deg, core, order, wq,
-               ctl, stk, sn);
+__device__ void block_drain(int k, bool chk, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            int32_t *deg, int32_t *core, int32_t *order, long long *wq, KcoreCtl *ctl, BlockPool *bp,
+                            int gen) {
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  for (;;) {
+    __syncthreads();  // the generation's rows are in place, its edges counted
+    const int ns = min(bp->ns[gen], kPoolShort), nl = min(bp->nl[gen], kPoolLong);
+    const long long walked = bp->edges;
+    __syncthreads();  // every thread has read the counters before they change
+    if (ns + nl == 0) break;
+    if (walked >= kBlockDrainEdges) {
+      for (int j0 = wib * 32; j0 < ns; j0 += kThreads) {
+        const int j = j0 + lane;
+        push_items(j < ns, j < ns ? bp->s[gen][j] : 0, rp, wq, ctl);
+      }
+      for (int j0 = wib * 32; j0 < nl; j0 += kThreads) {
+        const int j = j0 + lane;
+        push_items(j < nl, j < nl ? bp->l[gen][j] : 0, rp, wq, ctl);
+      }
+      break;
     }
+    if (threadIdx.x == 0) {
+      bp->ns[gen ^ 1] = 0;
+      bp->nl[gen ^ 1] = 0;
+    }
+    __syncthreads();
+    int mine = 0;
+    for (int j0 = wib * 32; j0 < ns; j0 += kThreads) {
+      const int j = j0 + lane;
+      const int u = j < ns ? bp->s[gen][j] : -1;
+      const int64_t b0 = u >= 0 ? rp[u] : 0;
+      const int len = u >= 0 ? (int)(rp[u + 1] - b0) : 0;
+      mine += len;
+      walk_short_rows<CLAIM>(b0, len, k, chk, rp, ci, deg, core, order, wq, ctl, bp, gen ^ 1);
+    }
+    for (int j = wib; j < nl; j += kWarps) {
+      const int u = bp->l[gen][j];
+      const int64_t b0 = rp[u];
+      const int len = (int)(rp[u + 1] - b0);
+      if (lane == 0) mine += len;
+      walk_row<CLAIM>(b0, len, k, chk, rp, ci, deg, core, order, wq, ctl, bp, gen ^ 1);
+    }
+    mine = dev::warp_sum(mine);
+    if (lane == 0 && mine) atomicAdd((unsigned long long *)&bp->edges, (unsigned long long)mine);
+    gen ^= 1;
   }
-  for (int i0 = 0; i0 < *sn; i0 += 32) {
-    const bool has = i0 + lane < *sn;
-    push_items(has, has ? stk[i0 + lane] : 0, rp, wq, ctl);
+  if (threadIdx.x == 0) {
+    bp->ns[0] = bp->ns[1] = 0;
+    bp->nl[0] = bp->nl[1] = 0;
+    bp->edges = 0;
   }
-  *sn = 0;
-  __syncwarp();
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, const int64_t *__restrict__ rp,
                                                                  const int32_t *__restrict__ ci, int32_t *deg,
                                                                  int32_t *core, int32_t *order, int32_t *live0,
                                                                  int32_t *live1, long long *wq, KcoreCtl *ctl,
-                                                                 int32_t *err, long long spin_limit) {
+                                                                 int32_t *err, long long spin_limit, int nocheck) {
   __shared__ int bmin;
-  __shared__ int s_stk[kWarps][kLocal];
+  extern __shared__ __align__(16) unsigned char s_pool[];
+  BlockPool *bp = (BlockPool *)s_pool;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gwarp = (int64_t)blockIdx.x * kWarps + wib;
   const int64_t nwarps = (int64_t)gridDim.x * kWarps;
   const unsigned nblocks = gridDim.x;
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   const unsigned lt = (1u << lane) - 1u;
+  const bool chk_sub = nocheck == 0;
+  if (threadIdx.x == 0) {
+    bp->ns[0] = bp->ns[1] = 0;
+    bp->nl[0] = bp->nl[1] = 0;
+    bp->edges = 0;
+  }
 
   int k = 0;
   unsigned level = 0;
   long long otail_now = 0, otail_prev = 0, wtail_now = 0, wstart = 0;
   int64_t live_count = n;  // level 0 scans every vertex (identity list)
   int32_t *lin = live0, *lout = live1;
-  int *stk = s_stk[wib];
 
   for (;;) {
     // ---------------- scan: frontier of level k, compaction of the rest ----
@@ -296,38 +374,65 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
       ctl->live_n[(level + 1) & 1] = 0;
     }
     __syncthreads();
-    int lmin = INT_MAX, sn0 = 0;
+    int lmin = INT_MAX;
     int *lout_n = &ctl->live_n[level & 1];
     const bool scan_local = live_count <= kScanLocalLive;  // the same in every block
-    for (int64_t base = gwarp * 32; base < live_count; base += nwarps * 32) {
-      int64_t i = base + lane;
-      int v = -1, d = INT_MIN;
-      if (i < live_count) {
-        v = (level == 0) ? (int)i : lin[i];
-        d = __ldcg(deg + v);
+    // groups of kScanSlices slices of 32 live entries go round-robin over the
+    // blocks first, so a run of frontier vertices in the list is spread over
+    // many blocks; a warp reads a group's entries and degrees at once, takes
+    // its place in the next live list with one atomic, and appends the
+    // group's frontier 32 vertices at a time
+    int *fw = bp->fscan[wib];
+    constexpr int kGroup = 32 * kScanSlices;
+    for (int64_t sg = blockIdx.x + (int64_t)nblocks * wib; sg * kGroup < live_count; sg += nwarps) {
+      int v[kScanSlices], d[kScanSlices];
+#pragma unroll
+      for (int q = 0; q < kScanSlices; q++) {
+        const int64_t i = sg * kGroup + q * 32 + lane;
+        v[q] = -1;
+        if (i < live_count) v[q] = (level == 0) ? (int)i : lin[i];
       }
-      const bool keep = d > k;
-      if (keep) lmin = min(lmin, d);
-      const unsigned km = __ballot_sync(0xffffffffu, keep);
-      if (km) {
-        int ob = 0;
-        if (lane == 0) ob = atomicAdd(lout_n, __popc(km));
-        ob = __shfl_sync(0xffffffffu, ob, 0);
-        if (keep) lout[ob + __popc(km & lt)] = v;
+#pragma unroll
+      for (int q = 0; q < kScanSlices; q++) d[q] = v[q] >= 0 ? __ldcg(deg + v[q]) : INT_MIN;
+      int ktot = 0;
+#pragma unroll
+      for (int q = 0; q < kScanSlices; q++) {
+        if (d[q] > k) lmin = min(lmin, d[q]);
+        ktot += __popc(__ballot_sync(0xffffffffu, d[q] > k));
       }
-      if (scan_local)
-        append_frontier<true>(d == k, v, k, rp, core, order, wq, ctl, stk, &sn0);
-      else
-        append_frontier<false>(d == k, v, k, rp, core, order, wq, ctl);
+      int ob = 0;
+      if (lane == 0 && ktot) ob = atomicAdd(lout_n, ktot);
+      ob = __shfl_sync(0xffffffffu, ob, 0);
+      int ftot = 0;
+#pragma unroll
+      for (int q = 0; q < kScanSlices; q++) {
+        const unsigned km = __ballot_sync(0xffffffffu, d[q] > k);
+        if (d[q] > k) lout[ob + __popc(km & lt)] = v[q];
+        ob += __popc(km);
+        const unsigned fm = __ballot_sync(0xffffffffu, d[q] == k);
+        if (d[q] == k) fw[ftot + __popc(fm & lt)] = v[q];
+        ftot += __popc(fm);
+      }
+      __syncwarp();
+      for (int f0 = 0; f0 < ftot; f0 += 32) {
+        const bool has = f0 + lane < ftot;
+        const int u = has ? fw[f0 + lane] : -1;
+        if (scan_local)
+          append_frontier<true>(has, u, k, rp, core, order, wq, ctl, bp, 0);
+        else
+          append_frontier<false>(has, u, k, rp, core, order, wq, ctl);
+      }
+      __syncwarp();
     }
-    // the frontier a warp found (up to its stack) is peeled at once by that
-    // warp, while others may still be scanning: a vertex they read at degree
-    // k after a decrement here is claimed once; one kept at k + 1 and then
-    // peeled here is dropped by the next scan, its degree being <= k.  Above
-    // kScanLocalLive live vertices the frontier is large enough to keep every
-    // warp busy in the sub-rounds: the scan only lists it (no decrement runs
-    // during the scan, so each vertex joins once without a claim)
-    if (scan_local) drain_stack<true>(k, rp, ci, deg, core, order, wq, ctl, stk, &sn0);
+    // the frontier a block found (up to its lists) is peeled at once by that
+    // block, while others may still be scanning: a vertex they read at
+    // degree k after a decrement here is claimed once; one kept at k + 1 and
+    // then peeled here is dropped by the next scan, its degree being <= k.
+    // Above kScanLocalLive live vertices the frontier is large enough to
+    // keep every warp busy in the sub-rounds: the scan only lists it (no
+    // decrement runs during the scan, so each vertex joins once without a
+    // claim)
+    if (scan_local) block_drain<true>(k, true, rp, ci, deg, core, order, wq, ctl, bp, 0);
     lmin = -dev::warp_max(-lmin);
     if (lane == 0 && lmin != INT_MAX) atomicMin(&bmin, lmin);
     __syncthreads();
@@ -354,10 +459,9 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
     // while processing them form the next sub-round.  Warps take groups of
     // 32 items statically: rows shorter than 32 edges are walked one lane per
     // item (lanes in step, so appends stay warp-aggregated), longer chunks by
-    // the whole warp.
+    // the whole warp.  The frontier they find goes to the block's lists.
     long long s0 = wstart, e0 = wtail_now;
     while (s0 < e0) {
-      int sn = 0;
       // pass A: items of fewer than 32 edges, 32 per warp, one lane each
       for (long long gb = s0 + gwarp * 32; gb < e0; gb += nwarps * 32) {
         const long long t = gb + lane;
@@ -370,7 +474,8 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
           b0 = rp[v] + (int64_t)c * kChunk;
           len = (int)(min(rp[v + 1], b0 + kChunk) - b0);
         }
-        walk_short_rows<false>(b0, (valid && len < 32) ? len : 0, k, rp, ci, deg, core, order, wq, ctl, stk, &sn);
+        walk_short_rows<false>(b0, (valid && len < 32) ? len : 0, k, chk_sub, rp, ci, deg, core, order, wq, ctl, bp,
+                               0);
       }
       // pass B: longer chunks, one warp each (coalesced row reads)
       for (long long t = s0 + gwarp; t < e0; t += nwarps) {
@@ -379,9 +484,9 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
         const int64_t b0 = rp[v] + (int64_t)c * kChunk;
         const int len = (int)(min(rp[v + 1], b0 + kChunk) - b0);
         if (len < 32) continue;
-        walk_row<false>(b0, len, k, rp, ci, deg, core, order, wq, ctl, stk, &sn);
+        walk_row<false>(b0, len, k, chk_sub, rp, ci, deg, core, order, wq, ctl, bp, 0);
       }
-      drain_stack<false>(k, rp, ci, deg, core, order, wq, ctl, stk, &sn);
+      block_drain<false>(k, chk_sub, rp, ci, deg, core, order, wq, ctl, bp, 0);
       long long e1 = 0;
       barrier_snap(ctl, nblocks, err, spin_limit, &otail_now, &e1, nullptr, nullptr);
       if (*(volatile int32_t *)err) return;
@@ -397,10 +502,17 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
   }
 }
 
+// A peel that stopped early (its spin limit ran out) leaves the tail of the
+// order unwritten: such entries are skipped and reported, never used as an
+// index.
 __global__ void peel_pos_kernel(int64_t n, const int32_t *__restrict__ order, int32_t *__restrict__ pos,
-                                const int32_t *__restrict__ core, int32_t *__restrict__ maxcore) {
+                                const int32_t *__restrict__ core, int32_t *__restrict__ maxcore, int32_t *err) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int v = order[i];
+    if (v < 0 || (int64_t)v >= n) {
+      atomicCAS(err, kDevOk, kDevCheck);
+      continue;
+    }
     pos[v] = (int32_t)i;
     if (i == n - 1) *maxcore = core[v];  // the peel order is nondecreasing in K
   }
@@ -581,7 +693,10 @@ int launch_core_numbers(mc_graph *g, long long spin_limit) {
   MC_CUDA_TRY(cudaGetLastError());
 
   int per_sm = 0;
-  MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kcore_peel_kernel, kThreads, 0));
+  const size_t pool = sizeof(BlockPool);
+  MC_CUDA_TRY(cudaFuncSetAttribute((const void *)kcore_peel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)pool));
+  MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kcore_peel_kernel, kThreads, pool));
   if (per_sm < 1) return MC_ERR_CUDA;
   int blocks = g->sm_count;
   int64_t need = (n + kThreads - 1) / kThreads;
@@ -591,11 +706,13 @@ int launch_core_numbers(mc_graph *g, long long spin_limit) {
   const int32_t *ci = g->col_idx;
   int32_t *core = g->core, *order = g->order, *err = g->err;
   long long sl = spin_limit;
-  void *args[] = {&n_arg, (void *)&rp, (void *)&ci, &deg, &core, &order, &live0, &live1, &wq, &ctl, &err, &sl};
-  MC_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)kcore_peel_kernel, dim3(blocks), dim3(kThreads), args, 0,
+  int nocheck = n <= kNoCheckMaxN ? 1 : 0;
+  void *args[] = {&n_arg, (void *)&rp, (void *)&ci, &deg, &core, &order, &live0, &live1, &wq, &ctl, &err, &sl,
+                  &nocheck};
+  MC_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)kcore_peel_kernel, dim3(blocks), dim3(kThreads), args, pool,
                                           g->stream));
   g_launches++;
-  peel_pos_kernel<<<ib, 256, 0, g->stream>>>(n, g->order, g->pos, g->core, maxdeg + 1);
+  peel_pos_kernel<<<ib, 256, 0, g->stream>>>(n, g->order, g->pos, g->core, maxdeg + 1, g->err);
   g_launches++;
   MC_CUDA_TRY(cudaGetLastError());
   if (g->capturing) {  // K(G) and the degree bound are kept from the direct solve before capture
@@ -732,18 +849,23 @@ extern "C" int mc_core_numbers_noalloc(int64_t n, const int64_t *row_ptr, const 
   g_launches++;
   MC_CUDA_TRY(cudaGetLastError());
   int per_sm = 0;
-  MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kcore_peel_kernel, kThreads, 0));
+  const size_t pool = sizeof(BlockPool);
+  MC_CUDA_TRY(cudaFuncSetAttribute((const void *)kcore_peel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)pool));
+  MC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kcore_peel_kernel, kThreads, pool));
   if (per_sm < 1) return MC_ERR_CUDA;
   int blocks = sms;
   const int64_t need = (n + kThreads - 1) / kThreads;
   if (need < blocks) blocks = (int)std::max<int64_t>(1, need);
   int64_t n_arg = n;
   long long sl = kDefaultSpinLimit;
+  int nocheck = n <= kNoCheckMaxN ? 1 : 0;
   void *args[] = {&n_arg, (void *)&row_ptr, (void *)&col_idx, &deg, &core_out, &order, &live0, &live1, &wq, &ctl,
-                  &err, &sl};
-  MC_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)kcore_peel_kernel, dim3(blocks), dim3(kThreads), args, 0, s));
+                  &err, &sl, &nocheck};
+  MC_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)kcore_peel_kernel, dim3(blocks), dim3(kThreads), args, pool,
+                                          s));
   g_launches++;
-  peel_pos_kernel<<<ib, 256, 0, s>>>(n, order, pos, core_out, maxdeg + 1);
+  peel_pos_kernel<<<ib, 256, 0, s>>>(n, order, pos, core_out, maxdeg + 1, err);
   g_launches++;
   MC_CUDA_TRY(cudaGetLastError());
   int32_t host[3] = {0, 0, 0};
