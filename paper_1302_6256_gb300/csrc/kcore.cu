@@ -48,8 +48,8 @@ constexpr int kPoolShort = 4096;  // block list of rows of 1..32 edges (one lane
 constexpr int kPoolLong = 2048;   // block list of rows of 33..kLocalRow edges (one warp per row)
 constexpr long long kBlockDrainEdges = 65536;  // edges a block walks from its lists per phase (then it spills)
 constexpr int64_t kScanLocalLive = (int64_t)1 << 21;  // live vertices up to which the scan peels locally
-constexpr int kScanSlices = 4;  // slices of 32 live entries a warp's scan reads at once
-constexpr int64_t kNoCheckMaxN = (int64_t)1 << 23;  // degree arrays up to 32 MB stay in L2: sub-rounds decrement unread
+constexpr int kScanSlices = 8;  // slices of 32 live entries a warp's scan reads at once
+constexpr int64_t kNoCheckMaxN = (int64_t)1 << 23;  // degree arrays up to 32 MB stay in L2: decrements unread
 
 struct KcoreCtl {
   unsigned bar_count, bar_gen;
@@ -223,16 +223,22 @@ __device__ __forceinline__ void push_items(bool has, int u, const int64_t *__res
   for (int c = 0; c < nch; c++) wq[at + c] = ((long long)u << 32) | (unsigned)c;
 }
 
-// One decrement of neighbour u at level k; true when it takes u's degree
-// from k + 1 to k.  With chk the degree is read first and only a degree
-// above k is decremented: while a scan may still read the degrees, a vertex
-// at exactly k must stay at k for it.  Without chk (sub-rounds, where every
-// vertex at k or below is already peeled and its degree no longer read) the
-// read is skipped and a peeled neighbour's degree just goes lower.
+// One decrement of neighbour u at level k; true when u joins the level-k
+// frontier through it.  With chk the degree is read first and only a degree
+// above k is decremented, so the decrement that takes it from k + 1 to k is
+// the one that finds u.  Without chk the read is skipped: a peeled
+// neighbour's degree (at most k, no longer read) just goes lower.  In the
+// sub-rounds every vertex at degree k or below is already peeled, so again
+// only k + 1 -> k finds one; while a scan may still read the degrees
+// (CLAIM), a vertex still at exactly k may not have been reached by it yet,
+// so the decrement from k claims it too (the claim's compare-and-swap keeps
+// each vertex to one join).
+template <bool CLAIM>
 __device__ __forceinline__ bool decrement(int32_t *deg, int u, int k, bool chk) {
   if (u < 0) return false;
   if (chk && __ldcg(deg + u) <= k) return false;
-  return atomicSub(deg + u, 1) == k + 1;
+  const int old = atomicSub(deg + u, 1);
+  return old == k + 1 || (CLAIM && !chk && old == k);
 }
 
 // Walk one row (b0, len) with the whole warp (coalesced), kPer edges per
@@ -251,7 +257,7 @@ __device__ __forceinline__ void walk_row(int64_t b0, int len, int k, bool chk, c
       u[q] = e < len ? ci[b0 + e] : -1;
     }
 #pragma unroll
-    for (int q = 0; q < kPer; q++) nf[q] = decrement(deg, u[q], k, chk);
+    for (int q = 0; q < kPer; q++) nf[q] = decrement<CLAIM>(deg, u[q], k, chk);
 #pragma unroll
     for (int q = 0; q < kPer; q++) append_frontier<CLAIM>(nf[q], u[q], k, rp, core, order, wq, ctl, bp, gen);
   }
@@ -272,7 +278,7 @@ __device__ __forceinline__ void walk_short_rows(int64_t b0, int len, int k, bool
 #pragma unroll
     for (int q = 0; q < kPer; q++) u[q] = (j0 + q < len) ? ci[b0 + j0 + q] : -1;
 #pragma unroll
-    for (int q = 0; q < kPer; q++) nf[q] = decrement(deg, u[q], k, chk);
+    for (int q = 0; q < kPer; q++) nf[q] = decrement<CLAIM>(deg, u[q], k, chk);
 #pragma unroll
     for (int q = 0; q < kPer; q++) append_frontier<CLAIM>(nf[q], u[q], k, rp, core, order, wq, ctl, bp, gen);
   }
@@ -353,7 +359,7 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
   const unsigned nblocks = gridDim.x;
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   const unsigned lt = (1u << lane) - 1u;
-  const bool chk_sub = nocheck == 0;
+  const bool chk = nocheck == 0;
   if (threadIdx.x == 0) {
     bp->ns[0] = bp->ns[1] = 0;
     bp->nl[0] = bp->nl[1] = 0;
@@ -432,7 +438,7 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
     // keep every warp busy in the sub-rounds: the scan only lists it (no
     // decrement runs during the scan, so each vertex joins once without a
     // claim)
-    if (scan_local) block_drain<true>(k, true, rp, ci, deg, core, order, wq, ctl, bp, 0);
+    if (scan_local) block_drain<true>(k, chk, rp, ci, deg, core, order, wq, ctl, bp, 0);
     lmin = -dev::warp_max(-lmin);
     if (lane == 0 && lmin != INT_MAX) atomicMin(&bmin, lmin);
     __syncthreads();
@@ -474,7 +480,7 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
           b0 = rp[v] + (int64_t)c * kChunk;
           len = (int)(min(rp[v + 1], b0 + kChunk) - b0);
         }
-        walk_short_rows<false>(b0, (valid && len < 32) ? len : 0, k, chk_sub, rp, ci, deg, core, order, wq, ctl, bp,
+        walk_short_rows<false>(b0, (valid && len < 32) ? len : 0, k, chk, rp, ci, deg, core, order, wq, ctl, bp,
                                0);
       }
       // pass B: longer chunks, one warp each (coalesced row reads)
@@ -484,9 +490,9 @@ __global__ void __launch_bounds__(kThreads, 1) kcore_peel_kernel(int64_t n, cons
         const int64_t b0 = rp[v] + (int64_t)c * kChunk;
         const int len = (int)(min(rp[v + 1], b0 + kChunk) - b0);
         if (len < 32) continue;
-        walk_row<false>(b0, len, k, chk_sub, rp, ci, deg, core, order, wq, ctl, bp, 0);
+        walk_row<false>(b0, len, k, chk, rp, ci, deg, core, order, wq, ctl, bp, 0);
       }
-      block_drain<false>(k, chk_sub, rp, ci, deg, core, order, wq, ctl, bp, 0);
+      block_drain<false>(k, chk, rp, ci, deg, core, order, wq, ctl, bp, 0);
       long long e1 = 0;
       barrier_snap(ctl, nblocks, err, spin_limit, &otail_now, &e1, nullptr, nullptr);
       if (*(volatile int32_t *)err) return;
