@@ -49,7 +49,7 @@ constexpr int kPoolLong = 2048;   // block list of rows of 33..kLocalRow edges (
 constexpr long long kBlockDrainEdges = 65536;  // edges a block walks from its lists per phase (then it spills)
 constexpr int64_t kScanLocalLive = (int64_t)1 << 21;  // live vertices up to which the scan peels locally
 constexpr int kScanSlices = 8;  // slices of 32 live entries a warp's scan reads at once
-constexpr int64_t kNoCheckMaxN = (int64_t)1 << 23;  // degree arrays up to 32 MB stay in L2: decrements unread
+constexpr int64_t kNoCheckMaxN = (int64_t)1 << 24;  // degree arrays up to 64 MB stay in L2: decrements unread
 
 struct KcoreCtl {
   unsigned bar_count, bar_gen;
