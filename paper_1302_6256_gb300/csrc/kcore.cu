@@ -11,10 +11,11 @@
 //           their place in the next list).  Up to kScanLocalLive live
 //           vertices, each block peels the frontier its warps found right
 //           after its scan, from lists in shared memory that all its warps
-//           share: rows of at most 32 edges one lane each, rows of up to
-//           kLocalRow edges one warp each, the cascade they start as further
-//           generations of the same lists, up to kBlockDrainEdges edges;
-//           everything else becomes work items, one per 128-edge chunk;
+//           share: rows of at most 32 edges one lane each, the 128-edge
+//           chunks of rows of up to kLocalRow edges one warp each, the
+//           cascade they start as further generations of the same lists, up
+//           to kBlockDrainEdges edges; everything else becomes work items,
+//           one per 128-edge chunk;
 //   process after a grid barrier, the work items appended so far are split
 //           statically over all warps (rows under 32 edges one lane per
 //           item, longer chunks one warp per item, coalesced); every
@@ -43,9 +44,9 @@ constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
 constexpr int kChunk = 128;  // edges per work item
 constexpr int kPer = 4;      // edges per lane in flight
-constexpr int kLocalRow = 512;  // rows of at most this many edges may go onto the block lists
+constexpr int kLocalRow = 4096;  // rows of at most this many edges may go onto the block lists
 constexpr int kPoolShort = 4096;  // block list of rows of 1..32 edges (one lane per row)
-constexpr int kPoolLong = 2048;   // block list of rows of 33..kLocalRow edges (one warp per row)
+constexpr int kPoolLong = 2048;   // block list of 128-edge chunks of rows of 33..kLocalRow edges (a warp each)
 constexpr long long kBlockDrainEdges = 65536;  // edges a block walks from its lists per phase (then it spills)
 constexpr int64_t kScanLocalLive = (int64_t)1 << 21;  // live vertices up to which the scan peels locally
 constexpr int kScanSlices = 8;  // slices of 32 live entries a warp's scan reads at once
@@ -113,14 +114,15 @@ __global__ void degree_init_kernel(int64_t n, const int64_t *__restrict__ rp, in
 }
 
 // The rows a block peels within one phase: two generations of two lists
-// (rows of 1..32 edges, walked one lane per row; rows of 33..kLocalRow
-// edges, walked by one warp each).  The new frontier found while one
-// generation is walked goes to the other, so the block's 32 warps share its
-// cascade.  A counter may run past its list's capacity: the entries beyond
-// it were not stored (those rows became work items instead).
+// (rows of 1..32 edges, walked one lane per row; the 128-edge chunks of rows
+// of 33..kLocalRow edges, encoded like work items and walked by one warp
+// each).  The new frontier found while one generation is walked goes to the
+// other, so the block's 32 warps share its cascade.  A counter may run past
+// its list's capacity: the entries beyond it were not stored (those rows or
+// chunks became work items instead).
 struct BlockPool {
   int s[2][kPoolShort];
-  int l[2][kPoolLong];
+  long long l[2][kPoolLong];
   int ns[2], nl[2];
   long long edges;  // edges walked from the lists in this phase
   int fscan[kWarps][32 * kScanSlices];  // a warp's scanned frontier, compacted
@@ -151,15 +153,23 @@ __device__ __forceinline__ void append_frontier(bool nf, int u, int k, const int
   const unsigned lt = (1u << lane) - 1u;
   int64_t d = 0;
   if (nf) d = rp[u + 1] - rp[u];
-  bool put = false;
+  // chunks [c0, c0 + nch) of the lane's row become work items
+  int c0 = 0, nch = (nf && d > 0) ? (int)((d + kChunk - 1) / kChunk) : 0;
   if (bp) {
     const bool sh = nf && d > 0 && d <= 32;
     const bool lg = nf && d > 32 && d <= kLocalRow;
-    const unsigned ms = __ballot_sync(0xffffffffu, sh), ml = __ballot_sync(0xffffffffu, lg);
+    const unsigned ms = __ballot_sync(0xffffffffu, sh);
+    int lincl = lg ? nch : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, lincl, o);
+      if (lane >= o) lincl += y;
+    }
+    const int ltot = __shfl_sync(0xffffffffu, lincl, 31);
     int bs = 0, bl = 0;
     if (lane == 0) {
       if (ms) bs = atomicAdd(&bp->ns[gen], __popc(ms));
-      if (ml) bl = atomicAdd(&bp->nl[gen], __popc(ml));
+      if (ltot) bl = atomicAdd(&bp->nl[gen], ltot);
     }
     bs = __shfl_sync(0xffffffffu, bs, 0);
     bl = __shfl_sync(0xffffffffu, bl, 0);
@@ -167,18 +177,18 @@ __device__ __forceinline__ void append_frontier(bool nf, int u, int k, const int
       const int at = bs + __popc(ms & lt);
       if (at < kPoolShort) {
         bp->s[gen][at] = u;
-        put = true;
+        nch = 0;
       }
     }
     if (lg) {
-      const int at = bl + __popc(ml & lt);
-      if (at < kPoolLong) {
-        bp->l[gen][at] = u;
-        put = true;
-      }
+      // the chunks that fit go onto the list, the rest become work items
+      const int at = bl + lincl - nch;
+      const int fit = max(0, min(nch, kPoolLong - at));
+      for (int c = 0; c < fit; c++) bp->l[gen][at + c] = ((long long)u << 32) | (unsigned)c;
+      c0 = fit;
+      nch -= fit;
     }
   }
-  const int nch = (nf && !put) ? (int)((d + kChunk - 1) / kChunk) : 0;
   int incl = nch;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -197,9 +207,20 @@ __device__ __forceinline__ void append_frontier(bool nf, int u, int k, const int
   if (nf) {
     order[ob + __popc(m & lt)] = u;
     long long at = wb + incl - nch;
-    for (int c = 0; c < nch; c++) wq[at + c] = ((long long)u << 32) | (unsigned)c;
+    for (int c = 0; c < nch; c++) wq[at + c] = ((long long)u << 32) | (unsigned)(c0 + c);
   }
   __syncwarp();
+}
+
+// One work item per lane that has one (a chunk entry of a block list).
+__device__ __forceinline__ void push_entry(bool has, long long e, long long *wq, KcoreCtl *ctl) {
+  const int lane = threadIdx.x & 31;
+  const unsigned m = __ballot_sync(0xffffffffu, has);
+  if (!m) return;
+  long long wb = 0;
+  if (lane == 0) wb = (long long)atomicAdd((unsigned long long *)&ctl->wtail, (unsigned long long)__popc(m));
+  wb = __shfl_sync(0xffffffffu, wb, 0);
+  if (has) wq[wb + __popc(m & ((1u << lane) - 1u))] = e;
 }
 
 // Work items (one per chunk) for lanes' vertices already in the peel order:
@@ -308,7 +329,7 @@ __device__ void block_drain(int k, bool chk, const int64_t *__restrict__ rp, con
       }
       for (int j0 = wib * 32; j0 < nl; j0 += kThreads) {
         const int j = j0 + lane;
-        push_items(j < nl, j < nl ? bp->l[gen][j] : 0, rp, wq, ctl);
+        push_entry(j < nl, j < nl ? bp->l[gen][j] : 0, wq, ctl);
       }
       break;
     }
@@ -327,9 +348,10 @@ __device__ void block_drain(int k, bool chk, const int64_t *__restrict__ rp, con
       walk_short_rows<CLAIM>(b0, len, k, chk, rp, ci, deg, core, order, wq, ctl, bp, gen ^ 1);
     }
     for (int j = wib; j < nl; j += kWarps) {
-      const int u = bp->l[gen][j];
-      const int64_t b0 = rp[u];
-      const int len = (int)(rp[u + 1] - b0);
+      const long long e = bp->l[gen][j];
+      const int u = (int)(e >> 32), c = (int)(e & 0xffffffff);
+      const int64_t b0 = rp[u] + (int64_t)c * kChunk;
+      const int len = (int)(min(rp[u + 1], b0 + kChunk) - b0);
       if (lane == 0) mine += len;
       walk_row<CLAIM>(b0, len, k, chk, rp, ci, deg, core, order, wq, ctl, bp, gen ^ 1);
     }
