@@ -25,8 +25,11 @@
 //           next sub-round, until a sub-round appends nothing.
 // In the scan phase a vertex joins by claiming its core number
 // (compare-and-swap from -1), so one that a scan reads at degree k just after
-// a decrement made it k joins once; in the sub-rounds only the decrement that
-// takes a degree from k + 1 to k finds a vertex, and a plain store does.  The
+// a decrement made it k joins once; where decrements skip the read of the
+// degree (degree arrays that fit in L2), a decrement from k also claims, for a
+// vertex still at k that the scan has not reached.  In the sub-rounds only the
+// decrement that takes a degree from k + 1 to k finds a vertex, and a plain
+// store does.  The
 // append order is a degeneracy order: when a vertex joins, every neighbour
 // that joins later is still counted in its remaining degree, which is at most
 // k.  It becomes the search's vertex ranking.
@@ -306,8 +309,8 @@ __device__ __forceinline__ void walk_short_rows(int64_t b0, int len, int k, bool
 }
 
 // The block's own cascade: the rows on its lists of generation gen, walked
-// by all its warps (short rows 32 to a warp, one lane each; long rows one
-// warp each), the new frontier going to the other generation, until the
+// by all its warps (short rows 32 to a warp, one lane each; chunks of long
+// rows one warp each), the new frontier going to the other generation, until the
 // lists are empty or kBlockDrainEdges edges were walked; what is left
 // becomes work items of the next sub-round.  Every thread of the block
 // calls; the lists are empty on return.
