@@ -93,6 +93,11 @@ C_MUTANTS = [
     ("threads-clique-member-as-index", "w->C[csize] = w->P[u];", "w->C[csize] = u;", False),
     ("threads-witness-in-new-ids", "sh->H[i] = sh->orig[w->C[i]];", "sh->H[i] = w->C[i];", False),
     ("threads-incumbent-not-published", "    __atomic_store_n(&sh->best, size, __ATOMIC_RELEASE);\n", "", False),
+    ("threads-branch-coloured-in-rank-order",
+     "static int cmp_knkey_id(const void *x, const void *y) {\n  const knkey *a = (const knkey *)x, *b = (const knkey *)y;\n"
+     "  return (a->id > b->id) - (a->id < b->id);",
+     "static int cmp_knkey_id(const void *x, const void *y) {\n  const knkey *a = (const knkey *)x, *b = (const knkey *)y;\n"
+     "  return (a->i > b->i) - (a->i < b->i);", False),
     # the partitioned search
     ("part-searches-the-other-roots", "if (sh->opos[u] % sh->part_count != sh->part_rank) return;",
      "if (sh->opos[u] % sh->part_count == sh->part_rank) return;", False),
