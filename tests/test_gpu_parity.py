@@ -89,6 +89,39 @@ def test_core_numbers_bit_exact(mc, g):
     assert kmax == (int(ref.max()) if g.n else 0)
 
 
+def _is_degeneracy_order(g, order, core):
+    """Every vertex has at most K(v) neighbours after it in the order."""
+    pos = np.empty(g.n, np.int64)
+    pos[order] = np.arange(g.n)
+    src = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    later = np.bincount(src[pos[g.col_idx] > pos[src]], minlength=g.n)
+    return np.array_equal(np.sort(order), np.arange(g.n)) and bool(np.all(later <= core))
+
+
+def test_peel_block_lists_overflow_and_long_cascades(mc):
+    """Shapes that push the peel past its per-block lists, with core numbers
+    fixed by closed forms: a perfect matching of 2^21 vertices (level 1 is
+    every vertex at once, 13,800 rows per block against lists of 4,096: the
+    rest becomes work items while the scan still claims), a path of 200,000
+    vertices (one cascade 100,000 steps long, past a block's edge budget, so
+    its list spills into the next sub-round) and K(40, 400000) (at level 40
+    the 400,000 rows of 40 edges overflow the 2,048 chunk entries of every
+    block).  The peel order must stay a degeneracy order."""
+    n = 1 << 21
+    ev = np.arange(0, n, 2)
+    cases = [(gg.from_edges(n, ev, ev + 1, "matching"), 1), (gg.path(200000), 1),
+             (gg.complete_bipartite(40, 400000), 40)]
+    for g, k in cases:
+        h = load(mc, g, flags=0)
+        core, kmax = mc.mc_core_numbers(h)
+        assert kmax == k and np.all(core == k), g.name
+        order = mc.mc_peel_order(h).copy()
+        assert _is_degeneracy_order(g, order, core), g.name
+        om, wit, st = mc.mc_max_clique(h)
+        assert om == 2 and oracle.is_clique(g, wit), g.name
+        h.close()
+
+
 @pytest.mark.parametrize("g", small_graphs() + medium_graphs(), ids=lambda g: g.name)
 def test_max_clique_matches_oracle(mc, g):
     h = load(mc, g)
